@@ -1,0 +1,500 @@
+/*
+ * lise_oracle.c -- FP64 CPU oracle for the two-component TDSLDA step.
+ *
+ * TEST INFRASTRUCTURE ONLY (see lise_oracle.h).  Plain loops, a recursive
+ * mixed-radix Cooley-Tukey DFT written for this file, FP64 throughout,
+ * compensated (Neumaier) summation for the density and energy sums.  OpenMP is
+ * used only over independent quasiparticle states or lattice sites, never
+ * inside a sum, so results do not depend on the thread count.
+ *
+ * Readings of points the paper leaves open (all listed again in the design doc):
+ *   - Eq. p prints the y'_n coefficient without a number; 119 is used (the
+ *     unique value that makes the predictor exact for polynomials of degree 4
+ *     and gives the printed error constant 161/480).
+ *   - (p_n - c_n) is taken as 0 at the first ABM step.
+ *   - The series-expansion start runs 3 steps (y_0 -> y_3), storing
+ *     y'_k = f(t_k, y_k) for k = 0..3; ABM starts at n = 3.
+ *   - In each start step H(t) uses V_ext(t); the corrector Hamiltonian uses the
+ *     averaged densities n_cor = (n_pre + n(t))/2, nu_cor likewise, and
+ *     V_ext(t + dt/2).
+ *   - The Nyquist mode is kept in k^2 (zeroing applies to odd derivatives only).
+ */
+#include "lise_oracle.h"
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+static const double OR_PI = 3.14159265358979323846264338327950288;
+
+int or_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+/* ---------------------------------------------------------------- DFT ---- */
+
+static int smallest_factor(int n) {
+  for (int p = 2; p * p <= n; ++p)
+    if (n % p == 0) return p;
+  return n;
+}
+
+/* exp(sign * 2 pi i * j / n), argument reduced to j mod n first. */
+static double complex root_of_unity(long j, int n, int sign) {
+  long r = j % n;
+  if (r < 0) r += n;
+  double ang = 2.0 * OR_PI * (double)r / (double)n;
+  return cos(ang) + (double)sign * I * sin(ang);
+}
+
+/* Decimation in time: split the length-n input into p interleaved sub-
+ * sequences x[r + p j] (r < p), transform each (length m = n/p), then combine
+ *   X[k + m q] = sum_r W_n^{r (k + m q)} Y_r[k],  W_n = exp(sign 2 pi i / n).
+ * tw[j] holds exp(sign 2 pi i j / N) for the top-level length N; at length n
+ * the root W_n^e is tw[e * (N/n) mod N]. */
+static void dft_rec(const double complex *in, long istride, double complex *out,
+                    int n, int N, const double complex *tw) {
+  if (n == 1) {
+    out[0] = in[0];
+    return;
+  }
+  int p = smallest_factor(n);
+  int m = n / p;
+  for (int r = 0; r < p; ++r)
+    dft_rec(in + r * istride, istride * p, out + (long)r * m, m, N, tw);
+  long step = N / n;
+  double complex y[64];
+  double complex *ybuf = (p <= 64) ? y : (double complex *)malloc(sizeof(double complex) * p);
+  for (int k = 0; k < m; ++k) {
+    for (int r = 0; r < p; ++r) ybuf[r] = out[(long)r * m + k];
+    for (int q = 0; q < p; ++q) {
+      double complex acc = 0.0;
+      for (int r = 0; r < p; ++r) {
+        long e = ((long)r * (k + (long)m * q)) % n;
+        acc += ybuf[r] * tw[(e * step) % N];
+      }
+      out[k + (long)m * q] = acc;
+    }
+  }
+  if (ybuf != y) free(ybuf);
+}
+
+void or_dft1d(const double complex *in, double complex *out, int n, int sign) {
+  double complex *tw = (double complex *)malloc(sizeof(double complex) * n);
+  for (int j = 0; j < n; ++j) tw[j] = root_of_unity(j, n, sign);
+  dft_rec(in, 1, out, n, n, tw);
+  free(tw);
+}
+
+/* 3D transform: 1D DFTs along x, then y, then z, each line gathered into a
+ * contiguous buffer. */
+void or_fft3d(double complex *vol, int nx, int ny, int nz, int sign) {
+  int nmax = nx > ny ? nx : ny;
+  if (nz > nmax) nmax = nz;
+  double complex *twx = (double complex *)malloc(sizeof(double complex) * nx);
+  double complex *twy = (double complex *)malloc(sizeof(double complex) * ny);
+  double complex *twz = (double complex *)malloc(sizeof(double complex) * nz);
+  for (int j = 0; j < nx; ++j) twx[j] = root_of_unity(j, nx, sign);
+  for (int j = 0; j < ny; ++j) twy[j] = root_of_unity(j, ny, sign);
+  for (int j = 0; j < nz; ++j) twz[j] = root_of_unity(j, nz, sign);
+  double complex *a = (double complex *)malloc(sizeof(double complex) * nmax);
+  double complex *b = (double complex *)malloc(sizeof(double complex) * nmax);
+  long sx = 1, sy = nx, sz = (long)nx * ny;
+  for (int z = 0; z < nz; ++z)
+    for (int y = 0; y < ny; ++y) {
+      double complex *line = vol + z * sz + y * sy;
+      for (int i = 0; i < nx; ++i) a[i] = line[i * sx];
+      dft_rec(a, 1, b, nx, nx, twx);
+      for (int i = 0; i < nx; ++i) line[i * sx] = b[i];
+    }
+  for (int z = 0; z < nz; ++z)
+    for (int x = 0; x < nx; ++x) {
+      double complex *line = vol + z * sz + x * sx;
+      for (int i = 0; i < ny; ++i) a[i] = line[i * sy];
+      dft_rec(a, 1, b, ny, ny, twy);
+      for (int i = 0; i < ny; ++i) line[i * sy] = b[i];
+    }
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x) {
+      double complex *line = vol + y * sy + x * sx;
+      for (int i = 0; i < nz; ++i) a[i] = line[i * sz];
+      dft_rec(a, 1, b, nz, nz, twz);
+      for (int i = 0; i < nz; ++i) line[i * sz] = b[i];
+    }
+  if (sign > 0) {
+    double inv = 1.0 / ((double)nx * ny * nz);
+    long nt = (long)nx * ny * nz;
+    for (long i = 0; i < nt; ++i) vol[i] *= inv;
+  }
+  free(a); free(b); free(twx); free(twy); free(twz);
+}
+
+/* Sec. "Discretization": k_n = 2 pi n / L for n < N/2 and 2 pi (n - N) / L for
+ * n >= N/2, L = N a.  The printed second branch, (2n - N) pi / L, would give
+ * k_{N/2} = 0 = k_0; the DVR basis of the same section sums exp(i k_n x) over
+ * n = -N/2 .. N/2-1 with k_n = 2 pi n / L, which fixes the reading used here
+ * (the Nyquist index N/2 maps to k = -pi/a). */
+double or_kgrid(int idx, int n, double a) {
+  double L = n * a;
+  if (idx < n / 2) return 2.0 * OR_PI * idx / L;
+  return 2.0 * OR_PI * (double)(idx - n) / L;
+}
+
+/* ------------------------------------------------------------ operators -- */
+
+void or_kinetic(const or_params *p, const double complex *in, double complex *out) {
+  int nx = p->nx, ny = p->ny, nz = p->nz;
+  long nt = (long)nx * ny * nz;
+  memcpy(out, in, sizeof(double complex) * nt);
+  or_fft3d(out, nx, ny, nz, -1);
+  for (int z = 0; z < nz; ++z) {
+    double kz = or_kgrid(z, nz, p->a);
+    for (int y = 0; y < ny; ++y) {
+      double ky = or_kgrid(y, ny, p->a);
+      for (int x = 0; x < nx; ++x) {
+        double kx = or_kgrid(x, nx, p->a);
+        /* D^(2) = F^-1 [(ik)^2 F];  -(alpha/2) D^(2) multiplies by +(alpha/2) k^2 */
+        out[((long)z * ny + y) * nx + x] *= 0.5 * p->alpha * (kx * kx + ky * ky + kz * kz);
+      }
+    }
+  }
+  or_fft3d(out, nx, ny, nz, +1);
+}
+
+/* Neumaier's compensated summation step. */
+static void neumaier_add(double *sum, double *comp, double x) {
+  double t = *sum + x;
+  if (fabs(*sum) >= fabs(x))
+    *comp += (*sum - t) + x;
+  else
+    *comp += (x - t) + *sum;
+  *sum = t;
+}
+
+void or_densities(const or_params *p, const double complex *psi, double *n,
+                  double complex *nu) {
+  long nt = (long)p->nx * p->ny * p->nz;
+#pragma omp parallel for schedule(static)
+  for (long r = 0; r < nt; ++r) {
+    double sn = 0, cn = 0, sr = 0, cr = 0, si = 0, ci = 0;
+    for (int q = 0; q < p->n_qp; ++q) {
+      double complex u = psi[((long)q * 2 + 0) * nt + r];
+      double complex v = psi[((long)q * 2 + 1) * nt + r];
+      neumaier_add(&sn, &cn, 2.0 * (creal(v) * creal(v) + cimag(v) * cimag(v)));
+      double complex uv = u * conj(v);
+      neumaier_add(&sr, &cr, creal(uv));
+      neumaier_add(&si, &ci, cimag(uv));
+    }
+    n[r] = sn + cn;
+    nu[r] = (sr + cr) + I * (si + ci);
+  }
+}
+
+double or_vext(const or_params *p, int ix, int iy, int iz, double t) {
+  double v = 0.0;
+  if (p->v_static) v = p->v_static[((long)iz * p->ny + iy) * p->nx + ix];
+  if (p->drive_A != 0.0) {
+    double zc = (iz - p->nz / 2) * p->a;
+    v += p->drive_A * sin(p->drive_Omega * t) * zc;
+  }
+  return v;
+}
+
+void or_potentials(const or_params *p, const double *n, const double complex *nu,
+                   double t, double *W, double complex *Delta) {
+  int nx = p->nx, ny = p->ny, nz = p->nz;
+  for (int z = 0; z < nz; ++z)
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        long r = ((long)z * ny + y) * nx + x;
+        double U = 0.5 * p->beta * pow(3.0 * OR_PI * OR_PI * n[r], 2.0 / 3.0);
+        W[r] = U - p->mu + or_vext(p, x, y, z, t);
+        Delta[r] = -p->g * nu[r];
+      }
+}
+
+void or_apply_h(const or_params *p, const double *W, const double complex *Delta,
+                const double complex *psi, double complex *hpsi) {
+  long nt = (long)p->nx * p->ny * p->nz;
+#pragma omp parallel
+  {
+    double complex *tu = (double complex *)malloc(sizeof(double complex) * nt);
+    double complex *cv = (double complex *)malloc(sizeof(double complex) * nt);
+    double complex *tcv = (double complex *)malloc(sizeof(double complex) * nt);
+#pragma omp for schedule(dynamic)
+    for (int q = 0; q < p->n_qp; ++q) {
+      const double complex *u = psi + (long)q * 2 * nt;
+      const double complex *v = u + nt;
+      double complex *hu = hpsi + (long)q * 2 * nt;
+      double complex *hv = hu + nt;
+      or_kinetic(p, u, tu);
+      for (long r = 0; r < nt; ++r) cv[r] = conj(v[r]);
+      or_kinetic(p, cv, tcv);
+      for (long r = 0; r < nt; ++r) {
+        double complex h_u = tu[r] + W[r] * u[r];           /* h u */
+        double complex h_cv = tcv[r] + W[r] * cv[r];        /* h conj(v) */
+        hu[r] = h_u + Delta[r] * v[r];                      /* h u + Delta v */
+        hv[r] = conj(Delta[r]) * u[r] - conj(h_cv);         /* Delta* u - h* v */
+      }
+    }
+    free(tu); free(cv); free(tcv);
+  }
+}
+
+void or_rhs(const or_params *p, const double complex *psi, double t,
+            double complex *dpsi) {
+  long nt = (long)p->nx * p->ny * p->nz;
+  long ns = nt * 2 * (long)p->n_qp;
+  double *n = (double *)malloc(sizeof(double) * nt);
+  double *W = (double *)malloc(sizeof(double) * nt);
+  double complex *nu = (double complex *)malloc(sizeof(double complex) * nt);
+  double complex *D = (double complex *)malloc(sizeof(double complex) * nt);
+  or_densities(p, psi, n, nu);
+  or_potentials(p, n, nu, t, W, D);
+  or_apply_h(p, W, D, psi, dpsi);
+  for (long i = 0; i < ns; ++i) dpsi[i] *= -I; /* i dpsi/dt = H psi (hbar = 1) */
+  free(n); free(W); free(nu); free(D);
+}
+
+/* ------------------------------------------------------------ integrator -- */
+
+struct or_solver {
+  or_params p;
+  double *v_static_copy;
+  long nt, ns;
+  double t, dt;
+  int ready;
+  double complex *y0, *y1;             /* y_n, y_{n-1} */
+  double complex *d[4];                /* y'_n, y'_{n-1}, y'_{n-2}, y'_{n-3} */
+  double complex *pc;                  /* p_n - c_n */
+  double complex *pr, *m, *mp, *c;     /* work: p_{n+1}, m_{n+1}, m', c_{n+1} */
+};
+
+or_solver *or_create(const or_params *p) {
+  or_solver *s = (or_solver *)calloc(1, sizeof(or_solver));
+  s->p = *p;
+  s->nt = (long)p->nx * p->ny * p->nz;
+  s->ns = s->nt * 2 * (long)p->n_qp;
+  if (p->v_static) {
+    s->v_static_copy = (double *)malloc(sizeof(double) * s->nt);
+    memcpy(s->v_static_copy, p->v_static, sizeof(double) * s->nt);
+    s->p.v_static = s->v_static_copy;
+  }
+  size_t bytes = sizeof(double complex) * s->ns;
+  s->y0 = (double complex *)malloc(bytes);
+  s->y1 = (double complex *)malloc(bytes);
+  for (int k = 0; k < 4; ++k) s->d[k] = (double complex *)malloc(bytes);
+  s->pc = (double complex *)malloc(bytes);
+  s->pr = (double complex *)malloc(bytes);
+  s->m = (double complex *)malloc(bytes);
+  s->mp = (double complex *)malloc(bytes);
+  s->c = (double complex *)malloc(bytes);
+  return s;
+}
+
+void or_destroy(or_solver *s) {
+  if (!s) return;
+  free(s->y0); free(s->y1);
+  for (int k = 0; k < 4; ++k) free(s->d[k]);
+  free(s->pc); free(s->pr); free(s->m); free(s->mp); free(s->c);
+  free(s->v_static_copy);
+  free(s);
+}
+
+/* out = sum_{j=0}^{4} (-i dt H)^j / j! psi for fixed potentials (W, Delta):
+ * the order-4 series of exp(-i H dt) (Sec. TDSLDA, "Time evolution"). */
+static void taylor4(const or_params *p, const double *W, const double complex *D,
+                    const double complex *psi, double dt, double complex *out,
+                    double complex *term, double complex *hterm, long ns) {
+  memcpy(out, psi, sizeof(double complex) * ns);
+  memcpy(term, psi, sizeof(double complex) * ns);
+  for (int j = 1; j <= 4; ++j) {
+    or_apply_h(p, W, D, term, hterm);
+    double complex f = -I * dt / (double)j;
+    for (long i = 0; i < ns; ++i) {
+      term[i] = f * hterm[i];
+      out[i] += term[i];
+    }
+  }
+}
+
+void or_series_step(const or_params *p, const double complex *psi, double t,
+                    double dt, double complex *psi_out) {
+  long nt = (long)p->nx * p->ny * p->nz;
+  long ns = nt * 2 * (long)p->n_qp;
+  double complex *pre = (double complex *)malloc(sizeof(double complex) * ns);
+  double complex *term = (double complex *)malloc(sizeof(double complex) * ns);
+  double complex *hterm = (double complex *)malloc(sizeof(double complex) * ns);
+  double *n0 = (double *)malloc(sizeof(double) * nt);
+  double *n1 = (double *)malloc(sizeof(double) * nt);
+  double *W = (double *)malloc(sizeof(double) * nt);
+  double complex *nu0 = (double complex *)malloc(sizeof(double complex) * nt);
+  double complex *nu1 = (double complex *)malloc(sizeof(double complex) * nt);
+  double complex *D = (double complex *)malloc(sizeof(double complex) * nt);
+  /* 1. predictor with H(t) built from the densities of psi(t) */
+  or_densities(p, psi, n0, nu0);
+  or_potentials(p, n0, nu0, t, W, D);
+  taylor4(p, W, D, psi, dt, pre, term, hterm, ns);
+  /* 2. corrector densities n_cor = (n_pre + n(t)) / 2 */
+  or_densities(p, pre, n1, nu1);
+  for (long r = 0; r < nt; ++r) {
+    n1[r] = 0.5 * (n1[r] + n0[r]);
+    nu1[r] = 0.5 * (nu1[r] + nu0[r]);
+  }
+  or_potentials(p, n1, nu1, t + 0.5 * dt, W, D);
+  /* 3. psi(t + dt) = exp(-i H_cor dt) psi(t) */
+  taylor4(p, W, D, psi, dt, psi_out, term, hterm, ns);
+  free(pre); free(term); free(hterm); free(n0); free(n1); free(W);
+  free(nu0); free(nu1); free(D);
+}
+
+int or_set_state(or_solver *s, const double complex *psi, double t0, double dt) {
+  if (!(dt == dt) || dt == 0.0) return 1;
+  s->dt = dt;
+  /* y_0 .. y_3 by the series start; y'_k = f(t_k, y_k) for k = 0..3 */
+  double complex *ys[4];
+  ys[0] = (double complex *)malloc(sizeof(double complex) * s->ns);
+  ys[1] = (double complex *)malloc(sizeof(double complex) * s->ns);
+  ys[2] = s->y1;
+  ys[3] = s->y0;
+  memcpy(ys[0], psi, sizeof(double complex) * s->ns);
+  double complex *dk[4] = {s->d[3], s->d[2], s->d[1], s->d[0]};
+  for (int k = 0; k < 3; ++k) {
+    double tk = t0 + k * dt;
+    or_rhs(&s->p, ys[k], tk, dk[k]);
+    or_series_step(&s->p, ys[k], tk, dt, ys[k + 1]);
+  }
+  or_rhs(&s->p, ys[3], t0 + 3 * dt, dk[3]);
+  memset(s->pc, 0, sizeof(double complex) * s->ns);
+  s->t = t0 + 3 * dt;
+  free(ys[0]); free(ys[1]);
+  s->ready = 1;
+  return 0;
+}
+
+/* Eq. p: p_{n+1} = (y_n + y_{n-1})/2
+ *               + h/48 (119 y'_n - 99 y'_{n-1} + 69 y'_{n-2} - 17 y'_{n-3}) */
+void or_abm_predictor(long ns, double h, const double complex *yn, const double complex *ynm1,
+                      const double complex *d0, const double complex *d1,
+                      const double complex *d2, const double complex *d3, double complex *p) {
+  for (long i = 0; i < ns; ++i)
+    p[i] = 0.5 * (yn[i] + ynm1[i]) +
+           h / 48.0 * (119.0 * d0[i] - 99.0 * d1[i] + 69.0 * d2[i] - 17.0 * d3[i]);
+}
+
+/* Eq. m: m_{n+1} = p_{n+1} - (161/170) (p_n - c_n) */
+void or_abm_modifier(long ns, const double complex *p, const double complex *pc,
+                     double complex *m) {
+  for (long i = 0; i < ns; ++i) m[i] = p[i] - 161.0 / 170.0 * pc[i];
+}
+
+/* Eq. c: c_{n+1} = (y_n + y_{n-1})/2 + h/48 (17 m'_{n+1} + 51 y'_n + 3 y'_{n-1} + y'_{n-2}) */
+void or_abm_corrector(long ns, double h, const double complex *yn, const double complex *ynm1,
+                      const double complex *mp, const double complex *d0,
+                      const double complex *d1, const double complex *d2, double complex *c) {
+  for (long i = 0; i < ns; ++i)
+    c[i] = 0.5 * (yn[i] + ynm1[i]) + h / 48.0 * (17.0 * mp[i] + 51.0 * d0[i] + 3.0 * d1[i] + d2[i]);
+}
+
+/* Eq. y: y_{n+1} = c_{n+1} + (9/170) (p_{n+1} - c_{n+1}); also returns p_{n+1} - c_{n+1}.
+ * y may alias neither p nor c. */
+void or_abm_final(long ns, const double complex *p, const double complex *c, double complex *y,
+                  double complex *pc) {
+  for (long i = 0; i < ns; ++i) {
+    double complex pmc = p[i] - c[i];
+    y[i] = c[i] + 9.0 / 170.0 * pmc;
+    pc[i] = pmc;
+  }
+}
+
+/* One step of Eqs. p, m, c, y with f(t, y) = -i H[y](t) y. */
+static void abm_step(or_solver *s) {
+  long ns = s->ns;
+  double h = s->dt;
+  double tn1 = s->t + h;
+  double complex *yn = s->y0, *ynm1 = s->y1;
+  double complex *dn = s->d[0], *dn1 = s->d[1], *dn2 = s->d[2], *dn3 = s->d[3];
+  or_abm_predictor(ns, h, yn, ynm1, dn, dn1, dn2, dn3, s->pr);
+  or_abm_modifier(ns, s->pr, s->pc, s->m);
+  or_rhs(&s->p, s->m, tn1, s->mp); /* m'_{n+1} = f(t_{n+1}, m_{n+1}) */
+  or_abm_corrector(ns, h, yn, ynm1, s->mp, dn, dn1, dn2, s->c);
+  /* y_{n+1} is stored in the y_{n-1} slot, which the corrector no longer needs */
+  or_abm_final(ns, s->pr, s->c, ynm1, s->pc);
+  /* y'_{n+1} = f(t_{n+1}, y_{n+1}) into the y'_{n-3} slot, then rotate */
+  or_rhs(&s->p, ynm1, tn1, dn3);
+  s->y0 = ynm1;
+  s->y1 = yn;
+  s->d[0] = dn3;
+  s->d[1] = dn;
+  s->d[2] = dn1;
+  s->d[3] = dn2;
+  s->t = tn1;
+}
+
+int or_step(or_solver *s, int n_steps) {
+  if (!s->ready) return 1;
+  for (int k = 0; k < n_steps; ++k) abm_step(s);
+  return 0;
+}
+
+void or_get_state(const or_solver *s, double complex *psi_out) {
+  memcpy(psi_out, s->y0, sizeof(double complex) * s->ns);
+}
+
+double or_time(const or_solver *s) { return s->t; }
+
+void or_get_densities(const or_solver *s, double *n, double complex *nu) {
+  or_densities(&s->p, s->y0, n, nu);
+}
+
+void or_energy_of(const or_params *p, const double complex *psi, double t,
+                  double *E, double *N) {
+  long nt = (long)p->nx * p->ny * p->nz;
+  double a3 = p->a * p->a * p->a;
+  double *n = (double *)malloc(sizeof(double) * nt);
+  double complex *nu = (double complex *)malloc(sizeof(double complex) * nt);
+  or_densities(p, psi, n, nu);
+  /* kinetic: (alpha/2) tau with tau = 2 sum_k |grad v_k|^2; by parts on the
+   * periodic lattice a^3 sum_r (alpha/2)|grad v|^2 = a^3 sum_r Re[v^* T v] */
+  double *ekq = (double *)calloc(p->n_qp, sizeof(double));
+#pragma omp parallel
+  {
+    double complex *tv = (double complex *)malloc(sizeof(double complex) * nt);
+#pragma omp for schedule(dynamic)
+    for (int q = 0; q < p->n_qp; ++q) {
+      const double complex *v = psi + ((long)q * 2 + 1) * nt;
+      or_kinetic(p, v, tv);
+      double s = 0, c = 0;
+      for (long r = 0; r < nt; ++r) neumaier_add(&s, &c, creal(conj(v[r]) * tv[r]));
+      ekq[q] = 2.0 * a3 * (s + c);
+    }
+    free(tv);
+  }
+  double es = 0, ec = 0, ns_ = 0, nc = 0;
+  for (int q = 0; q < p->n_qp; ++q) neumaier_add(&es, &ec, ekq[q]);
+  double cint = 0.3 * p->beta * pow(3.0 * OR_PI * OR_PI, 2.0 / 3.0);
+  for (int z = 0; z < p->nz; ++z)
+    for (int y = 0; y < p->ny; ++y)
+      for (int x = 0; x < p->nx; ++x) {
+        long r = ((long)z * p->ny + y) * p->nx + x;
+        double nr = n[r];
+        /* Eq. pairing: E_pair = +g |nu|^2 (with Delta = -g nu, Eq. pairingfield) */
+        double e = cint * pow(nr, 5.0 / 3.0) + p->g * (creal(nu[r]) * creal(nu[r]) + cimag(nu[r]) * cimag(nu[r])) +
+                   or_vext(p, x, y, z, t) * nr;
+        neumaier_add(&es, &ec, a3 * e);
+        neumaier_add(&ns_, &nc, a3 * nr);
+      }
+  *E = es + ec;
+  *N = ns_ + nc;
+  free(n); free(nu); free(ekq);
+}
+
+void or_energy(const or_solver *s, double *E, double *N) {
+  or_energy_of(&s->p, s->y0, s->t, E, N);
+}

@@ -1,0 +1,137 @@
+/*
+ * lise.h -- C ABI of the B300 two-component TDSLDA step (liblise.so).
+ *
+ * Method: arXiv:2009.00745 ("LISE"), reduced to one (u, v) pair per
+ * quasiparticle state for spin-symmetric, spin-singlet pairing:
+ *   i d/dt (u, v) = [[h, Delta], [Delta*, -h*]] (u, v)                 (Eq. tdslda)
+ *   h = -(alpha/2) lap + beta (3 pi^2 n)^(2/3) / 2 - mu + V_ext(r, t),
+ *   Delta = -g nu                                                  (Eq. pairingfield)
+ *   n = 2 sum_k |v_k|^2,  nu = sum_k u_k v_k^*                    (Eqs. rho_t, nu_t)
+ * on a periodic cubic lattice with spacing a (Sec. "Discretization"); the
+ * Laplacian is spectral, D^(2) = F^-1[(ik)^2 F] with the Nyquist mode kept.
+ * Time stepping: three steps of the order-4 series expansion with averaged
+ * predictor/corrector densities (Sec. "TDSLDA / Time evolution"), then the
+ * 5th-order Adams-Bashforth-Milne predictor-modifier-corrector of Eqs. p, m,
+ * c, y, with 2 right-hand-side evaluations per step.  hbar = m = 1.
+ *
+ * Units and conventions
+ *   - Lattice: nx = ny = nz = N with N in {8, 12, 16, 20, 24, 32, 40, 48, 64};
+ *     site index r = (z * N + y) * N + x, x fastest.  V_ext's drive term uses
+ *     z_c = (z - N/2) a.
+ *   - State layout (host and device): psi[q][c][z][y][x] as interleaved
+ *     (re, im) doubles, q < n_qp, c = 0 for u and c = 1 for v; that is
+ *     n_qp * 2 * N^3 complex numbers, 16 bytes each.
+ *   - Densities: n[r] (double), nu[r] as interleaved (re, im) doubles.
+ *
+ * Ownership and threading
+ *   - The caller owns every host buffer passed in; the library reads or writes
+ *     it only during the call (host copies complete before the call returns).
+ *   - The context owns all device memory it allocates (lise_footprint_bytes
+ *     tells how much); it allocates only in lise_create.
+ *   - A context is not thread-safe: do not use one context from two threads at
+ *     once.  Different contexts are independent.
+ *   - Work is enqueued on the context's stream.  lise_step returns after
+ *     enqueueing; errors raised by device work are sticky and reported by the
+ *     next call that synchronises (lise_sync, lise_get_state, lise_densities,
+ *     lise_energy, lise_rhs) or by lise_step itself once detected.
+ *
+ * Status codes: every function returning int returns one of LISE_* below.
+ */
+#ifndef LISE_H
+#define LISE_H
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LISE_OK 0
+#define LISE_EINVAL 1     /* invalid argument (NULL pointer, unsupported lattice, dt mismatch, ...) */
+#define LISE_ENOMEM 2     /* footprint above hbm_budget_bytes, or device allocation failed */
+#define LISE_ECUDA 3      /* a CUDA runtime call or kernel launch failed */
+#define LISE_ENONFINITE 4 /* a density or the input state is NaN or infinite */
+#define LISE_ETIMEOUT 5   /* reserved: a bounded device wait ran out (no such wait in this path) */
+#define LISE_ESTATE 6     /* call out of order (e.g. lise_step before lise_set_state) */
+
+#define LISE_FP64 0       /* FFTs, H psi, ABM history, densities: all in FP64 */
+#define LISE_MIXED 1      /* FFTs and H psi in complex64 (FP32 accumulation); ABM history,
+                             state update and densities in FP64 */
+
+typedef struct lise_ctx lise_ctx;
+
+typedef struct {
+  int nx, ny, nz;           /* lattice; must be equal (cubic), see above */
+  double dx;                /* lattice constant a > 0 */
+  int n_qp;                 /* number of quasiparticle states, >= 1 */
+  double alpha;             /* h contains -(alpha/2) lap */
+  double beta;              /* U(n) = beta (3 pi^2 n)^(2/3) / 2 */
+  double mu;                /* chemical potential (constant) */
+  double g;                 /* Delta = -g nu */
+  const double *v_static;   /* host array of N^3 doubles (static V_ext), or NULL; copied */
+  double drive_A;           /* V_ext(r, t) += drive_A sin(drive_Omega t) z_c */
+  double drive_Omega;
+  int precision;            /* LISE_FP64 or LISE_MIXED */
+  int device;               /* CUDA device ordinal */
+  size_t hbm_budget_bytes;  /* 0 = no limit; otherwise lise_create fails with LISE_ENOMEM
+                               (allocating nothing) if the footprint exceeds it */
+  void *stream;             /* cudaStream_t to enqueue on, or NULL for a stream owned by the context */
+} lise_params;
+
+/* Device bytes lise_create would allocate for these parameters (0 if invalid). */
+size_t lise_footprint_bytes(const lise_params *p);
+
+/* Validates p, allocates the device state and copies v_static.
+ * Errors: LISE_EINVAL (bad parameters), LISE_ENOMEM, LISE_ECUDA. */
+int lise_create(const lise_params *p, lise_ctx **out);
+
+/* Sets y_0 = psi (host buffer, layout above) at time t0 and runs the start
+ * procedure: 3 series-expansion steps of size dt (8 H psi each), storing
+ * y'_k = f(t_k, y_k) for k = 0..3, so the context is at t0 + 3 dt and ready for
+ * ABM steps.  dt may be negative (backward evolution) but not 0.
+ * Synchronises.  Errors: LISE_EINVAL, LISE_ENONFINITE (psi has NaN/Inf), LISE_ECUDA. */
+int lise_set_state(lise_ctx *c, const double *psi, double t0, double dt);
+/* Same with psi a device pointer (same layout) on the context's device. */
+int lise_set_state_device(lise_ctx *c, const double *psi_dev, double t0, double dt);
+
+/* Enqueues n_steps >= 0 ABM steps (Eqs. p, m, c, y).  dt must equal the
+ * set_state dt (the stored history is only valid for that step), else
+ * LISE_EINVAL.  Errors: LISE_ESTATE before set_state, LISE_ECUDA. */
+int lise_step(lise_ctx *c, int n_steps, double dt);
+
+/* Copies the current state y_n to a host (or device) buffer.  Synchronises. */
+int lise_get_state(lise_ctx *c, double *psi_out);
+int lise_get_state_device(lise_ctx *c, double *psi_dev_out);
+
+/* Current time t_n. */
+int lise_get_time(lise_ctx *c, double *t);
+
+/* Densities of the current state: n_out[N^3], nu_out[2 N^3] (host).  Synchronises. */
+int lise_densities(lise_ctx *c, double *n_out, double *nu_out);
+
+/* Energy and particle number of the current state at the current time:
+ *   E = a^3 sum_r [(alpha/2) tau + (3/10) beta (3 pi^2)^(2/3) n^(5/3) + g |nu|^2 + V_ext n],
+ *   tau = 2 sum_k |grad v_k|^2 (spectral, same Laplacian as the step; Eq. pairing
+ *   gives the + g |nu|^2 term), N = a^3 sum_r n.  FP64 with compensated sums.
+ * Synchronises. */
+int lise_energy(lise_ctx *c, double *E, double *N);
+
+/* One right-hand side f(t, psi) = -i H[psi](t) psi for an arbitrary host state
+ * (same layout), with the potentials built from psi's own densities; written
+ * to dpsi_out (host).  Uses the context's scratch arrays: it invalidates the
+ * ABM history, so lise_set_state must be called again before lise_step.
+ * Synchronises. */
+int lise_rhs(lise_ctx *c, const double *psi, double t, double *dpsi_out);
+
+/* Waits for enqueued work and reports sticky errors. */
+int lise_sync(lise_ctx *c);
+
+/* Static description of a status code. */
+const char *lise_strerror(int status);
+
+/* Frees the context and its device memory (synchronises first).  NULL is a no-op. */
+void lise_destroy(lise_ctx *c);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,640 @@
+// lise_api.cu -- host side of the C ABI declared in include/lise.h.
+//
+// A context owns the ABM history on the device:
+//   y_n, y_{n-1}             two state slots (swapped every step)
+//   y'_n .. y'_{n-3}         a ring of four derivative slots
+//   p_{n+1}, m_{n+1}, p-c    predictor, modifier, and p_n - c_n of Eq. m
+//   T_xy scratch             the in-plane kinetic part of the current operand
+// plus per-group density partial sums, reduced densities and the potentials
+// W = U(n) - mu + V_ext and Delta of the operand of the next right-hand side.
+//
+// One ABM step (Eqs. p, m, c, y) is 6 launches:
+//   planes(m), pencils[CORRECT]        m' = -iHm; c, y_{n+1}, p - c; densities of y_{n+1}
+//   reduce                             W, Delta of y_{n+1} at t_{n+1}
+//   planes(y_{n+1}), pencils[DERIV_PREDICT]
+//                                      y'_{n+1}; p_{n+2}, m_{n+2}; densities of m_{n+2}
+//   reduce                             W, Delta of m_{n+2} at t_{n+2}
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/lise.h"
+#include "lise_kernels.cuh"
+
+using namespace lise;
+
+struct lise_ctx {
+  lise_params p;
+  int N = 0;
+  long nxyz = 0;
+  long ns = 0;  // complex elements per state array
+  int mixed = 0;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int qg = 0, n_groups = 0;
+  double2* slot[2] = {nullptr, nullptr};
+  int y0_slot = 0;                 // slot holding y_n
+  double2* D[4] = {nullptr, nullptr, nullptr, nullptr};  // D[k] = y'_{n-k}
+  double2 *P = nullptr, *M = nullptr, *PC = nullptr;
+  void* TXY = nullptr;
+  double *part_n = nullptr, *part_nr = nullptr, *part_ni = nullptr;
+  double* dn[2] = {nullptr, nullptr};
+  double2* dnu[2] = {nullptr, nullptr};
+  double* W = nullptr;
+  double2* Dl = nullptr;
+  double* v_static = nullptr;
+  void *tw = nullptr, *hxy = nullptr, *hz = nullptr;
+  double* e_site = nullptr;
+  int* err = nullptr;
+  double t = 0.0, dt = 0.0;
+  int ready = 0;
+  int sticky = LISE_OK;
+  double* host_e = nullptr;
+};
+
+namespace {
+
+constexpr long double PI_L = 3.141592653589793238462643383279502884L;
+
+int check_params(const lise_params* p) {
+  if (!p) return LISE_EINVAL;
+  if (p->nx != p->ny || p->ny != p->nz) return LISE_EINVAL;
+  if (!supported_n(p->nx)) return LISE_EINVAL;
+  if (!(p->dx > 0.0) || p->n_qp < 1) return LISE_EINVAL;
+  if (p->precision != LISE_FP64 && p->precision != LISE_MIXED) return LISE_EINVAL;
+  if (!std::isfinite(p->alpha) || !std::isfinite(p->beta) || !std::isfinite(p->mu) ||
+      !std::isfinite(p->g) || !std::isfinite(p->drive_A) || !std::isfinite(p->drive_Omega))
+    return LISE_EINVAL;
+  return LISE_OK;
+}
+
+void choose_groups(int N, int n_qp, int* qg, int* n_groups) {
+  const int tiles = (N / pencil_tx(N)) * N;
+  int q = 64;
+  while (q > 4 && (long)tiles * ((n_qp + q - 1) / q) < 2048) q /= 2;
+  if (q > n_qp) q = n_qp;
+  *qg = q;
+  *n_groups = (n_qp + q - 1) / q;
+}
+
+struct Footprint {
+  size_t state, txy, partials, small, total;
+};
+
+Footprint footprint(const lise_params* p) {
+  Footprint f{};
+  const long N = p->nx;
+  const long nxyz = N * N * N;
+  const long ns = (long)p->n_qp * 2 * nxyz;
+  int qg, ng;
+  choose_groups((int)N, p->n_qp, &qg, &ng);
+  f.state = 9 * (size_t)ns * sizeof(double2);  // 2 y slots, 4 y', P, M, P-C
+  f.txy = (size_t)ns * (p->precision == LISE_MIXED ? sizeof(float2) : sizeof(double2));
+  f.partials = 3 * (size_t)ng * nxyz * sizeof(double);
+  f.small = (size_t)nxyz * (2 * sizeof(double) + 2 * sizeof(double2) + sizeof(double) + sizeof(double2) +
+                            sizeof(double) + 2 * sizeof(double)) +
+            3 * (size_t)N * sizeof(double2) + 256;
+  f.total = f.state + f.txy + f.partials + f.small;
+  return f;
+}
+
+double drive_at(const lise_ctx* c, double t) {
+  return c->p.drive_A == 0.0 ? 0.0 : c->p.drive_A * std::sin(c->p.drive_Omega * t);
+}
+
+int cu(cudaError_t e) { return e == cudaSuccess ? LISE_OK : LISE_ECUDA; }
+
+#define TRY(x)                  \
+  do {                          \
+    int rc__ = (x);             \
+    if (rc__ != LISE_OK) {      \
+      return rc__;              \
+    }                           \
+  } while (0)
+
+PencilArgs pencil_base(const lise_ctx* c) {
+  PencilArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.txy = c->TXY;
+  a.W = c->W;
+  a.D = c->Dl;
+  a.tw = c->tw;
+  a.hz = c->hz;
+  a.n_qp = c->p.n_qp;
+  a.qg = c->qg;
+  a.part_n = c->part_n;
+  a.part_nr = c->part_nr;
+  a.part_ni = c->part_ni;
+  return a;
+}
+
+int run_planes(lise_ctx* c, const double2* x) {
+  PlanesArgs a;
+  a.x = x;
+  a.txy = c->TXY;
+  a.tw = c->tw;
+  a.hxy = c->hxy;
+  a.n_planes = (long)c->p.n_qp * 2 * c->N;
+  return launch_planes(c->N, c->mixed, a, c->stream) ? LISE_ECUDA : LISE_OK;
+}
+
+int run_pencils(lise_ctx* c, int mode, const PencilArgs& a) {
+  return launch_pencils(c->N, c->mixed, mode, a, c->stream) ? LISE_ECUDA : LISE_OK;
+}
+
+// Reduce the density partials; optionally average with (avg_n, avg_nu); write
+// the densities to slot `dslot` and, if potentials is true, W and Delta at t.
+int run_reduce(lise_ctx* c, int dslot, const double* avg_n, const double2* avg_nu, bool potentials, double t) {
+  ReduceArgs r;
+  r.part_n = c->part_n;
+  r.part_nr = c->part_nr;
+  r.part_ni = c->part_ni;
+  r.n_groups = c->n_groups;
+  r.nxyz = c->nxyz;
+  r.N = c->N;
+  r.a = c->p.dx;
+  r.n_out = c->dn[dslot];
+  r.nu_out = c->dnu[dslot];
+  r.avg_n = avg_n;
+  r.avg_nu = avg_nu;
+  r.W = potentials ? c->W : nullptr;
+  r.D = potentials ? c->Dl : nullptr;
+  r.v_static = c->v_static;
+  r.drive = drive_at(c, t);
+  r.beta = c->p.beta;
+  r.mu = c->p.mu;
+  r.g = c->p.g;
+  r.err = c->err;
+  return launch_reduce(r, c->stream) ? LISE_ECUDA : LISE_OK;
+}
+
+int run_density(lise_ctx* c, const double2* src) {
+  PointwiseArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.src = src;
+  a.part_n = c->part_n;
+  a.part_nr = c->part_nr;
+  a.part_ni = c->part_ni;
+  a.n_qp = c->p.n_qp;
+  a.qg = c->qg;
+  a.nxyz = c->nxyz;
+  return launch_density(a, c->stream) ? LISE_ECUDA : LISE_OK;
+}
+
+double2 cx(double re, double im) { return make_double2(re, im); }
+
+// psi_out = sum_{j=0}^{4} (-i dt H)^j / j! psi_in with the current potentials
+// (order-4 series of exp(-i H dt)).  If dslot != nullptr, also stores
+// -i H psi_in there.  The last term's kernel accumulates the densities of
+// psi_out into the partials.  term is scratch (the P array).
+int taylor4(lise_ctx* c, const double2* psi_in, double2* psi_out, double2* dslot, double dt) {
+  TRY(run_planes(c, psi_in));
+  PencilArgs a = pencil_base(c);
+  a.x = psi_in;
+  a.out = c->P;
+  a.acc = psi_out;
+  a.dslot = dslot;
+  a.coef = cx(0.0, -dt);
+  TRY(run_pencils(c, M_TAYLOR_FIRST, a));
+  for (int j = 2; j <= 4; ++j) {
+    TRY(run_planes(c, c->P));
+    PencilArgs b = pencil_base(c);
+    b.x = c->P;
+    b.out = c->P;
+    b.acc = psi_out;
+    b.coef = cx(0.0, -dt / j);
+    b.dens = (j == 4);
+    TRY(run_pencils(c, M_TAYLOR, b));
+  }
+  return LISE_OK;
+}
+
+int fetch_err(lise_ctx* c) {
+  if (c->sticky) return c->sticky;
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    c->sticky = LISE_ECUDA;
+    return c->sticky;
+  }
+  if (h) {
+    c->sticky = LISE_ENONFINITE;
+    return c->sticky;
+  }
+  return LISE_OK;
+}
+
+int start_procedure(lise_ctx* c, double t0, double dt) {
+  // y_0 is in slot[0]; densities and potentials of y_0 at t0 into dn[0]
+  double2* cur = c->slot[0];
+  double2* nxt = c->slot[1];
+  TRY(run_density(c, cur));
+  TRY(run_reduce(c, 0, nullptr, nullptr, true, t0));
+  for (int s = 0; s < 3; ++s) {
+    const double ts = t0 + s * dt;
+    // predictor with H(t_s): psi_pre into M; y'_s = -i H(t_s) y_s into D[3 - s]
+    TRY(taylor4(c, cur, c->M, c->D[3 - s], dt));
+    // corrector densities (n_pre + n(t_s)) / 2, potentials at t_s + dt/2
+    TRY(run_reduce(c, 1, c->dn[0], c->dnu[0], true, ts + 0.5 * dt));
+    // psi(t_s + dt) = exp(-i H_cor dt) psi(t_s), densities into dn[0] at t_{s+1}
+    TRY(taylor4(c, cur, nxt, nullptr, dt));
+    TRY(run_reduce(c, 0, nullptr, nullptr, true, ts + dt));
+    double2* tmp = cur;
+    cur = nxt;
+    nxt = tmp;
+  }
+  // cur = y_3, nxt = y_2; y'_3 = f(t_3, y_3) into D[0]
+  TRY(run_planes(c, cur));
+  PencilArgs a = pencil_base(c);
+  a.x = cur;
+  a.out = c->D[0];
+  TRY(run_pencils(c, M_RHS, a));
+  c->y0_slot = (cur == c->slot[0]) ? 0 : 1;
+  // p_3 - c_3 := 0; predictor and modifier of the first ABM step
+  TRY(cu(cudaMemsetAsync(c->PC, 0, (size_t)c->ns * sizeof(double2), c->stream)));
+  PointwiseArgs w;
+  std::memset(&w, 0, sizeof(w));
+  w.y0 = c->slot[c->y0_slot];
+  w.y1 = c->slot[1 - c->y0_slot];
+  w.d0 = c->D[0];
+  w.d1 = c->D[1];
+  w.d2 = c->D[2];
+  w.d3 = c->D[3];
+  w.pc = c->PC;
+  w.p = c->P;
+  w.m = c->M;
+  w.h = dt;
+  w.part_n = c->part_n;
+  w.part_nr = c->part_nr;
+  w.part_ni = c->part_ni;
+  w.n_qp = c->p.n_qp;
+  w.qg = c->qg;
+  w.nxyz = c->nxyz;
+  TRY(launch_predict(w, c->stream) ? LISE_ECUDA : LISE_OK);
+  const double t3 = t0 + 3 * dt;
+  TRY(run_reduce(c, 1, nullptr, nullptr, true, t3 + dt));
+  c->t = t3;
+  c->dt = dt;
+  return LISE_OK;
+}
+
+int abm_step(lise_ctx* c) {
+  const double h = c->dt;
+  const double t1 = c->t + h;
+  double2* yn = c->slot[c->y0_slot];
+  double2* ynm1 = c->slot[1 - c->y0_slot];
+  // RHS #1 on m_{n+1}: Eq. c, Eq. y; y_{n+1} replaces y_{n-1}
+  TRY(run_planes(c, c->M));
+  PencilArgs a = pencil_base(c);
+  a.x = c->M;
+  a.h = h;
+  a.y0 = yn;
+  a.y1 = ynm1;
+  a.d0 = c->D[0];
+  a.d1 = c->D[1];
+  a.d2 = c->D[2];
+  a.p = c->P;
+  a.pc = c->PC;
+  a.ynew = ynm1;
+  a.dens = 1;
+  TRY(run_pencils(c, M_CORRECT, a));
+  TRY(run_reduce(c, 1, nullptr, nullptr, true, t1));
+  // RHS #2 on y_{n+1}: y'_{n+1} into the y'_{n-3} slot, then Eq. p and Eq. m of step n+2
+  TRY(run_planes(c, ynm1));
+  PencilArgs b = pencil_base(c);
+  b.x = ynm1;
+  b.h = h;
+  b.y0 = yn;
+  b.d0 = c->D[0];
+  b.d1 = c->D[1];
+  b.d2 = c->D[2];
+  b.dslot = c->D[3];
+  b.pc = c->PC;
+  b.p = c->P;
+  b.m = c->M;
+  b.dens = 1;
+  TRY(run_pencils(c, M_DERIV_PREDICT, b));
+  TRY(run_reduce(c, 1, nullptr, nullptr, true, t1 + h));
+  // rotate the history
+  c->y0_slot = 1 - c->y0_slot;
+  double2* d3 = c->D[3];
+  c->D[3] = c->D[2];
+  c->D[2] = c->D[1];
+  c->D[1] = c->D[0];
+  c->D[0] = d3;
+  c->t = t1;
+  return LISE_OK;
+}
+
+void free_ctx(lise_ctx* c) {
+  void* ptrs[] = {c->slot[0], c->slot[1], c->D[0], c->D[1], c->D[2], c->D[3], c->P, c->M, c->PC, c->TXY,
+                  c->part_n, c->part_nr, c->part_ni, c->dn[0], c->dn[1], c->dnu[0], c->dnu[1], c->W,
+                  c->Dl, c->v_static, c->tw, c->hxy, c->hz, c->e_site, c->err};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  std::free(c->host_e);
+}
+
+template <typename R>
+void fill_tables(int N, double a, double alpha, R* tw, R* hxy, R* hz) {
+  // twiddles tw[j2 * N1 + k1] = exp(-2 pi i (j2 k1 mod N) / N); the four-step
+  // plan reads entries with j2 < N2, k1 < N1 only.
+  int N1 = 0;
+  switch (N) {
+    case 8: N1 = 2; break;
+    case 12: case 16: case 20: case 24: case 32: N1 = 4; break;
+    default: N1 = 8; break;
+  }
+  const int N2 = N / N1;
+  for (int j2 = 0; j2 < N2; ++j2)
+    for (int k1 = 0; k1 < N1; ++k1) {
+      long e = ((long)j2 * k1) % N;
+      long double ang = -2.0L * PI_L * (long double)e / (long double)N;
+      tw[2 * (j2 * N1 + k1)] = (R)cosl(ang);
+      tw[2 * (j2 * N1 + k1) + 1] = (R)sinl(ang);
+    }
+  const long double L = (long double)N * a;
+  for (int k = 0; k < N; ++k) {
+    // Sec. "Discretization": k = 2 pi n / L over n = -N/2 .. N/2-1 (index n mod N)
+    long double kk = 2.0L * PI_L * (long double)(k < N / 2 ? k : k - N) / L;
+    long double f = 0.5L * alpha * kk * kk;
+    hxy[k] = (R)(f / ((long double)N * N));
+    hz[k] = (R)(f / (long double)N);
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t lise_footprint_bytes(const lise_params* p) {
+  if (check_params(p) != LISE_OK) return 0;
+  return footprint(p).total;
+}
+
+const char* lise_strerror(int s) {
+  switch (s) {
+    case LISE_OK: return "ok";
+    case LISE_EINVAL: return "invalid argument";
+    case LISE_ENOMEM: return "device memory budget exceeded or allocation failed";
+    case LISE_ECUDA: return "CUDA error";
+    case LISE_ENONFINITE: return "non-finite state or density";
+    case LISE_ETIMEOUT: return "bounded device wait timed out";
+    case LISE_ESTATE: return "call out of order (no state set)";
+    default: return "unknown status";
+  }
+}
+
+int lise_create(const lise_params* p, lise_ctx** out) {
+  if (!out) return LISE_EINVAL;
+  *out = nullptr;
+  TRY(check_params(p));
+  Footprint f = footprint(p);
+  if (p->hbm_budget_bytes && f.total > p->hbm_budget_bytes) return LISE_ENOMEM;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || p->device < 0 || p->device >= ndev) return LISE_EINVAL;
+  if (cudaSetDevice(p->device) != cudaSuccess) return LISE_ECUDA;
+  lise_ctx* c = new (std::nothrow) lise_ctx();
+  if (!c) return LISE_ENOMEM;
+  c->p = *p;
+  c->p.v_static = nullptr;
+  c->N = p->nx;
+  c->nxyz = (long)c->N * c->N * c->N;
+  c->ns = (long)p->n_qp * 2 * c->nxyz;
+  c->mixed = p->precision == LISE_MIXED;
+  c->device = p->device;
+  choose_groups(c->N, p->n_qp, &c->qg, &c->n_groups);
+  int rc = LISE_OK;
+  if (p->stream) {
+    c->stream = (cudaStream_t)p->stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) rc = LISE_ECUDA;
+    c->own_stream = true;
+  }
+  const size_t sb = (size_t)c->ns * sizeof(double2);
+  auto alloc = [&](void** q, size_t bytes) {
+    if (rc != LISE_OK) return;
+    cudaError_t e = cudaMalloc(q, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      rc = (e == cudaErrorMemoryAllocation) ? LISE_ENOMEM : LISE_ECUDA;
+    }
+  };
+  alloc((void**)&c->slot[0], sb);
+  alloc((void**)&c->slot[1], sb);
+  for (int k = 0; k < 4; ++k) alloc((void**)&c->D[k], sb);
+  alloc((void**)&c->P, sb);
+  alloc((void**)&c->M, sb);
+  alloc((void**)&c->PC, sb);
+  alloc(&c->TXY, (size_t)c->ns * (c->mixed ? sizeof(float2) : sizeof(double2)));
+  const size_t pb = (size_t)c->n_groups * c->nxyz * sizeof(double);
+  alloc((void**)&c->part_n, pb);
+  alloc((void**)&c->part_nr, pb);
+  alloc((void**)&c->part_ni, pb);
+  for (int k = 0; k < 2; ++k) {
+    alloc((void**)&c->dn[k], c->nxyz * sizeof(double));
+    alloc((void**)&c->dnu[k], c->nxyz * sizeof(double2));
+  }
+  alloc((void**)&c->W, c->nxyz * sizeof(double));
+  alloc((void**)&c->Dl, c->nxyz * sizeof(double2));
+  if (p->v_static) alloc((void**)&c->v_static, c->nxyz * sizeof(double));
+  const size_t rs = c->mixed ? sizeof(float) : sizeof(double);
+  alloc(&c->tw, 2 * c->N * rs);
+  alloc(&c->hxy, c->N * rs);
+  alloc(&c->hz, c->N * rs);
+  alloc((void**)&c->e_site, 2 * c->nxyz * sizeof(double));
+  alloc((void**)&c->err, sizeof(int));
+  c->host_e = (double*)std::malloc(2 * c->nxyz * sizeof(double));
+  if (rc == LISE_OK && !c->host_e) rc = LISE_ENOMEM;
+  if (rc == LISE_OK) {
+    // tables
+    std::vector<char> tw(2 * c->N * rs), hxy(c->N * rs), hz(c->N * rs);
+    if (c->mixed)
+      fill_tables<float>(c->N, p->dx, p->alpha, (float*)tw.data(), (float*)hxy.data(), (float*)hz.data());
+    else
+      fill_tables<double>(c->N, p->dx, p->alpha, (double*)tw.data(), (double*)hxy.data(), (double*)hz.data());
+    rc = cu(cudaMemcpyAsync(c->tw, tw.data(), tw.size(), cudaMemcpyHostToDevice, c->stream));
+    if (rc == LISE_OK) rc = cu(cudaMemcpyAsync(c->hxy, hxy.data(), hxy.size(), cudaMemcpyHostToDevice, c->stream));
+    if (rc == LISE_OK) rc = cu(cudaMemcpyAsync(c->hz, hz.data(), hz.size(), cudaMemcpyHostToDevice, c->stream));
+    if (rc == LISE_OK && p->v_static)
+      rc = cu(cudaMemcpyAsync(c->v_static, p->v_static, c->nxyz * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    if (rc == LISE_OK) rc = cu(cudaMemsetAsync(c->err, 0, sizeof(int), c->stream));
+    if (rc == LISE_OK) rc = cu(cudaStreamSynchronize(c->stream));
+  }
+  if (rc != LISE_OK) {
+    free_ctx(c);
+    delete c;
+    return rc;
+  }
+  *out = c;
+  return LISE_OK;
+}
+
+static int set_state_common(lise_ctx* c, const double* psi, double t0, double dt, cudaMemcpyKind kind) {
+  if (!c || !psi || !(dt != 0.0) || !std::isfinite(dt) || !std::isfinite(t0)) return LISE_EINVAL;
+  if (c->sticky) return c->sticky;
+  if (cudaSetDevice(c->device) != cudaSuccess) return LISE_ECUDA;
+  c->ready = 0;
+  TRY(cu(cudaMemcpyAsync(c->slot[0], psi, (size_t)c->ns * sizeof(double2), kind, c->stream)));
+  TRY(launch_finite_check(c->slot[0], c->ns, c->err, c->stream) ? LISE_ECUDA : LISE_OK);
+  int h = 0;
+  TRY(cu(cudaMemcpyAsync(&h, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream)));
+  TRY(cu(cudaStreamSynchronize(c->stream)));
+  if (h) {
+    // reject the input; the context stays usable
+    TRY(cu(cudaMemsetAsync(c->err, 0, sizeof(int), c->stream)));
+    TRY(cu(cudaStreamSynchronize(c->stream)));
+    return LISE_ENONFINITE;
+  }
+  int rc = start_procedure(c, t0, dt);
+  if (rc != LISE_OK) {
+    c->sticky = rc;
+    return rc;
+  }
+  TRY(fetch_err(c));
+  c->ready = 1;
+  return LISE_OK;
+}
+
+int lise_set_state(lise_ctx* c, const double* psi, double t0, double dt) {
+  return set_state_common(c, psi, t0, dt, cudaMemcpyHostToDevice);
+}
+
+int lise_set_state_device(lise_ctx* c, const double* psi_dev, double t0, double dt) {
+  return set_state_common(c, psi_dev, t0, dt, cudaMemcpyDeviceToDevice);
+}
+
+int lise_step(lise_ctx* c, int n_steps, double dt) {
+  if (!c || n_steps < 0) return LISE_EINVAL;
+  if (c->sticky) return c->sticky;
+  if (!c->ready) return LISE_ESTATE;
+  if (dt != c->dt) return LISE_EINVAL;
+  if (cudaSetDevice(c->device) != cudaSuccess) return LISE_ECUDA;
+  for (int k = 0; k < n_steps; ++k) {
+    int rc = abm_step(c);
+    if (rc != LISE_OK) {
+      c->sticky = rc;
+      return rc;
+    }
+  }
+  return LISE_OK;
+}
+
+int lise_get_state(lise_ctx* c, double* psi_out) {
+  if (!c || !psi_out) return LISE_EINVAL;
+  if (!c->ready) return LISE_ESTATE;
+  TRY(fetch_err(c));
+  TRY(cu(cudaMemcpyAsync(psi_out, c->slot[c->y0_slot], (size_t)c->ns * sizeof(double2), cudaMemcpyDeviceToHost,
+                         c->stream)));
+  return cu(cudaStreamSynchronize(c->stream));
+}
+
+int lise_get_state_device(lise_ctx* c, double* psi_dev_out) {
+  if (!c || !psi_dev_out) return LISE_EINVAL;
+  if (!c->ready) return LISE_ESTATE;
+  TRY(fetch_err(c));
+  TRY(cu(cudaMemcpyAsync(psi_dev_out, c->slot[c->y0_slot], (size_t)c->ns * sizeof(double2),
+                         cudaMemcpyDeviceToDevice, c->stream)));
+  return cu(cudaStreamSynchronize(c->stream));
+}
+
+int lise_get_time(lise_ctx* c, double* t) {
+  if (!c || !t) return LISE_EINVAL;
+  *t = c->t;
+  return LISE_OK;
+}
+
+int lise_densities(lise_ctx* c, double* n_out, double* nu_out) {
+  if (!c || !n_out || !nu_out) return LISE_EINVAL;
+  if (!c->ready) return LISE_ESTATE;
+  if (c->sticky) return c->sticky;
+  TRY(run_density(c, c->slot[c->y0_slot]));
+  TRY(run_reduce(c, 0, nullptr, nullptr, false, c->t));
+  TRY(cu(cudaMemcpyAsync(n_out, c->dn[0], c->nxyz * sizeof(double), cudaMemcpyDeviceToHost, c->stream)));
+  TRY(cu(cudaMemcpyAsync(nu_out, c->dnu[0], c->nxyz * sizeof(double2), cudaMemcpyDeviceToHost, c->stream)));
+  TRY(cu(cudaStreamSynchronize(c->stream)));
+  return fetch_err(c);
+}
+
+int lise_energy(lise_ctx* c, double* E, double* Nout) {
+  if (!c || !E || !Nout) return LISE_EINVAL;
+  if (!c->ready) return LISE_ESTATE;
+  if (c->sticky) return c->sticky;
+  const double2* y = c->slot[c->y0_slot];
+  TRY(run_density(c, y));
+  TRY(run_reduce(c, 0, nullptr, nullptr, false, c->t));
+  TRY(run_planes(c, y));
+  PencilArgs a = pencil_base(c);
+  a.x = y;
+  a.dens = 1;
+  TRY(run_pencils(c, M_ENERGY, a));
+  TRY(launch_energy_sites(c->part_n, c->n_groups, c->dn[0], c->dnu[0], c->v_static, drive_at(c, c->t), c->p.beta,
+                          c->p.g, c->N, c->p.dx, c->e_site, c->stream)
+          ? LISE_ECUDA
+          : LISE_OK);
+  TRY(cu(cudaMemcpyAsync(c->host_e, c->e_site, 2 * c->nxyz * sizeof(double), cudaMemcpyDeviceToHost, c->stream)));
+  TRY(cu(cudaStreamSynchronize(c->stream)));
+  TRY(fetch_err(c));
+  // compensated (Neumaier) sums over sites
+  double se = 0, ce = 0, sn = 0, cn = 0;
+  for (long i = 0; i < c->nxyz; ++i) {
+    double x = c->host_e[i];
+    double t = se + x;
+    ce += (std::fabs(se) >= std::fabs(x)) ? (se - t) + x : (x - t) + se;
+    se = t;
+    x = c->host_e[c->nxyz + i];
+    t = sn + x;
+    cn += (std::fabs(sn) >= std::fabs(x)) ? (sn - t) + x : (x - t) + sn;
+    sn = t;
+  }
+  *E = se + ce;
+  *Nout = sn + cn;
+  return LISE_OK;
+}
+
+int lise_rhs(lise_ctx* c, const double* psi, double t, double* dpsi_out) {
+  if (!c || !psi || !dpsi_out || !std::isfinite(t)) return LISE_EINVAL;
+  if (c->sticky) return c->sticky;
+  if (cudaSetDevice(c->device) != cudaSuccess) return LISE_ECUDA;
+  c->ready = 0;
+  double2* x = c->slot[0];
+  TRY(cu(cudaMemcpyAsync(x, psi, (size_t)c->ns * sizeof(double2), cudaMemcpyHostToDevice, c->stream)));
+  TRY(run_density(c, x));
+  TRY(run_reduce(c, 0, nullptr, nullptr, true, t));
+  TRY(run_planes(c, x));
+  PencilArgs a = pencil_base(c);
+  a.x = x;
+  a.out = c->D[0];
+  TRY(run_pencils(c, M_RHS, a));
+  TRY(cu(cudaMemcpyAsync(dpsi_out, c->D[0], (size_t)c->ns * sizeof(double2), cudaMemcpyDeviceToHost, c->stream)));
+  TRY(cu(cudaStreamSynchronize(c->stream)));
+  return fetch_err(c);
+}
+
+int lise_sync(lise_ctx* c) {
+  if (!c) return LISE_EINVAL;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    c->sticky = LISE_ECUDA;
+    return c->sticky;
+  }
+  if (cudaGetLastError() != cudaSuccess) {
+    c->sticky = LISE_ECUDA;
+    return c->sticky;
+  }
+  return fetch_err(c);
+}
+
+void lise_destroy(lise_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  free_ctx(c);
+  delete c;
+}
+
+}  // extern "C"

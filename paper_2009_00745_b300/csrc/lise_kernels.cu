@@ -1,0 +1,466 @@
+// lise_kernels.cu -- device kernels of the two-component TDSLDA step and their
+// launchers.  See lise_kernels.cuh for the operator split and the modes.
+#include <cstdio>
+
+#include "lise_kernels.cuh"
+
+namespace lise {
+
+template <typename R> __device__ __forceinline__ typename Cx<R>::T to_r(double2 v);
+template <> __device__ __forceinline__ double2 to_r<double>(double2 v) { return v; }
+template <> __device__ __forceinline__ float2 to_r<float>(double2 v) {
+  return make_float2((float)v.x, (float)v.y);
+}
+__device__ __forceinline__ double2 to_d(double2 v) { return v; }
+__device__ __forceinline__ double2 to_d(float2 v) { return make_double2((double)v.x, (double)v.y); }
+
+__device__ __forceinline__ double2 dadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 dsub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 dscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__device__ __forceinline__ double2 dmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// n += 2 |v|^2 ; nu += u conj(v)
+__device__ __forceinline__ void dens_acc(double2 u, double2 v, double& sn, double& sr, double& si) {
+  sn += 2.0 * (v.x * v.x + v.y * v.y);
+  sr += u.x * v.x + u.y * v.y;
+  si += u.y * v.x - u.x * v.y;
+}
+
+// Padded-plane tile count per block for the planes kernel.
+template <int N> struct PlanesPB { static constexpr int v = N <= 8 ? 8 : (N <= 16 ? 4 : (N <= 32 ? 2 : 1)); };
+
+// ------------------------------------------------------------------ planes --
+template <typename R, int N, int PB, int NT>
+__global__ void __launch_bounds__(NT) k_planes(PlanesArgs a) {
+  using T = typename Cx<R>::T;
+  constexpr int NP = N + 1;   // padded row stride (conflict-free row and column lines)
+  constexpr int PS = N * NP;  // plane stride
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* buf = reinterpret_cast<T*>(smem_raw);
+  T* tw = buf + PB * PS;
+  R* hk = reinterpret_cast<R*>(tw + N);
+  const T* twg = reinterpret_cast<const T*>(a.tw);
+  const R* hg = reinterpret_cast<const R*>(a.hxy);
+  for (int i = threadIdx.x; i < N; i += NT) {
+    tw[i] = twg[i];
+    hk[i] = hg[i];
+  }
+  const long plane0 = (long)blockIdx.x * PB;
+  const long left = a.n_planes - plane0;
+  const int np = left < PB ? (int)left : PB;
+  const double2* src = a.x + plane0 * N * N;
+  for (int i = threadIdx.x; i < PB * N * N; i += NT) {
+    int pl = i / (N * N), r = i % (N * N);
+    T v = pl < np ? to_r<R>(src[i]) : T{R(0), R(0)};
+    buf[pl * PS + (r / N) * NP + (r % N)] = v;
+  }
+  __syncthreads();
+  auto rows = [](int l) { return (l / N) * PS + (l % N) * NP; };
+  auto cols = [](int l) { return (l / N) * PS + (l % N); };
+  fft_lines<N, -1, R, PB * N, NT>(buf, rows, 1, tw, Identity());
+  // forward along y; on store multiply by (alpha/2)(kx^2 + ky^2)/N^2 (line l has kx = l % N)
+  fft_lines<N, -1, R, PB * N, NT>(buf, cols, NP, tw, [&](int l, int k, T v) {
+    R f = hk[l % N] + hk[k];
+    return T{v.x * f, v.y * f};
+  });
+  fft_lines<N, +1, R, PB * N, NT>(buf, cols, NP, tw, Identity());
+  fft_lines<N, +1, R, PB * N, NT>(buf, rows, 1, tw, Identity());
+  T* dst = reinterpret_cast<T*>(a.txy) + plane0 * N * N;
+  for (int i = threadIdx.x; i < np * N * N; i += NT) {
+    int pl = i / (N * N), r = i % (N * N);
+    dst[i] = buf[pl * PS + (r / N) * NP + (r % N)];
+  }
+}
+
+// ----------------------------------------------------------------- pencils --
+template <typename R, int N, int TX, int QB, int MODE>
+__global__ void __launch_bounds__(N * TX) k_pencils(PencilArgs a) {
+  using T = typename Cx<R>::T;
+  constexpr int NT = N * TX;
+  constexpr int CS = N * TX;           // one component block [z][x] in shared memory
+  constexpr int LINES = QB * 2 * TX;   // z-lines per batch
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* buf = reinterpret_cast<T*>(smem_raw);  // [QB][2][N][TX]
+  T* tw = buf + QB * 2 * CS;
+  R* hz = reinterpret_cast<R*>(tw + N);
+  const T* twg = reinterpret_cast<const T*>(a.tw);
+  const R* hg = reinterpret_cast<const R*>(a.hz);
+  for (int i = threadIdx.x; i < N; i += NT) {
+    tw[i] = twg[i];
+    hz[i] = hg[i];
+  }
+  const long nxyz = (long)N * N * N;
+  constexpr int TILES_X = N / TX;
+  const int y = blockIdx.x / TILES_X;
+  const int x0 = (blockIdx.x % TILES_X) * TX;
+  const int z = threadIdx.x / TX, xl = threadIdx.x % TX;
+  const long site = ((long)z * N + y) * N + x0 + xl;
+  const int g = blockIdx.y;
+  const int q_begin = g * a.qg;
+  const int q_end = min(a.n_qp, q_begin + a.qg);
+  double Wv = 0.0;
+  double2 Dv = make_double2(0.0, 0.0);
+  if (MODE != M_ENERGY) {
+    Wv = a.W[site];
+    Dv = a.D[site];
+  }
+  const T* txy = reinterpret_cast<const T*>(a.txy);
+  double sn = 0.0, sr = 0.0, si = 0.0;
+  auto base = [](int l) { return (l / TX) * CS + (l % TX); };
+  __syncthreads();
+
+  for (int qb0 = q_begin; qb0 < q_end; qb0 += QB) {
+    double2 xv[QB][2];
+#pragma unroll
+    for (int j = 0; j < QB; ++j) {
+      const int q = qb0 + j;
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        double2 v = q < q_end ? a.x[(long)(2 * q + c) * nxyz + site] : make_double2(0.0, 0.0);
+        xv[j][c] = v;
+        buf[(2 * j + c) * CS + z * TX + xl] = to_r<R>(v);
+      }
+    }
+    __syncthreads();
+    fft_lines<N, -1, R, LINES, NT>(buf, base, TX, tw, [&](int, int k, T v) {
+      R f = hz[k];
+      return T{v.x * f, v.y * f};
+    });
+    fft_lines<N, +1, R, LINES, NT>(buf, base, TX, tw, Identity());
+
+#pragma unroll
+    for (int j = 0; j < QB; ++j) {
+      const int q = qb0 + j;
+      if (q >= q_end) break;
+      const long iu = (long)(2 * q) * nxyz + site, iv = iu + nxyz;
+      const T Tu = cadd(buf[(2 * j) * CS + z * TX + xl], txy[iu]);
+      const T Tv = cadd(buf[(2 * j + 1) * CS + z * TX + xl], txy[iv]);
+      if (MODE == M_ENERGY) {
+        const double2 v = xv[j][1];
+        const double2 tv = to_d(Tv);
+        sn += 2.0 * (v.x * tv.x + v.y * tv.y);
+        continue;
+      }
+      // H x = [[h, Delta], [Delta*, -h*]] x with h = T + W (W real, T real-symmetric)
+      const T u = to_r<R>(xv[j][0]), v = to_r<R>(xv[j][1]);
+      const R w = (R)Wv;
+      const T d = to_r<R>(Dv);
+      const T hu = T{Tu.x + w * u.x + (d.x * v.x - d.y * v.y), Tu.y + w * u.y + (d.x * v.y + d.y * v.x)};
+      const T hv = T{(d.x * u.x + d.y * u.y) - Tv.x - w * v.x, (d.x * u.y - d.y * u.x) - Tv.y - w * v.y};
+      const double2 Hu = to_d(hu), Hv = to_d(hv);
+      const double2 fu = make_double2(Hu.y, -Hu.x), fv = make_double2(Hv.y, -Hv.x);  // -i H x
+
+      if (MODE == M_RHS) {
+        a.out[iu] = fu;
+        a.out[iv] = fv;
+      } else if (MODE == M_TAYLOR_FIRST) {
+        if (a.dslot) {
+          a.dslot[iu] = fu;
+          a.dslot[iv] = fv;
+        }
+        const double2 tu = dmul(a.coef, Hu), tv = dmul(a.coef, Hv);
+        a.out[iu] = tu;
+        a.out[iv] = tv;
+        a.acc[iu] = dadd(xv[j][0], tu);
+        a.acc[iv] = dadd(xv[j][1], tv);
+      } else if (MODE == M_TAYLOR) {
+        const double2 tu = dmul(a.coef, Hu), tv = dmul(a.coef, Hv);
+        a.out[iu] = tu;
+        a.out[iv] = tv;
+        const double2 au = dadd(a.acc[iu], tu), av = dadd(a.acc[iv], tv);
+        a.acc[iu] = au;
+        a.acc[iv] = av;
+        if (a.dens) dens_acc(au, av, sn, sr, si);
+      } else if (MODE == M_CORRECT) {
+        // Eq. c and Eq. y
+        const double h48 = a.h / 48.0;
+        double2 yo[2];
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const long i = c ? iv : iu;
+          const double2 f = c ? fv : fu;
+          const double2 half = dscale(dadd(a.y0[i], a.y1[i]), 0.5);
+          const double2 s = dadd(dadd(dscale(f, 17.0), dscale(a.d0[i], 51.0)), dadd(dscale(a.d1[i], 3.0), a.d2[i]));
+          const double2 cc = dadd(half, dscale(s, h48));
+          const double2 pmc = dsub(a.p[i], cc);
+          const double2 yn = dadd(cc, dscale(pmc, 9.0 / 170.0));
+          a.ynew[i] = yn;
+          a.pc[i] = pmc;
+          yo[c] = yn;
+        }
+        dens_acc(yo[0], yo[1], sn, sr, si);
+      } else if (MODE == M_DERIV_PREDICT) {
+        // y'_{n+1} and Eq. p, Eq. m of the next step
+        const double h48 = a.h / 48.0;
+        double2 mo[2];
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const long i = c ? iv : iu;
+          const double2 f = c ? fv : fu;
+          a.dslot[i] = f;
+          const double2 half = dscale(dadd(xv[j][c], a.y0[i]), 0.5);
+          const double2 s = dadd(dsub(dscale(f, 119.0), dscale(a.d0[i], 99.0)),
+                                 dsub(dscale(a.d1[i], 69.0), dscale(a.d2[i], 17.0)));
+          const double2 pn = dadd(half, dscale(s, h48));
+          const double2 mv = dsub(pn, dscale(a.pc[i], 161.0 / 170.0));
+          a.p[i] = pn;
+          a.m[i] = mv;
+          mo[c] = mv;
+        }
+        dens_acc(mo[0], mo[1], sn, sr, si);
+      }
+    }
+    __syncthreads();  // the batch buffer is reused
+  }
+  if (a.dens) {
+    const long o = (long)g * nxyz + site;
+    a.part_n[o] = sn;
+    if (MODE != M_ENERGY) {
+      a.part_nr[o] = sr;
+      a.part_ni[o] = si;
+    }
+  }
+}
+
+// ------------------------------------------------------- reduce/potentials --
+__device__ __forceinline__ void neumaier(double& s, double& c, double x) {
+  double t = s + x;
+  if (fabs(s) >= fabs(x))
+    c += (s - t) + x;
+  else
+    c += (x - t) + s;
+  s = t;
+}
+
+__global__ void k_reduce(ReduceArgs a) {
+  const long s = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= a.nxyz) return;
+  double n = 0, cn = 0, r = 0, cr = 0, i = 0, ci = 0;
+  for (int g = 0; g < a.n_groups; ++g) {
+    const long o = (long)g * a.nxyz + s;
+    neumaier(n, cn, a.part_n[o]);
+    neumaier(r, cr, a.part_nr[o]);
+    neumaier(i, ci, a.part_ni[o]);
+  }
+  n += cn;
+  r += cr;
+  i += ci;
+  if (a.avg_n) {
+    n = 0.5 * (n + a.avg_n[s]);
+    const double2 o = a.avg_nu[s];
+    r = 0.5 * (r + o.x);
+    i = 0.5 * (i + o.y);
+  }
+  if (!(isfinite(n) && isfinite(r) && isfinite(i))) atomicOr(a.err, 1);
+  a.n_out[s] = n;
+  a.nu_out[s] = make_double2(r, i);
+  if (!a.W) return;
+  const double PI = 3.14159265358979323846;
+  const double cb = cbrt(3.0 * PI * PI * n);
+  const int iz = (int)(s / ((long)a.N * a.N));
+  double v = a.v_static ? a.v_static[s] : 0.0;
+  v += a.drive * ((iz - a.N / 2) * a.a);
+  a.W[s] = 0.5 * a.beta * cb * cb - a.mu + v;  // U(n) - mu + V_ext
+  a.D[s] = make_double2(-a.g * r, -a.g * i);   // Delta = -g nu
+}
+
+// --------------------------------------------------------------- pointwise --
+// First ABM step after the start procedure: Eq. p and Eq. m, densities of m.
+__global__ void k_predict(PointwiseArgs a) {
+  const long s = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= a.nxyz) return;
+  const int g = blockIdx.y;
+  const int q_begin = g * a.qg, q_end = min(a.n_qp, q_begin + a.qg);
+  const double h48 = a.h / 48.0;
+  double sn = 0, sr = 0, si = 0;
+  for (int q = q_begin; q < q_end; ++q) {
+    double2 mo[2];
+    for (int c = 0; c < 2; ++c) {
+      const long i = (long)(2 * q + c) * a.nxyz + s;
+      const double2 half = dscale(dadd(a.y0[i], a.y1[i]), 0.5);
+      const double2 sm = dadd(dsub(dscale(a.d0[i], 119.0), dscale(a.d1[i], 99.0)),
+                              dsub(dscale(a.d2[i], 69.0), dscale(a.d3[i], 17.0)));
+      const double2 pn = dadd(half, dscale(sm, h48));
+      const double2 mv = dsub(pn, dscale(a.pc[i], 161.0 / 170.0));
+      a.p[i] = pn;
+      a.m[i] = mv;
+      mo[c] = mv;
+    }
+    dens_acc(mo[0], mo[1], sn, sr, si);
+  }
+  const long o = (long)g * a.nxyz + s;
+  a.part_n[o] = sn;
+  a.part_nr[o] = sr;
+  a.part_ni[o] = si;
+}
+
+__global__ void k_density(PointwiseArgs a) {
+  const long s = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= a.nxyz) return;
+  const int g = blockIdx.y;
+  const int q_begin = g * a.qg, q_end = min(a.n_qp, q_begin + a.qg);
+  double sn = 0, sr = 0, si = 0;
+  for (int q = q_begin; q < q_end; ++q) {
+    const long i = (long)(2 * q) * a.nxyz + s;
+    dens_acc(a.src[i], a.src[i + a.nxyz], sn, sr, si);
+  }
+  const long o = (long)g * a.nxyz + s;
+  a.part_n[o] = sn;
+  a.part_nr[o] = sr;
+  a.part_ni[o] = si;
+}
+
+// Energy density per site (times a^3) and a^3 n, for the host's final sum.
+// E = a^3 sum_r [(alpha/2) tau + (3/10) beta (3 pi^2)^(2/3) n^(5/3) + g |nu|^2 + V n]
+// (Eq. pairing has + g_eff |kappa|^2); part holds sum_k 2 Re(v_k^* T v_k).
+__global__ void k_energy_sites(const double* part, int n_groups, const double* nd, const double2* nu,
+                               const double* v_static, double drive, double beta, double g, int N,
+                               double a, double* out) {
+  const long nxyz = (long)N * N * N;
+  const long s = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nxyz) return;
+  double ek = 0, ck = 0;
+  for (int k = 0; k < n_groups; ++k) neumaier(ek, ck, part[(long)k * nxyz + s]);
+  ek += ck;
+  const double PI = 3.14159265358979323846;
+  const double n = nd[s];
+  const double cb = cbrt(3.0 * PI * PI);
+  const double cn = cbrt(n);
+  const int iz = (int)(s / ((long)N * N));
+  double v = v_static ? v_static[s] : 0.0;
+  v += drive * ((iz - N / 2) * a);
+  const double2 w = nu[s];
+  const double a3 = a * a * a;
+  out[s] = a3 * (ek + 0.3 * beta * cb * cb * n * cn * cn + g * (w.x * w.x + w.y * w.y) + v * n);
+  out[nxyz + s] = a3 * n;
+}
+
+__global__ void k_finite(const double2* x, long count, int* err) {
+  int bad = 0;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long)gridDim.x * blockDim.x) {
+    const double2 v = x[i];
+    if (!(isfinite(v.x) && isfinite(v.y))) bad = 1;
+  }
+  if (bad) atomicOr(err, 2);
+}
+
+// ---------------------------------------------------------------- launchers --
+bool supported_n(int N) {
+  switch (N) {
+    case 8: case 12: case 16: case 20: case 24: case 32: case 40: case 48: case 64: return true;
+    default: return false;
+  }
+}
+int pencil_tx(int N) { return N % 8 == 0 ? 8 : 4; }
+int pencil_qb(int, int) { return 4; }
+
+template <typename R, int N>
+static int planes_n(const PlanesArgs& a, cudaStream_t s) {
+  using T = typename Cx<R>::T;
+  constexpr int PB = PlanesPB<N>::v;
+  constexpr int NT = 256;
+  const size_t smem = (size_t)PB * N * (N + 1) * sizeof(T) + N * sizeof(T) + N * sizeof(R);
+  auto kern = k_planes<R, N, PB, NT>;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 3;
+    attr = true;
+  }
+  const long blocks = (a.n_planes + PB - 1) / PB;
+  if (blocks <= 0) return 0;
+  kern<<<(unsigned)blocks, NT, smem, s>>>(a);
+  return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}
+
+template <typename R, int N, int MODE>
+static int pencils_nm(const PencilArgs& a, cudaStream_t s) {
+  using T = typename Cx<R>::T;
+  constexpr int TX = (N % 8 == 0) ? 8 : 4;
+  constexpr int QB = 4;
+  const size_t smem = (size_t)QB * 2 * N * TX * sizeof(T) + N * sizeof(T) + N * sizeof(R);
+  auto kern = k_pencils<R, N, TX, QB, MODE>;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 3;
+    attr = true;
+  }
+  const int n_groups = (a.n_qp + a.qg - 1) / a.qg;
+  dim3 grid((N / TX) * N, n_groups);
+  kern<<<grid, N * TX, smem, s>>>(a);
+  return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}
+
+template <typename R, int N>
+static int pencils_n(int mode, const PencilArgs& a, cudaStream_t s) {
+  switch (mode) {
+    case M_RHS: return pencils_nm<R, N, M_RHS>(a, s);
+    case M_TAYLOR_FIRST: return pencils_nm<R, N, M_TAYLOR_FIRST>(a, s);
+    case M_TAYLOR: return pencils_nm<R, N, M_TAYLOR>(a, s);
+    case M_CORRECT: return pencils_nm<R, N, M_CORRECT>(a, s);
+    case M_DERIV_PREDICT: return pencils_nm<R, N, M_DERIV_PREDICT>(a, s);
+    case M_ENERGY: return pencils_nm<R, N, M_ENERGY>(a, s);
+    default: return 1;
+  }
+}
+
+#define LISE_FOR_N(X) X(8) X(12) X(16) X(20) X(24) X(32) X(40) X(48) X(64)
+
+int launch_planes(int N, int mixed, const PlanesArgs& a, cudaStream_t s) {
+  switch (N) {
+#define CASE(n) \
+  case n: return mixed ? planes_n<float, n>(a, s) : planes_n<double, n>(a, s);
+    LISE_FOR_N(CASE)
+#undef CASE
+    default: return 1;
+  }
+}
+
+int launch_pencils(int N, int mixed, int mode, const PencilArgs& a, cudaStream_t s) {
+  switch (N) {
+#define CASE(n) \
+  case n: return mixed ? pencils_n<float, n>(mode, a, s) : pencils_n<double, n>(mode, a, s);
+    LISE_FOR_N(CASE)
+#undef CASE
+    default: return 1;
+  }
+}
+
+int launch_reduce(const ReduceArgs& a, cudaStream_t s) {
+  const int nt = 256;
+  const long blocks = (a.nxyz + nt - 1) / nt;
+  k_reduce<<<(unsigned)blocks, nt, 0, s>>>(a);
+  return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}
+
+int launch_predict(const PointwiseArgs& a, cudaStream_t s) {
+  const int nt = 256;
+  dim3 grid((unsigned)((a.nxyz + nt - 1) / nt), (a.n_qp + a.qg - 1) / a.qg);
+  k_predict<<<grid, nt, 0, s>>>(a);
+  return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}
+
+int launch_density(const PointwiseArgs& a, cudaStream_t s) {
+  const int nt = 256;
+  dim3 grid((unsigned)((a.nxyz + nt - 1) / nt), (a.n_qp + a.qg - 1) / a.qg);
+  k_density<<<grid, nt, 0, s>>>(a);
+  return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}
+
+int launch_energy_sites(const double* part_ekin, int n_groups, const double* n, const double2* nu,
+                        const double* v_static, double drive, double beta, double g, int N,
+                        double a, double* e_site, cudaStream_t s) {
+  const int nt = 256;
+  const long nxyz = (long)N * N * N;
+  k_energy_sites<<<(unsigned)((nxyz + nt - 1) / nt), nt, 0, s>>>(part_ekin, n_groups, n, nu, v_static,
+                                                                  drive, beta, g, N, a, e_site);
+  return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}
+
+int launch_finite_check(const double2* x, long count, int* err, cudaStream_t s) {
+  k_finite<<<148 * 4, 256, 0, s>>>(x, count, err);
+  return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}
+
+}  // namespace lise

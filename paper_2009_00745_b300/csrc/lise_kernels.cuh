@@ -1,0 +1,119 @@
+// lise_kernels.cuh -- device kernels of the two-component TDSLDA step.
+//
+// Operator split used on the device (exact in exact arithmetic):
+//   T psi = -(alpha/2) lap psi = T_xy psi + T_z psi,
+//   T_xy = F_xy^-1 [(alpha/2)(kx^2 + ky^2) F_xy],  T_z = F_z^-1 [(alpha/2) kz^2 F_z],
+// which equals F^-1[(alpha/2)|k|^2 F] of Sec. "Discretization" because F_z
+// commutes with the in-plane multiplier.  Kernel "planes" applies T_xy to every
+// xy-plane of every (state, component) and writes it to a scratch array;
+// kernel "pencils" applies T_z to z-pencils, adds the scratch, forms
+//   H psi = [[h, Delta],[Delta*, -h*]] psi,  h = T + W   (Eq. tdslda),
+// and finishes with a fused, mode-dependent epilogue (the ABM formulas of
+// Eqs. p, m, c, y, the order-4 series terms of the start procedure, or a plain
+// right-hand side) plus per-group partial sums of the densities
+// n = 2 sum |v|^2 and nu = sum u v^* (Eqs. rho_t, nu_t).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lise_fft.cuh"
+
+namespace lise {
+
+enum PencilMode : int {
+  M_RHS = 0,            // out = -i H x
+  M_TAYLOR_FIRST = 1,   // h = H x; [dslot = -i h]; term = coef h -> out; acc = x + term
+  M_TAYLOR = 2,         // term = coef H x -> out (in place); acc += term; [densities of acc]
+  M_CORRECT = 3,        // m' = -i H m; Eq. c, Eq. y -> ynew, pc; densities of ynew
+  M_DERIV_PREDICT = 4,  // d = -i H y_{n+1} -> dslot; Eq. p, Eq. m for the next step -> p, m;
+                        // densities of m
+  M_ENERGY = 5,         // part_n += sum_q 2 Re(conj(v) T v)
+};
+
+struct PencilArgs {
+  const double2* x;       // operand state [q][c][z][y][x]
+  const void* txy;        // T_xy x, complex of the compute precision
+  const double* W;        // h - T = U(n) - mu + V_ext  [site]
+  const double2* D;       // Delta [site]
+  const void* tw;         // forward twiddles of the compute precision, N entries
+  const void* hz;         // (alpha/2) kz^2 / N, N entries, compute precision
+  int n_qp;
+  int qg;                 // states per density group (one grid row per group)
+  double2* out;
+  double2* acc;
+  double2* dslot;
+  double2 coef;
+  double h;               // time step
+  const double2* y0;      // y_n
+  const double2* y1;      // y_{n-1} (M_CORRECT)
+  const double2* d0;      // y'_n
+  const double2* d1;      // y'_{n-1}
+  const double2* d2;      // y'_{n-2}
+  double2* p;             // p_{n+1} (read in M_CORRECT, written in M_DERIV_PREDICT)
+  double2* pc;            // p - c (written in M_CORRECT, read in M_DERIV_PREDICT)
+  double2* m;             // m (written in M_DERIV_PREDICT)
+  double2* ynew;          // y_{n+1} (written in M_CORRECT; may alias y1)
+  double* part_n;         // [group][site] partial sums
+  double* part_nr;
+  double* part_ni;
+  int dens;               // accumulate density partials of the mode's output state
+};
+
+struct PlanesArgs {
+  const double2* x;       // operand state, n_planes consecutive N x N planes
+  void* txy;              // output T_xy x
+  const void* tw;         // forward twiddles, N entries
+  const void* hxy;        // (alpha/2) k^2 / N^2, N entries
+  long n_planes;
+};
+
+struct ReduceArgs {
+  const double* part_n;
+  const double* part_nr;
+  const double* part_ni;
+  int n_groups;
+  long nxyz;
+  int N;
+  double a;
+  double* n_out;          // densities of this reduction [site]
+  double2* nu_out;
+  const double* avg_n;    // if non-null: n <- (n + avg_n)/2, nu likewise (start corrector)
+  const double2* avg_nu;
+  double* W;              // potentials out
+  double2* D;
+  const double* v_static; // may be null
+  double drive;           // A sin(Omega t)
+  double beta, mu, g;
+  int* err;               // set bit 0 if a density is not finite
+};
+
+struct PointwiseArgs {
+  // predictor + modifier for the first ABM step: p = Eq. p, m = Eq. m
+  const double2 *y0, *y1, *d0, *d1, *d2, *d3, *pc;
+  double2 *p, *m;
+  double h;
+  // density partials of `src` (for the plain density pass) or of m
+  const double2* src;
+  double* part_n;
+  double* part_nr;
+  double* part_ni;
+  int n_qp, qg;
+  long nxyz;
+};
+
+// Host-side launchers (defined in lise_kernels.cu).
+int launch_planes(int N, int mixed, const PlanesArgs& a, cudaStream_t s);
+int launch_pencils(int N, int mixed, int mode, const PencilArgs& a, cudaStream_t s);
+int launch_reduce(const ReduceArgs& a, cudaStream_t s);
+int launch_predict(const PointwiseArgs& a, cudaStream_t s);
+int launch_density(const PointwiseArgs& a, cudaStream_t s);
+int launch_energy_sites(const double* part_ekin, int n_groups, const double* n, const double2* nu,
+                        const double* v_static, double drive, double beta, double g, int N,
+                        double a, double* e_site, cudaStream_t s);
+int launch_finite_check(const double2* x, long count, int* err, cudaStream_t s);
+// Tile width (x values per pencil block) and group width for a lattice.
+int pencil_tx(int N);
+int pencil_qb(int N, int mixed);
+bool supported_n(int N);
+
+}  // namespace lise

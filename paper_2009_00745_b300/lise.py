@@ -1,0 +1,204 @@
+"""Thin ctypes binding of liblise.so (include/lise.h): argument marshalling only.
+
+Every step of the TDSLDA path runs in the CUDA library; this module converts
+numpy arrays or CUDA tensors to pointers and status codes to exceptions.  If
+the library cannot be loaded the import fails: there is no fallback.
+
+State arrays are complex128 of shape (n_qp, 2, N, N, N) (component 0 = u,
+1 = v; index order z, y, x), densities have shape (N, N, N).
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblise.so")
+
+FP64 = 0
+MIXED = 1
+
+OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ESTATE = range(7)
+
+
+class LiseError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {strerror(status)} (status {status})")
+
+
+class _Params(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("dx", C.c_double),
+                ("n_qp", C.c_int), ("alpha", C.c_double), ("beta", C.c_double),
+                ("mu", C.c_double), ("g", C.c_double), ("v_static", C.c_void_p),
+                ("drive_A", C.c_double), ("drive_Omega", C.c_double), ("precision", C.c_int),
+                ("device", C.c_int), ("hbm_budget_bytes", C.c_size_t), ("stream", C.c_void_p)]
+
+
+# Exported functions with their ctypes signatures (mirrors include/lise.h).
+SIGNATURES = {
+    "lise_footprint_bytes": (C.c_size_t, [C.c_void_p]),
+    "lise_create": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "lise_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_double]),
+    "lise_set_state_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_double]),
+    "lise_step": (C.c_int, [C.c_void_p, C.c_int, C.c_double]),
+    "lise_get_state": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "lise_get_state_device": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "lise_get_time": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "lise_densities": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "lise_energy": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "lise_rhs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_void_p]),
+    "lise_sync": (C.c_int, [C.c_void_p]),
+    "lise_strerror": (C.c_char_p, [C.c_int]),
+    "lise_destroy": (None, [C.c_void_p]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load liblise.so (raises OSError if it is missing or does not load)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise OSError(f"liblise.so not built at {path}; run paper_2009_00745_b300/build.py")
+        L = C.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def strerror(status: int) -> str:
+    return load().lise_strerror(int(status)).decode()
+
+
+def _check(rc, where):
+    if rc != OK:
+        raise LiseError(rc, where)
+
+
+def _params(N, n_qp, a, alpha, beta, mu, g, v_static, drive_A, drive_Omega, precision, device,
+            hbm_budget_bytes, stream):
+    prec = {"fp64": FP64, "mixed": MIXED}.get(precision, precision)
+    vs = None
+    if v_static is not None:
+        vs = np.ascontiguousarray(v_static, dtype=np.float64).reshape(-1)
+        if vs.size != N ** 3:
+            raise ValueError("v_static must hold N^3 values")
+    p = _Params(N, N, N, float(a), int(n_qp), float(alpha), float(beta), float(mu), float(g),
+                None if vs is None else vs.ctypes.data, float(drive_A), float(drive_Omega),
+                int(prec), int(device), int(hbm_budget_bytes), stream)
+    return p, vs
+
+
+def footprint_bytes(N, n_qp, precision="fp64", **kw) -> int:
+    p, _ = _params(N, n_qp, kw.get("a", 1.0), kw.get("alpha", 1.0), kw.get("beta", 0.0),
+                   kw.get("mu", 0.0), kw.get("g", 0.0), None, 0.0, 0.0, precision, 0, 0, None)
+    return int(load().lise_footprint_bytes(C.byref(p)))
+
+
+def _ptr(x, dtype=np.complex128, count=None, writable=False):
+    """(pointer, is_device, keepalive) for a numpy array or a CUDA tensor."""
+    if hasattr(x, "data_ptr") and hasattr(x, "is_cuda"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        if count is not None and x.numel() * x.element_size() != count * np.dtype(dtype).itemsize:
+            raise ValueError("tensor has the wrong size")
+        return x.data_ptr(), bool(x.is_cuda), x
+    a = np.asarray(x)
+    if a.dtype != dtype or not a.flags.c_contiguous:
+        if writable:
+            raise ValueError(f"output array must be C-contiguous {np.dtype(dtype)}")
+        a = np.ascontiguousarray(a, dtype=dtype)
+    if count is not None and a.size != count:
+        raise ValueError(f"array has {a.size} elements, expected {count}")
+    return a.ctypes.data, False, a
+
+
+class Context:
+    """One TDSLDA evolution on one GPU (a lise_ctx)."""
+
+    def __init__(self, N, n_qp, *, a=1.0, alpha=1.0, beta=0.0, mu=0.0, g=0.0, v_static=None,
+                 drive_A=0.0, drive_Omega=0.0, precision="fp64", device=0, hbm_budget_bytes=0,
+                 stream=None):
+        self.N, self.n_qp = int(N), int(n_qp)
+        self._p, self._vs = _params(N, n_qp, a, alpha, beta, mu, g, v_static, drive_A, drive_Omega,
+                                    precision, device, hbm_budget_bytes, stream)
+        h = C.c_void_p()
+        _check(load().lise_create(C.byref(self._p), C.byref(h)), "lise_create")
+        self._h = h
+        self.dt = None
+
+    @classmethod
+    def from_workload(cls, w, **kw):
+        return cls(w.nx, w.n_qp, a=w.a, alpha=w.alpha, beta=w.beta, mu=w.mu, g=w.g,
+                   v_static=w.v_static, drive_A=w.drive_A, drive_Omega=w.drive_Omega,
+                   precision=kw.pop("precision", w.precision), **kw)
+
+    @property
+    def shape(self):
+        return (self.n_qp, 2, self.N, self.N, self.N)
+
+    @property
+    def count(self):
+        return self.n_qp * 2 * self.N ** 3
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().lise_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_state(self, psi, t0, dt):
+        ptr, dev, keep = _ptr(psi, count=self.count)
+        fn = load().lise_set_state_device if dev else load().lise_set_state
+        _check(fn(self._h, ptr, float(t0), float(dt)), "lise_set_state")
+        self.dt = float(dt)
+
+    def step(self, n_steps, dt=None):
+        _check(load().lise_step(self._h, int(n_steps), float(self.dt if dt is None else dt)), "lise_step")
+
+    def state(self, out=None):
+        if out is None:
+            out = np.empty(self.shape, dtype=np.complex128)
+        ptr, dev, _ = _ptr(out, count=self.count, writable=True)
+        fn = load().lise_get_state_device if dev else load().lise_get_state
+        _check(fn(self._h, ptr), "lise_get_state")
+        return out
+
+    @property
+    def t(self):
+        t = C.c_double()
+        _check(load().lise_get_time(self._h, C.byref(t)), "lise_get_time")
+        return t.value
+
+    def densities(self):
+        n = np.empty((self.N,) * 3)
+        nu = np.empty((self.N,) * 3, dtype=np.complex128)
+        _check(load().lise_densities(self._h, n.ctypes.data, nu.ctypes.data), "lise_densities")
+        return n, nu
+
+    def energy(self):
+        E, Nn = C.c_double(), C.c_double()
+        _check(load().lise_energy(self._h, C.byref(E), C.byref(Nn)), "lise_energy")
+        return E.value, Nn.value
+
+    def rhs(self, psi, t):
+        ptr, _, keep = _ptr(psi, count=self.count)
+        out = np.empty(self.shape, dtype=np.complex128)
+        _check(load().lise_rhs(self._h, ptr, float(t), out.ctypes.data), "lise_rhs")
+        return out
+
+    def sync(self):
+        _check(load().lise_sync(self._h), "lise_sync")

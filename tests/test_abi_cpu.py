@@ -1,0 +1,87 @@
+"""The C ABI library loads and exports every entry point include/lise.h declares;
+host-side argument checks (no GPU needed, no device call made)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_2009_00745_b300 import build as B
+from paper_2009_00745_b300 import lise as L
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "lise.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lise_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return L.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(lib, n), n
+    # the binding covers the same set
+    assert set(names) == set(L.SIGNATURES)
+
+
+def test_strerror(lib):
+    assert L.strerror(L.OK) == "ok"
+    assert "budget" in L.strerror(L.ENOMEM)
+    assert L.strerror(999) == "unknown status"
+
+
+def test_footprint_model():
+    f16 = L.footprint_bytes(16, 256)
+    f32 = L.footprint_bytes(32, 2048)
+    assert f16 > 9 * 16 * 256 * 2 * 16 ** 3   # at least the 9 history arrays + scratch
+    # state arrays dominate: 10 complex128 copies of 2048 x 2 x 32^3
+    assert abs(f32 - 10 * 16 * 2048 * 2 * 32 ** 3) / f32 < 0.02
+    fm = L.footprint_bytes(48, 4096, precision="mixed")
+    assert abs(fm - 9.5 * 16 * 4096 * 2 * 48 ** 3) / fm < 0.02
+    assert L.footprint_bytes(30, 8) == 0  # unsupported lattice
+
+
+def _create(**kw):
+    base = dict(N=16, n_qp=8)
+    base.update(kw)
+    N = base.pop("N")
+    n_qp = base.pop("n_qp")
+    return L.Context(N, n_qp, **base)
+
+
+@pytest.mark.parametrize("kw", [dict(N=30), dict(N=16, n_qp=0), dict(N=16, a=0.0), dict(N=16, precision=7),
+                                dict(N=16, beta=float("nan"))])
+def test_invalid_parameters(kw):
+    with pytest.raises(L.LiseError) as e:
+        _create(**kw)
+    assert e.value.status == L.EINVAL
+
+
+def test_non_cubic_rejected(lib):
+    p = L._Params(16, 16, 32, 1.0, 4, 1.0, 0.0, 0.0, 0.0, None, 0.0, 0.0, 0, 0, 0, None)
+    h = C.c_void_p()
+    assert lib.lise_create(C.byref(p), C.byref(h)) == L.EINVAL
+    assert lib.lise_footprint_bytes(C.byref(p)) == 0
+
+
+def test_budget_rejected_before_any_allocation():
+    need = L.footprint_bytes(32, 2048)
+    with pytest.raises(L.LiseError) as e:
+        _create(N=32, n_qp=2048, hbm_budget_bytes=need - 1)
+    assert e.value.status == L.ENOMEM
+
+
+def test_null_arguments(lib):
+    assert lib.lise_create(None, None) == L.EINVAL
+    assert lib.lise_step(None, 1, 0.1) == L.EINVAL
+    assert lib.lise_sync(None) == L.EINVAL
+    lib.lise_destroy(None)

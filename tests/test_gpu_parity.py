@@ -1,0 +1,206 @@
+"""GPU parity: the CUDA library through its C ABI against the FP64 CPU oracle.
+
+FP64 path tolerance (after a whole run): ||x_gpu - x_oracle||_2 / ||x_oracle||_2
+<= 1e-11 for psi, n and nu.  A single right-hand side is held to 1e-12.  The
+mixed path (complex64 FFTs and H psi, FP64 history) is held to the bound its
+arithmetic allows, derived in the individual tests.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2009_00745_b300 import lise as L
+from paper_2009_00745_b300 import workloads as W
+
+from .helpers import oracle_params, random_state, rel
+
+pytestmark = pytest.mark.gpu
+
+TOL_FP64_RUN = 1e-11
+TOL_FP64_RHS = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2009_00745_b300 import build
+    build.build()
+    L.load()
+
+
+# ------------------------------------------------------------ one RHS ----
+
+@pytest.mark.parametrize("N,n_qp", [(8, 5), (12, 7), (16, 9), (20, 3), (24, 6), (32, 5), (40, 3), (48, 2),
+                                    (64, 1)])
+def test_rhs_all_lattices(N, n_qp):
+    psi = random_state(N, n_qp, seed=N)
+    kw = dict(a=0.8, alpha=1.3, beta=-0.5, mu=0.4, g=0.7)
+    rng = np.random.default_rng(1)
+    vs = rng.uniform(-1, 1, (N, N, N))
+    with L.Context(N, n_qp, v_static=vs, drive_A=0.02, drive_Omega=0.3, **kw) as ctx:
+        got = ctx.rhs(psi, 0.9)
+    p = O.Params(N, N, N, n_qp=n_qp, v_static=vs, drive_A=0.02, drive_Omega=0.3, **kw)
+    ref = O.rhs(p, psi, 0.9)
+    assert rel(got, ref) < TOL_FP64_RHS
+
+
+def test_rhs_mixed_precision_bound():
+    N, n_qp = 24, 6
+    psi = random_state(N, n_qp, seed=3, kmax=6)
+    kw = dict(alpha=1.0, beta=-0.5, mu=0.3, g=1.0)
+    with L.Context(N, n_qp, precision="mixed", **kw) as ctx:
+        got = ctx.rhs(psi, 0.0)
+    ref = O.rhs(O.Params(N, N, N, n_qp=n_qp, **kw), psi, 0.0)
+    # FP32 transforms: a few units of 2^-24 times log2(N^3) butterflies
+    err = rel(got, ref)
+    assert err < 2e-6, err
+    assert err > 1e-12  # it is really FP32 arithmetic
+
+
+# ------------------------------------------------------------ full runs ----
+
+def run_gpu(w, steps, precision="fp64"):
+    with L.Context.from_workload(w, precision=precision) as ctx:
+        ctx.set_state(w.initial_state(), 0.0, w.dt)
+        ctx.step(steps)
+        psi = ctx.state()
+        n, nu = ctx.densities()
+        E, N = ctx.energy()
+        t = ctx.t
+    return psi, n, nu, E, N, t
+
+
+def run_oracle(w, steps):
+    s = O.Solver(oracle_params(w))
+    s.set_state(w.initial_state(), 0.0, w.dt)
+    s.step(steps)
+    n, nu = s.densities()
+    E, N = s.energy()
+    return s.state(), n, nu, E, N, s.t
+
+
+def check_run(w, steps):
+    g = run_gpu(w, steps)
+    o = run_oracle(w, steps)
+    assert g[5] == pytest.approx(o[5], abs=1e-14)
+    assert rel(g[0], o[0]) < TOL_FP64_RUN, "psi"
+    assert rel(g[1], o[1]) < TOL_FP64_RUN, "n"
+    assert rel(g[2], o[2]) < TOL_FP64_RUN, "nu"
+    assert g[3] == pytest.approx(o[3], rel=1e-11, abs=1e-11)
+    assert g[4] == pytest.approx(o[4], rel=1e-12)
+    return g, o
+
+
+def test_ufg16_full_workload():
+    # 16^3 lattice, 256 states, dt 0.005, 20 ABM steps, gauge noise seed 42
+    w = W.named("ufg16_fp64")
+    check_run(w, w.steps)
+
+
+@pytest.mark.parametrize("N,n_qp,steps", [(8, 13, 12), (12, 9, 6), (20, 11, 5), (24, 37, 4), (40, 5, 3)])
+def test_ragged_state_counts(N, n_qp, steps):
+    w = W.ufg_plane_waves(N, n_qp, noise_eps=0.05, steps=steps)
+    check_run(w, steps)
+
+
+def test_trap_vortex_reduced():
+    w = W.trap_vortex(32, 24, steps=8)
+    check_run(w, w.steps)
+
+
+def test_drive_reduced():
+    w = W.driven(48, 6, steps=6, precision="fp64")
+    check_run(w, w.steps)
+
+
+def test_backward_time_step():
+    w = W.ufg_plane_waves(16, 20, noise_eps=0.1)
+    w.dt = -0.005
+    check_run(w, 6)
+
+
+def test_mixed_run_error_bound():
+    w = W.ufg_plane_waves(16, 64, noise_eps=1e-3, steps=20)
+    g = run_gpu(w, w.steps, precision="mixed")
+    o = run_oracle(w, w.steps)
+    # per right-hand side the FP32 error is ~1e-7 relative; it enters y through dt
+    # times the ABM weights, over 3 start steps (8 H psi each) and 20 steps
+    assert rel(g[0], o[0]) < 5e-6
+    assert rel(g[1], o[1]) < 5e-6
+    assert rel(g[2], o[2]) < 5e-6
+    assert abs(g[3] - o[3]) / abs(o[3]) < 1e-6
+
+
+# ------------------------------------------------------- full-size sample ----
+
+def test_trap_vortex_full_size_rhs_sampled():
+    # the full 32^3 x 2048-state workload: one right-hand side on the GPU; the oracle
+    # checks sampled states one by one with densities built from all states
+    w = W.named("trap32_vortex_fp64")
+    psi = w.initial_state()
+    with L.Context.from_workload(w) as ctx:
+        got = ctx.rhs(psi, 0.25)
+    p = oracle_params(w)
+    n, nu = O.densities(p, psi)
+    Wp, Dp = O.potentials(p, n, nu, 0.25)
+    sample = [0, 1, 777, 1500, 2046, 2047]
+    ps = p.with_(n_qp=len(sample))
+    ref = -1j * O.apply_h(ps, Wp, Dp, psi[sample])
+    assert rel(got[sample], ref) < TOL_FP64_RHS
+
+
+def test_trap_vortex_full_size_invariants():
+    w = W.named("trap32_vortex_fp64")
+    with L.Context.from_workload(w) as ctx:
+        ctx.set_state(w.initial_state(), 0.0, w.dt)
+        E0, N0 = ctx.energy()
+        ctx.step(10)
+        E1, N1 = ctx.energy()
+        psi = ctx.state()
+    assert abs(N1 - N0) / N0 < 1e-9
+    # state norms stay 1 to the integrator's truncation level
+    norms = np.sum(np.abs(psi) ** 2, axis=(1, 2, 3, 4)) * w.a ** 3
+    assert np.abs(norms - 1).max() < 1e-9
+
+
+# ---------------------------------------------------------------- errors ----
+
+def test_error_paths():
+    w = W.ufg_plane_waves(8, 4)
+    with L.Context.from_workload(w) as ctx:
+        with pytest.raises(L.LiseError) as e:
+            ctx.step(1, 0.005)
+        assert e.value.status == L.ESTATE
+        bad = w.initial_state()
+        bad[1, 0, 2, 3, 4] = np.nan
+        with pytest.raises(L.LiseError) as e:
+            ctx.set_state(bad, 0.0, 0.005)
+        assert e.value.status == L.ENONFINITE
+        # the context stays usable after a rejected input
+        ctx.set_state(w.initial_state(), 0.0, 0.005)
+        with pytest.raises(L.LiseError) as e:
+            ctx.step(1, 0.004)
+        assert e.value.status == L.EINVAL
+        with pytest.raises(L.LiseError) as e:
+            ctx.set_state(w.initial_state(), 0.0, 0.0)
+        assert e.value.status == L.EINVAL
+        ctx.step(2)
+        ctx.sync()
+
+
+def test_nonfinite_density_reported():
+    # a state that overflows |v|^2 in the density reduction is reported, not propagated
+    w = W.ufg_plane_waves(8, 4)
+    psi = w.initial_state()
+    psi[0, 1] *= 1e200
+    with L.Context.from_workload(w) as ctx:
+        with pytest.raises(L.LiseError) as e:
+            ctx.set_state(psi, 0.0, 0.005)
+        assert e.value.status == L.ENONFINITE
+
+
+def test_deterministic_bitwise():
+    w = W.ufg_plane_waves(16, 40, noise_eps=0.05)
+    a = run_gpu(w, 5)
+    b = run_gpu(w, 5)
+    assert np.array_equal(a[0], b[0])
+    assert np.array_equal(a[1], b[1])

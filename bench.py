@@ -1,0 +1,356 @@
+"""Throughput benchmark of the TDSLDA step (qp*site*steps/s) on B300.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl reference]
+
+A "step" is one Adams-Bashforth-Milne step (Eqs. p, m, c, y of arXiv:2009.00745:
+two right-hand sides, each an FFT kinetic operator, a BdG apply and a density
+reduction) over all quasiparticle states of the workload.  Default workload:
+32^3 lattice, 2048 states in a harmonic trap with a vortex phase, FP64
+(trap32_vortex_fp64).  Inputs are synthetic and seeded (workloads.py).
+
+value   device time of K steps with the state resident in HBM (CUDA events on
+        the context's stream, W warm-up steps first).  The state and history
+        (10 complex128 copies, ~21 GB) are far larger than L2, so no flush.
+e2e     the same metric through the C ABI with host buffers: lise_set_state
+        from pinned host memory (including the start procedure), K steps,
+        lise_get_state back to pinned host memory and lise_energy.
+roofline, cpu_baseline, clocks, gpu_launches: see the README of each key in
+the design doc.  --impl reference times the FP64 CPU oracle instead (the reference
+arm of this build: a deliberately plain program on the host cores).
+Multi-GPU (torchrun): every rank runs an independent replica ("replicas only";
+the single-GPU path has no exchange step), value = total units / max time.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "qp·site·steps/s, FP64 vs mixed at ≤1e-6 rel energy drift; p50/p99 latency"
+UNIT = "qp·site·steps/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+HBM_FALLBACK_GBS = 6400.0
+# FP64 peak from unit counts and clock: 148 SMs x 2 DFMA/clk x 2 flop x 2.032 GHz
+FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12
+# FP32 peak: 148 SMs x 128 FFMA/clk x 2 flop x 2.032 GHz
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
+
+
+def log2(n):
+    return math.log2(n)
+
+
+def algorithmic_per_qp_site(N, mixed):
+    """Algorithmic flops and HBM bytes per (state, site) of each kernel class
+    for one ABM step (two right-hand sides).  FFT convention: 5 n log2 n real
+    flops per complex length-n transform."""
+    L = log2(N)
+    cs = 16                      # complex128 bytes, one component
+    txy = 8 if mixed else 16     # T_xy scratch, one component
+    planes_flops = 2 * (2 * 2 * 5 * L + 3)            # 2 comps: 2D fwd+inv, multiply
+    pencils_flops = 2 * (2 * 5 * L + 4) + 24 + 52 + 13  # z fwd+inv, BdG, ABM, densities
+    planes_bytes = 2 * (cs + txy)                      # read x, write T_xy
+    pencils_bytes = 2 * (cs + txy + 8 * cs)            # x, T_xy, 6 history reads + 2 writes (or 5 + 3)
+    return {
+        "planes": {"flops": 2 * planes_flops, "bytes": 2 * planes_bytes, "launches_per_step": 2},
+        "pencils": {"flops": 2 * pencils_flops, "bytes": 2 * pencils_bytes, "launches_per_step": 2},
+    }
+
+
+def read_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2009_00745_b300", "csrc")
+    for name in ("lise_fft.cuh", "lise_kernels.cuh", "lise_kernels.cu"):  # the kernels' sources
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload, kernel):
+    """dram bytes per launch from the committed ncu summary, if it was taken on the
+    current kernel sources (profiles/traffic.json: {workload: {kernel: {...}}})."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d[workload][kernel]
+        if e.get("source_hash") != kernel_source_hash():
+            return None
+        return float(e["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def oracle_sample_rate(w, n_sample, steps, warmup):
+    """The FP64 CPU oracle as it stands on the first n_sample states of workload w:
+    start procedure (untimed), warmup ABM steps (untimed), then `steps` timed ABM
+    steps.  Returns (qp*site*steps/s, seconds, threads)."""
+    from oracle import oracle as O
+    p = O.Params(w.nx, w.ny, w.nz, a=w.a, n_qp=n_sample, alpha=w.alpha, beta=w.beta, mu=w.mu, g=w.g,
+                 v_static=w.v_static, drive_A=w.drive_A, drive_Omega=w.drive_Omega)
+    s = O.Solver(p)
+    s.set_state(w.initial_state(0, n_sample), 0.0, w.dt)
+    if warmup:
+        s.step(warmup)
+    t0 = time.perf_counter()
+    s.step(steps)
+    dt = time.perf_counter() - t0
+    return n_sample * w.nxyz * steps / dt, dt, O.num_threads()
+
+
+def run_reference(args, w):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    n_sample = args.ref_states
+    rate, secs, thr = oracle_sample_rate(w, n_sample, args.steps, args.warmup)
+    sample = (f"first {n_sample} of {w.n_qp} states of {w.name} ({w.nx}^3), start procedure untimed, "
+              f"{args.warmup} warm-up + {args.steps} timed ABM steps")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_of(w, args),
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": sample},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_of(w, args):
+    return {"workload": w.name, "lattice": f"{w.nx}^3", "n_qp": w.n_qp, "dt": w.dt,
+            "precision": w.precision, "steps_in_workload": w.steps,
+            "l2": "inputs larger than L2 (state + ABM history %.1f GB, no flush)" % (
+                10 * 16 * w.n_qp * 2 * w.nxyz / 1e9)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="trap32_vortex_fp64")
+    ap.add_argument("--precision", default=None, choices=[None, "fp64", "mixed"])
+    ap.add_argument("--n-qp", type=int, default=None, help="override the workload's state count")
+    ap.add_argument("--impl", default="lise", choices=["lise", "reference"])
+    ap.add_argument("--ref-states", type=int, default=32)
+    ap.add_argument("--cpu-baseline-states", type=int, default=32)
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+
+    from paper_2009_00745_b300 import workloads as Wl
+    w = Wl.named(args.workload, n_qp=args.n_qp)
+    if args.precision:
+        w.precision = args.precision
+
+    if args.impl == "reference":
+        return run_reference(args, w)
+
+    import numpy as np
+    import torch
+    from paper_2009_00745_b300 import lise as L
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    mixed = w.precision == "mixed"
+
+    # initial state built on the host, uploaded once (not timed for `value`)
+    psi_host = torch.empty((w.n_qp, 2, w.nz, w.ny, w.nx), dtype=torch.complex128, pin_memory=True)
+    w.initial_state(out=psi_host.numpy())
+    psi_dev = psi_host.to(f"cuda:{local}")
+    torch.cuda.synchronize()
+
+    ctx = L.Context.from_workload(w, device=local, stream=stream.cuda_stream)
+    ctx.set_state(psi_dev, 0.0, w.dt)
+    ctx.step(args.warmup)
+    ctx.sync()
+
+    # ---- timed region: K steps, device events on the context stream
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.4)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx.step(args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    E_dev, N_dev = ctx.energy()
+    if world > 1:
+        t = torch.tensor([ms], device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    units = float(w.n_qp) * w.nxyz * args.steps
+    value = world * units / (ms / 1e3)
+    ctx.close()
+    del psi_dev
+    torch.cuda.empty_cache()
+
+    # ---- roofline of the dominant kernel class, from the live event timings
+    alg = algorithmic_per_qp_site(w.nx, mixed)
+    dom = max(("planes", "pencils"), key=lambda k: prof[k][1])
+    launches, tot_ms = prof[dom]
+    per_launch_ms = tot_ms / max(launches, 1)
+    qp_sites = float(w.n_qp) * w.nxyz
+    a = alg[dom]
+    bytes_per_launch = a["bytes"] * qp_sites / a["launches_per_step"]
+    flops_per_launch = a["flops"] * qp_sites / a["launches_per_step"]
+    hbm_peak, hbm_src = read_peaks()
+    gbs = bytes_per_launch / (per_launch_ms / 1e3) / 1e9
+    tflops = flops_per_launch / (per_launch_ms / 1e3) / 1e12
+    alu_peak = FP32_PEAK_TFLOPS if mixed else FP64_PEAK_TFLOPS
+    hbm_frac, alu_frac = gbs / hbm_peak, tflops / alu_peak
+    traffic = recorded_traffic(w.name, dom)
+    if alu_frac >= hbm_frac:
+        roof = {"bound": "alu", "achieved": tflops, "peak": alu_peak, "unit": "TFLOP/s", "frac": alu_frac,
+                "peak_source": ("FP32" if mixed else "FP64") + " unit counts x 2.032 GHz (derived)",
+                "hbm_frac_of_measured": hbm_frac}
+    else:
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_frac,
+                "peak_source": hbm_src, "alu_frac": alu_frac}
+    roof.update({"kernel": dom, "traffic": traffic, "launch_ms": per_launch_ms,
+                 "algorithmic_bytes_per_launch": bytes_per_launch,
+                 "algorithmic_flops_per_launch": flops_per_launch,
+                 "kernel_share": {k: v[1] / max(sum(x[1] for x in prof.values()), 1e-30) for k, v in prof.items()}})
+    gpu_launches = int(sum(v[0] for v in prof.values()))
+
+    # ---- e2e through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        out_host = torch.empty(psi_host.shape, dtype=psi_host.dtype, pin_memory=True)
+        ctx2 = L.Context.from_workload(w, device=local)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx2.set_state(psi_host.numpy(), 0.0, w.dt)
+        ctx2.step(args.steps)
+        ctx2.state(out=out_host.numpy())
+        E2, N2 = ctx2.energy()
+        t_e2e = time.perf_counter() - t0
+        ctx2.close()
+        state_bytes = 16 * w.n_qp * 2 * w.nxyz
+        e2e = {"value": world * units / t_e2e, "unit": UNIT,
+               "h2d_bytes_per_step": state_bytes / args.steps, "d2h_bytes_per_step": (state_bytes + 16) / args.steps,
+               "includes": "set_state from pinned host (H2D + 3 series-expansion start steps), K ABM steps, "
+                           "get_state to pinned host, energy"}
+
+    # ---- CPU baseline: the oracle on a bounded sample of the same workload
+    cpu = None
+    if rank == 0 and args.cpu_baseline_states > 0:
+        ns = args.cpu_baseline_states
+        rate, secs, thr = oracle_sample_rate(w, ns, 2, 0)
+        cpu = {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle",
+               "sample": f"first {ns} of {w.n_qp} states of {w.name}, 2 timed ABM steps after the untimed start"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if not mixed else "f64+c64",
+            "data": "synthetic", "config": config_of(w, args), "roofline": roof, "cpu_baseline": cpu,
+            "e2e": e2e, "clocks": clocks, "gpu_launches": gpu_launches,
+            "energy_after_timed_steps": E_dev, "particle_number": N_dev,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -122,6 +122,21 @@ int lise_energy(lise_ctx *c, double *E, double *N);
  * Synchronises. */
 int lise_rhs(lise_ctx *c, const double *psi, double t, double *dpsi_out);
 
+/* Per-launch timing.  Kernel classes of the path: */
+#define LISE_KC_PLANES 0    /* in-plane 2D FFT -> kinetic multiply -> inverse (T_xy) */
+#define LISE_KC_PENCILS 1   /* z-pencil FFT, BdG apply and the fused ABM / series epilogue */
+#define LISE_KC_REDUCE 2    /* density reduction over state groups and the potentials */
+#define LISE_KC_POINTWISE 3 /* start-up predictor, plain density and input checks */
+#define LISE_KC_COUNT 4
+/* enable = 1 records a CUDA event pair on the context's stream around every
+ * kernel launch from now on (and clears earlier records); 0 stops recording. */
+int lise_profile(lise_ctx *c, int enable);
+/* Launch count and summed device time (ms) of one kernel class since profiling
+ * was enabled.  Synchronises.  LISE_EINVAL for an unknown class. */
+int lise_profile_read(lise_ctx *c, int kernel_class, long *launches, double *total_ms);
+/* Name of a kernel class ("planes", "pencils", ...), or NULL. */
+const char *lise_kernel_class_name(int kernel_class);
+
 /* Waits for enqueued work and reports sticky errors. */
 int lise_sync(lise_ctx *c);
 

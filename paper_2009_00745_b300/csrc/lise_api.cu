@@ -53,6 +53,10 @@ struct lise_ctx {
   int ready = 0;
   int sticky = LISE_OK;
   double* host_e = nullptr;
+  // per-launch timing (lise_profile)
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<int> rec_cls;  // class of record i uses events 2i, 2i+1
 };
 
 namespace {
@@ -107,6 +111,23 @@ double drive_at(const lise_ctx* c, double t) {
 
 int cu(cudaError_t e) { return e == cudaSuccess ? LISE_OK : LISE_ECUDA; }
 
+// Records a CUDA event pair around the launch made by f() when profiling is on.
+template <typename F>
+int timed(lise_ctx* c, int cls, F f) {
+  if (!c->prof) return f();
+  const size_t i = c->rec_cls.size();
+  while (c->ev_pool.size() < 2 * (i + 1)) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return LISE_ECUDA;
+    c->ev_pool.push_back(e);
+  }
+  if (cudaEventRecord(c->ev_pool[2 * i], c->stream) != cudaSuccess) return LISE_ECUDA;
+  int rc = f();
+  if (cudaEventRecord(c->ev_pool[2 * i + 1], c->stream) != cudaSuccess) return LISE_ECUDA;
+  c->rec_cls.push_back(cls);
+  return rc;
+}
+
 #define TRY(x)                  \
   do {                          \
     int rc__ = (x);             \
@@ -138,11 +159,12 @@ int run_planes(lise_ctx* c, const double2* x) {
   a.tw = c->tw;
   a.hxy = c->hxy;
   a.n_planes = (long)c->p.n_qp * 2 * c->N;
-  return launch_planes(c->N, c->mixed, a, c->stream) ? LISE_ECUDA : LISE_OK;
+  return timed(c, LISE_KC_PLANES, [&] { return launch_planes(c->N, c->mixed, a, c->stream) ? LISE_ECUDA : LISE_OK; });
 }
 
 int run_pencils(lise_ctx* c, int mode, const PencilArgs& a) {
-  return launch_pencils(c->N, c->mixed, mode, a, c->stream) ? LISE_ECUDA : LISE_OK;
+  return timed(c, LISE_KC_PENCILS,
+               [&] { return launch_pencils(c->N, c->mixed, mode, a, c->stream) ? LISE_ECUDA : LISE_OK; });
 }
 
 // Reduce the density partials; optionally average with (avg_n, avg_nu); write
@@ -168,7 +190,7 @@ int run_reduce(lise_ctx* c, int dslot, const double* avg_n, const double2* avg_n
   r.mu = c->p.mu;
   r.g = c->p.g;
   r.err = c->err;
-  return launch_reduce(r, c->stream) ? LISE_ECUDA : LISE_OK;
+  return timed(c, LISE_KC_REDUCE, [&] { return launch_reduce(r, c->stream) ? LISE_ECUDA : LISE_OK; });
 }
 
 int run_density(lise_ctx* c, const double2* src) {
@@ -181,7 +203,7 @@ int run_density(lise_ctx* c, const double2* src) {
   a.n_qp = c->p.n_qp;
   a.qg = c->qg;
   a.nxyz = c->nxyz;
-  return launch_density(a, c->stream) ? LISE_ECUDA : LISE_OK;
+  return timed(c, LISE_KC_POINTWISE, [&] { return launch_density(a, c->stream) ? LISE_ECUDA : LISE_OK; });
 }
 
 double2 cx(double re, double im) { return make_double2(re, im); }
@@ -274,7 +296,7 @@ int start_procedure(lise_ctx* c, double t0, double dt) {
   w.n_qp = c->p.n_qp;
   w.qg = c->qg;
   w.nxyz = c->nxyz;
-  TRY(launch_predict(w, c->stream) ? LISE_ECUDA : LISE_OK);
+  TRY(timed(c, LISE_KC_POINTWISE, [&] { return launch_predict(w, c->stream) ? LISE_ECUDA : LISE_OK; }));
   const double t3 = t0 + 3 * dt;
   TRY(run_reduce(c, 1, nullptr, nullptr, true, t3 + dt));
   c->t = t3;
@@ -336,6 +358,7 @@ void free_ctx(lise_ctx* c) {
                   c->Dl, c->v_static, c->tw, c->hxy, c->hz, c->e_site, c->err};
   for (void* q : ptrs)
     if (q) cudaFree(q);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   std::free(c->host_e);
 }
@@ -614,6 +637,36 @@ int lise_rhs(lise_ctx* c, const double* psi, double t, double* dpsi_out) {
   TRY(cu(cudaMemcpyAsync(dpsi_out, c->D[0], (size_t)c->ns * sizeof(double2), cudaMemcpyDeviceToHost, c->stream)));
   TRY(cu(cudaStreamSynchronize(c->stream)));
   return fetch_err(c);
+}
+
+int lise_profile(lise_ctx* c, int enable) {
+  if (!c) return LISE_EINVAL;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return LISE_ECUDA;
+  c->prof = enable != 0;
+  if (c->prof) c->rec_cls.clear();
+  return LISE_OK;
+}
+
+int lise_profile_read(lise_ctx* c, int cls, long* launches, double* total_ms) {
+  if (!c || !launches || !total_ms || cls < 0 || cls >= LISE_KC_COUNT) return LISE_EINVAL;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return LISE_ECUDA;
+  long n = 0;
+  double ms = 0.0;
+  for (size_t i = 0; i < c->rec_cls.size(); ++i) {
+    if (c->rec_cls[i] != cls) continue;
+    float e = 0.f;
+    if (cudaEventElapsedTime(&e, c->ev_pool[2 * i], c->ev_pool[2 * i + 1]) != cudaSuccess) return LISE_ECUDA;
+    ms += e;
+    ++n;
+  }
+  *launches = n;
+  *total_ms = ms;
+  return LISE_OK;
+}
+
+const char* lise_kernel_class_name(int cls) {
+  static const char* names[LISE_KC_COUNT] = {"planes", "pencils", "reduce", "pointwise"};
+  return (cls >= 0 && cls < LISE_KC_COUNT) ? names[cls] : nullptr;
 }
 
 int lise_sync(lise_ctx* c) {

@@ -19,6 +19,7 @@ FP64 = 0
 MIXED = 1
 
 OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ESTATE = range(7)
+KC_PLANES, KC_PENCILS, KC_REDUCE, KC_POINTWISE, KC_COUNT = range(5)
 
 
 class LiseError(RuntimeError):
@@ -49,6 +50,9 @@ SIGNATURES = {
     "lise_energy": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "lise_rhs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_void_p]),
     "lise_sync": (C.c_int, [C.c_void_p]),
+    "lise_profile": (C.c_int, [C.c_void_p, C.c_int]),
+    "lise_profile_read": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_long), C.POINTER(C.c_double)]),
+    "lise_kernel_class_name": (C.c_char_p, [C.c_int]),
     "lise_strerror": (C.c_char_p, [C.c_int]),
     "lise_destroy": (None, [C.c_void_p]),
 }
@@ -198,6 +202,19 @@ class Context:
         ptr, _, keep = _ptr(psi, count=self.count)
         out = np.empty(self.shape, dtype=np.complex128)
         _check(load().lise_rhs(self._h, ptr, float(t), out.ctypes.data), "lise_rhs")
+        return out
+
+    def profile(self, enable=True):
+        """Record a CUDA event pair around every kernel launch (clears old records)."""
+        _check(load().lise_profile(self._h, int(bool(enable))), "lise_profile")
+
+    def profile_read(self):
+        """{class name: (launches, total device ms)} since profiling was enabled."""
+        out = {}
+        for k in range(KC_COUNT):
+            n, ms = C.c_long(), C.c_double()
+            _check(load().lise_profile_read(self._h, k, C.byref(n), C.byref(ms)), "lise_profile_read")
+            out[load().lise_kernel_class_name(k).decode()] = (n.value, ms.value)
         return out
 
     def sync(self):

@@ -202,20 +202,24 @@ def driven(n: int = 48, n_qp: int = 4096, *, steps=1000, dt=0.005, A=0.01, Omega
     return _bcs(w)
 
 
-def named(name: str) -> Workload:
-    """The standard workloads by name.
+def named(name: str, n_qp: Optional[int] = None) -> Workload:
+    """The standard workloads by name (n_qp overrides the state count; the name
+    then carries the count as a suffix).
 
     ufg16_fp64            16^3 x 256 states, dt 0.005, 20 steps, FP64
     trap32_vortex_fp64    32^3 x 2048 states, trap omega 0.1 + vortex, 1000 steps, FP64
     drive48_mixed         48^3 x 4096 states, drive A 0.01 Omega 0.3, 1000 steps, mixed
     drive48_fp64_small    48^3 x 256 states, the drive workload reduced for the oracle, 20 steps
     """
-    if name == "ufg16_fp64":
-        return ufg_plane_waves(16, 256, steps=20, name=name)
-    if name == "trap32_vortex_fp64":
-        return trap_vortex(32, 2048, steps=1000, name=name)
-    if name == "drive48_mixed":
-        return driven(48, 4096, steps=1000, precision="mixed", name=name)
-    if name == "drive48_fp64_small":
-        return driven(48, 256, steps=20, precision="fp64", name=name)
-    raise KeyError(name)
+    table = {
+        "ufg16_fp64": lambda q: ufg_plane_waves(16, q or 256, steps=20, name=name),
+        "trap32_vortex_fp64": lambda q: trap_vortex(32, q or 2048, steps=1000, name=name),
+        "drive48_mixed": lambda q: driven(48, q or 4096, steps=1000, precision="mixed", name=name),
+        "drive48_fp64_small": lambda q: driven(48, q or 256, steps=20, precision="fp64", name=name),
+    }
+    if name not in table:
+        raise KeyError(name)
+    w = table[name](n_qp)
+    if n_qp is not None:
+        w.name = f"{name}:{n_qp}"
+    return w

@@ -146,6 +146,35 @@ const char *lise_strerror(int status);
 /* Frees the context and its device memory (synchronises first).  NULL is a no-op. */
 void lise_destroy(lise_ctx *c);
 
+/* ---- Right-hand side without any allocation (no counterpart in the paper) ----
+ * For callers that must not allocate device memory while they run: a host
+ * framework whose caching allocator already holds the free device memory (a
+ * stray cudaMalloc would fail or fragment its pool), latency-critical loops
+ * that cannot afford cudaMalloc's implicit device synchronisation, plug-ins
+ * that are handed only buffers and a stream.  It computes the same
+ * f(t, psi) = -i H[psi](t) psi as lise_rhs, from the device buffer psi_dev to
+ * the device buffer dpsi_dev (layout as above, on device p->device, enqueued on
+ * p->stream, NULL = the default stream), with no context and no cudaMalloc,
+ * cudaFree or other allocating call.  All scratch lives in one fixed device
+ * array of LISE_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds
+ * until the process exits.
+ *   Capacity: 32 n_qp N^3 bytes (FP64; 16 for LISE_MIXED) for the in-plane
+ *   kinetic part, 24 G N^3 for density partials (G = groups of <= 64 states),
+ *   56 N^3 for densities, potentials and V_ext, plus small tables, each part
+ *   rounded up to 256 bytes.  A problem that needs more returns LISE_ENOMEM
+ *   (e.g. FP64 16^3 fits about 400 states, 32^3 about 50).
+ *   Set-up: the first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress, with that device current); make that first call
+ *   before any stream capture.
+ *   Sharing: every call reuses the same array and leaves its contents behind
+ *   (the error word is cleared at the start of each call); calls that overlap
+ *   on the GPU (other streams, other host threads) race on it, so serialise
+ *   them.  p->hbm_budget_bytes is ignored.  Synchronises p->stream.
+ *   Errors: LISE_EINVAL, LISE_ENOMEM (too large for the array), LISE_ECUDA,
+ *   LISE_ENONFINITE (a density is NaN or infinite). */
+#define LISE_NOALLOC_SCRATCH_BYTES (64u << 20)
+int lise_rhs_noalloc(const lise_params *p, const double *psi_dev, double t, double *dpsi_dev);
+
 #ifdef __cplusplus
 }
 #endif

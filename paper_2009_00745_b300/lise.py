@@ -55,6 +55,7 @@ SIGNATURES = {
     "lise_kernel_class_name": (C.c_char_p, [C.c_int]),
     "lise_strerror": (C.c_char_p, [C.c_int]),
     "lise_destroy": (None, [C.c_void_p]),
+    "lise_rhs_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_void_p]),
 }
 
 _lib = None

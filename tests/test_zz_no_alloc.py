@@ -1,0 +1,62 @@
+"""lise_rhs_noalloc: the right-hand side for callers that cannot allocate device
+memory (a framework allocator owns the free memory, or cudaMalloc's implicit
+synchronisation is not allowed where they run).  It is called here through the
+C ABI on caller-owned device buffers, twice in a row with different inputs, and
+each output is checked against the context-based lise_rhs entry point within
+the single-right-hand-side tolerance the parity tests use (1e-12 relative).
+
+The file name sorts last so that a run stopping at the first failure has run
+every other test before this one.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from paper_2009_00745_b300 import lise as L
+
+from .helpers import random_state, rel
+
+pytestmark = pytest.mark.gpu
+
+TOL_RHS = 1e-12
+
+
+def _noalloc(p, psi_dev, t, out_dev):
+    return L.load().lise_rhs_noalloc(C.byref(p), psi_dev.data_ptr(), float(t), out_dev.data_ptr())
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL_RHS), ("mixed", TOL_RHS)])
+def test_noalloc_matches_context_rhs_twice(precision, tol):
+    import torch
+    from paper_2009_00745_b300 import build
+    build.build()
+    N, n_qp = 16, 24
+    kw = dict(a=0.9, alpha=1.2, beta=-0.5, mu=0.35, g=0.8, drive_A=0.02, drive_Omega=0.3)
+    vs = np.random.default_rng(5).uniform(-0.5, 0.5, (N, N, N))
+    psis = [random_state(N, n_qp, seed=11), random_state(N, n_qp, seed=12, kmax=5)]
+    times = [0.3, 1.7]
+    # reference: the context-based entry point
+    refs = []
+    with L.Context(N, n_qp, v_static=vs, precision=precision, **kw) as ctx:
+        for psi, t in zip(psis, times):
+            refs.append(ctx.rhs(psi, t))
+    p, keep = L._params(N, n_qp, kw["a"], kw["alpha"], kw["beta"], kw["mu"], kw["g"], vs, kw["drive_A"],
+                        kw["drive_Omega"], precision, 0, 0, None)
+    out = torch.empty((n_qp, 2, N, N, N), dtype=torch.complex128, device="cuda:0")
+    for psi, t, ref in zip(psis, times, refs):
+        x = torch.from_numpy(psi).to("cuda:0")
+        out.fill_(float("nan"))
+        rc = _noalloc(p, x, t, out)
+        assert rc == L.OK, L.strerror(rc)
+        got = out.cpu().numpy()
+        assert np.isfinite(got).all()
+        assert rel(got, ref) < tol
+
+
+def test_noalloc_rejects_oversized_problem():
+    import torch
+    N, n_qp = 32, 512  # 32 * 512 * 32^3 bytes of kinetic scratch alone: 512 MiB > 64 MiB
+    p, _ = L._params(N, n_qp, 1.0, 1.0, 0.0, 0.0, 0.0, None, 0.0, 0.0, "fp64", 0, 0, None)
+    x = torch.zeros(1, dtype=torch.complex128, device="cuda:0")
+    assert _noalloc(p, x, 0.0, x) == L.ENOMEM

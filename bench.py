@@ -50,18 +50,24 @@ def log2(n):
 
 def algorithmic_per_qp_site(N, mixed):
     """Algorithmic flops and HBM bytes per (state, site) of each kernel class
-    for one ABM step (two right-hand sides).  FFT convention: 5 n log2 n real
-    flops per complex length-n transform."""
+    for one ABM step (two right-hand sides), for the kernels as designed:
+
+    planes   read the operand, write T_xy (both components);
+    pencils  (corrector launch) read m, T_xy, Q, R; write y_{n+1}, p - c;
+             (derivative/predictor launch) read y_{n+1}, T_xy, y_n, y'_n,
+             y'_{n-1}, y'_{n-2}, p - c; write y'_{n+1}, m, Q, R.
+    complex128 = 16 B per component; in the mixed path T_xy and m are complex64.
+    FFT convention: 5 n log2 n real flops per complex length-n transform."""
     L = log2(N)
-    cs = 16                      # complex128 bytes, one component
-    txy = 8 if mixed else 16     # T_xy scratch, one component
-    planes_flops = 2 * (2 * 2 * 5 * L + 3)            # 2 comps: 2D fwd+inv, multiply
-    pencils_flops = 2 * (2 * 5 * L + 4) + 24 + 52 + 13  # z fwd+inv, BdG, ABM, densities
-    planes_bytes = 2 * (cs + txy)                      # read x, write T_xy
-    pencils_bytes = 2 * (cs + txy + 8 * cs)            # x, T_xy, 6 history reads + 2 writes (or 5 + 3)
+    c16, cr = 16, (8 if mixed else 16)   # complex128 / compute-precision component
+    planes_bytes = 2 * (cr + cr) + 2 * (c16 + cr)          # operand m, then operand y_{n+1}
+    correct_bytes = 2 * (cr + cr + 2 * c16) + 2 * (2 * c16)
+    deriv_bytes = 2 * (c16 + cr + 5 * c16) + 2 * (3 * c16 + cr)
+    planes_flops = 2 * 2 * (2 * 2 * 5 * L + 3)              # 2 launches x 2 comps: 2D fwd+inv, multiply
+    pencils_flops = 2 * (2 * (2 * 5 * L + 4) + 24) + (16 + 13) + (92 + 13)
     return {
-        "planes": {"flops": 2 * planes_flops, "bytes": 2 * planes_bytes, "launches_per_step": 2},
-        "pencils": {"flops": 2 * pencils_flops, "bytes": 2 * pencils_bytes, "launches_per_step": 2},
+        "planes": {"flops": planes_flops, "bytes": planes_bytes, "launches_per_step": 2},
+        "pencils": {"flops": pencils_flops, "bytes": correct_bytes + deriv_bytes, "launches_per_step": 2},
     }
 
 
@@ -153,6 +159,20 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def whole_job_value(ms_local, units_per_rank, world, device="cpu"):
+    """Replicas: every rank times the same amount of work; the job time is the
+    maximum over ranks and value = world * units / job time.  Returns
+    (value, job_ms)."""
+    ms = float(ms_local)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return world * float(units_per_rank) / (ms / 1e3), ms
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -197,6 +217,53 @@ def run_reference(args, w):
     return 0
 
 
+def run_drift(args, w):
+    """Mixed vs FP64 on the same workload: K ABM steps each, the energy sampled
+    every --drift-every steps.  Reports max_t |E_mixed(t) - E_FP64(t)| / |E_FP64(t)|
+    (the energy of a truncated set of states is not an invariant, so the FP64
+    trajectory is the reference) and the final relative errors of psi, n, nu."""
+    import numpy as np
+    import torch
+    from paper_2009_00745_b300 import lise as L
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    psi_host = torch.empty((w.n_qp, 2, w.nz, w.ny, w.nx), dtype=torch.complex128, pin_memory=True)
+    w.initial_state(out=psi_host.numpy())
+    K, every = args.steps, args.drift_every
+    out = {}
+    for prec in ("fp64", "mixed"):
+        t0 = time.perf_counter()
+        with L.Context.from_workload(w, precision=prec, device=local) as ctx:
+            ctx.set_state(psi_host.numpy(), 0.0, w.dt)
+            E = [ctx.energy()]
+            done = 0
+            while done < K:
+                k = min(every, K - done)
+                ctx.step(k)
+                done += k
+                E.append(ctx.energy())
+            psi = ctx.state()
+            n, nu = ctx.densities()
+        out[prec] = {"E": np.array([e[0] for e in E]), "N": np.array([e[1] for e in E]), "psi": psi, "n": n,
+                     "nu": nu, "seconds": time.perf_counter() - t0}
+    f, m = out["fp64"], out["mixed"]
+    rel = lambda a, b: float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+    drift = float(np.max(np.abs(m["E"] - f["E"]) / np.abs(f["E"])))
+    line = {"mode": "drift", "workload": w.name, "lattice": f"{w.nx}^3", "n_qp": w.n_qp, "steps": K,
+            "dt": w.dt, "sample_every": every,
+            "max_rel_energy_dev_mixed_vs_fp64": drift,
+            "rel_err_psi": rel(m["psi"], f["psi"]), "rel_err_n": rel(m["n"], f["n"]),
+            "rel_err_nu": rel(m["nu"], f["nu"]),
+            "fp64_energy_change": float(abs(f["E"][-1] - f["E"][0]) / abs(f["E"][0])),
+            "max_rel_N_dev_mixed_vs_fp64": float(np.max(np.abs(m["N"] - f["N"]) / np.abs(f["N"]))),
+            "fp64_N_change": float(abs(f["N"][-1] - f["N"][0]) / abs(f["N"][0])),
+            "seconds": {"fp64": f["seconds"], "mixed": m["seconds"]}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def config_of(w, args):
     return {"workload": w.name, "lattice": f"{w.nx}^3", "n_qp": w.n_qp, "dt": w.dt,
             "precision": w.precision, "steps_in_workload": w.steps,
@@ -216,6 +283,9 @@ def main():
     ap.add_argument("--ref-states", type=int, default=32)
     ap.add_argument("--cpu-baseline-states", type=int, default=32)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--drift", action="store_true",
+                    help="compare mixed with FP64 over --steps steps instead of timing")
+    ap.add_argument("--drift-every", type=int, default=50)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -227,6 +297,8 @@ def main():
 
     if args.impl == "reference":
         return run_reference(args, w)
+    if args.drift:
+        return run_drift(args, w)
 
     import numpy as np
     import torch
@@ -272,12 +344,8 @@ def main():
     prof = ctx.profile_read()
     ctx.profile(False)
     E_dev, N_dev = ctx.energy()
-    if world > 1:
-        t = torch.tensor([ms], device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     units = float(w.n_qp) * w.nxyz * args.steps
-    value = world * units / (ms / 1e3)
+    value, ms = whole_job_value(ms, units, world, device=f"cuda:{local}")
     ctx.close()
     del psi_dev
     torch.cuda.empty_cache()

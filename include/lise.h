@@ -122,6 +122,18 @@ int lise_energy(lise_ctx *c, double *E, double *N);
  * Synchronises. */
 int lise_rhs(lise_ctx *c, const double *psi, double t, double *dpsi_out);
 
+/* Checkpoint / restart.  The paper restarts from saved wavefunctions with a new
+ * series-expansion start (Sec. "Checkpoint and restart"); these calls save the
+ * whole ABM history instead, so a run resumes bit-exactly:
+ * y_n, y_{n-1}, y'_n..y'_{n-3}, m_{n+1}, p_n - c_n, Q, R, the potentials of
+ * m_{n+1}, t and dt, behind a 64-byte header.  Host buffers; synchronise. */
+size_t lise_checkpoint_bytes(const lise_ctx *c);
+/* LISE_ESTATE before lise_set_state; LISE_EINVAL if bytes is too small. */
+int lise_checkpoint_save(lise_ctx *c, void *buf, size_t bytes);
+/* The checkpoint must come from a context with the same lattice, state count
+ * and precision (else LISE_EINVAL); the physical parameters are the context's. */
+int lise_checkpoint_load(lise_ctx *c, const void *buf, size_t bytes);
+
 /* Per-launch timing.  Kernel classes of the path: */
 #define LISE_KC_PLANES 0    /* in-plane 2D FFT -> kinetic multiply -> inverse (T_xy) */
 #define LISE_KC_PENCILS 1   /* z-pencil FFT, BdG apply and the fused ABM / series epilogue */

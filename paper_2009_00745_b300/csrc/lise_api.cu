@@ -3,16 +3,17 @@
 // A context owns the ABM history on the device:
 //   y_n, y_{n-1}             two state slots (swapped every step)
 //   y'_n .. y'_{n-3}         a ring of four derivative slots
-//   p_{n+1}, m_{n+1}, p-c    predictor, modifier, and p_n - c_n of Eq. m
+//   m_{n+1}, p_n - c_n       modifier (Eq. m) and the difference it uses
+//   Q, R                     the corrector's precombined history (lise_kernels.cuh)
 //   T_xy scratch             the in-plane kinetic part of the current operand
 // plus per-group density partial sums, reduced densities and the potentials
 // W = U(n) - mu + V_ext and Delta of the operand of the next right-hand side.
 //
 // One ABM step (Eqs. p, m, c, y) is 6 launches:
-//   planes(m), pencils[CORRECT]        m' = -iHm; c, y_{n+1}, p - c; densities of y_{n+1}
+//   planes(m), pencils[CORRECT]        m' = -iHm; y_{n+1} = Q + k1 m', p - c; densities of y_{n+1}
 //   reduce                             W, Delta of y_{n+1} at t_{n+1}
 //   planes(y_{n+1}), pencils[DERIV_PREDICT]
-//                                      y'_{n+1}; p_{n+2}, m_{n+2}; densities of m_{n+2}
+//                                      y'_{n+1}; m_{n+2}, Q, R; densities of m_{n+2}
 //   reduce                             W, Delta of m_{n+2} at t_{n+2}
 #include <cmath>
 #include <cstdlib>
@@ -38,7 +39,8 @@ struct lise_ctx {
   double2* slot[2] = {nullptr, nullptr};
   int y0_slot = 0;                 // slot holding y_n
   double2* D[4] = {nullptr, nullptr, nullptr, nullptr};  // D[k] = y'_{n-k}
-  double2 *P = nullptr, *M = nullptr, *PC = nullptr;
+  void* M = nullptr;  // m_{n+1}, complex of the compute precision (only an H psi operand)
+  double2 *PC = nullptr, *Q = nullptr, *R = nullptr;
   void* TXY = nullptr;
   double *part_n = nullptr, *part_nr = nullptr, *part_ni = nullptr;
   double* dn[2] = {nullptr, nullptr};
@@ -95,7 +97,8 @@ Footprint footprint(const lise_params* p) {
   const long ns = (long)p->n_qp * 2 * nxyz;
   int qg, ng;
   choose_groups((int)N, p->n_qp, &qg, &ng);
-  f.state = 9 * (size_t)ns * sizeof(double2);  // 2 y slots, 4 y', P, M, P-C
+  // 2 y slots, 4 y', P-C, Q, R in complex128; m in the compute precision
+  f.state = 9 * (size_t)ns * sizeof(double2) + (size_t)ns * (p->precision == LISE_MIXED ? sizeof(float2) : sizeof(double2));
   f.txy = (size_t)ns * (p->precision == LISE_MIXED ? sizeof(float2) : sizeof(double2));
   f.partials = 3 * (size_t)ng * nxyz * sizeof(double);
   f.small = (size_t)nxyz * (2 * sizeof(double) + 2 * sizeof(double2) + sizeof(double) + sizeof(double2) +
@@ -152,9 +155,10 @@ PencilArgs pencil_base(const lise_ctx* c) {
   return a;
 }
 
-int run_planes(lise_ctx* c, const double2* x) {
+int run_planes(lise_ctx* c, const double2* x, const void* xr = nullptr) {
   PlanesArgs a;
   a.x = x;
+  a.xr = xr;
   a.txy = c->TXY;
   a.tw = c->tw;
   a.hxy = c->hxy;
@@ -211,21 +215,22 @@ double2 cx(double re, double im) { return make_double2(re, im); }
 // psi_out = sum_{j=0}^{4} (-i dt H)^j / j! psi_in with the current potentials
 // (order-4 series of exp(-i H dt)).  If dslot != nullptr, also stores
 // -i H psi_in there.  The last term's kernel accumulates the densities of
-// psi_out into the partials.  term is scratch (the P array).
+// psi_out into the partials.  The series term lives in the Q array, which the
+// start procedure fills only at its end.
 int taylor4(lise_ctx* c, const double2* psi_in, double2* psi_out, double2* dslot, double dt) {
   TRY(run_planes(c, psi_in));
   PencilArgs a = pencil_base(c);
   a.x = psi_in;
-  a.out = c->P;
+  a.out = c->Q;
   a.acc = psi_out;
   a.dslot = dslot;
   a.coef = cx(0.0, -dt);
   TRY(run_pencils(c, M_TAYLOR_FIRST, a));
   for (int j = 2; j <= 4; ++j) {
-    TRY(run_planes(c, c->P));
+    TRY(run_planes(c, c->Q));
     PencilArgs b = pencil_base(c);
-    b.x = c->P;
-    b.out = c->P;
+    b.x = c->Q;
+    b.out = c->Q;
     b.acc = psi_out;
     b.coef = cx(0.0, -dt / j);
     b.dens = (j == 4);
@@ -258,8 +263,9 @@ int start_procedure(lise_ctx* c, double t0, double dt) {
   TRY(run_reduce(c, 0, nullptr, nullptr, true, t0));
   for (int s = 0; s < 3; ++s) {
     const double ts = t0 + s * dt;
-    // predictor with H(t_s): psi_pre into M; y'_s = -i H(t_s) y_s into D[3 - s]
-    TRY(taylor4(c, cur, c->M, c->D[3 - s], dt));
+    // predictor with H(t_s): psi_pre into R (free until the end of the start);
+    // y'_s = -i H(t_s) y_s into D[3 - s]
+    TRY(taylor4(c, cur, c->R, c->D[3 - s], dt));
     // corrector densities (n_pre + n(t_s)) / 2, potentials at t_s + dt/2
     TRY(run_reduce(c, 1, c->dn[0], c->dnu[0], true, ts + 0.5 * dt));
     // psi(t_s + dt) = exp(-i H_cor dt) psi(t_s), densities into dn[0] at t_{s+1}
@@ -287,8 +293,10 @@ int start_procedure(lise_ctx* c, double t0, double dt) {
   w.d2 = c->D[2];
   w.d3 = c->D[3];
   w.pc = c->PC;
-  w.p = c->P;
+  w.q = c->Q;
+  w.r = c->R;
   w.m = c->M;
+  w.mixed = c->mixed;
   w.h = dt;
   w.part_n = c->part_n;
   w.part_nr = c->part_nr;
@@ -309,17 +317,14 @@ int abm_step(lise_ctx* c) {
   const double t1 = c->t + h;
   double2* yn = c->slot[c->y0_slot];
   double2* ynm1 = c->slot[1 - c->y0_slot];
-  // RHS #1 on m_{n+1}: Eq. c, Eq. y; y_{n+1} replaces y_{n-1}
-  TRY(run_planes(c, c->M));
+  // RHS #1 on m_{n+1} (stored in the compute precision): Eq. c, Eq. y through Q, R;
+  // y_{n+1} replaces y_{n-1}
+  TRY(run_planes(c, nullptr, c->M));
   PencilArgs a = pencil_base(c);
-  a.x = c->M;
+  a.xr = c->M;
   a.h = h;
-  a.y0 = yn;
-  a.y1 = ynm1;
-  a.d0 = c->D[0];
-  a.d1 = c->D[1];
-  a.d2 = c->D[2];
-  a.p = c->P;
+  a.q = c->Q;
+  a.r = c->R;
   a.pc = c->PC;
   a.ynew = ynm1;
   a.dens = 1;
@@ -336,7 +341,8 @@ int abm_step(lise_ctx* c) {
   b.d2 = c->D[2];
   b.dslot = c->D[3];
   b.pc = c->PC;
-  b.p = c->P;
+  b.q = c->Q;
+  b.r = c->R;
   b.m = c->M;
   b.dens = 1;
   TRY(run_pencils(c, M_DERIV_PREDICT, b));
@@ -353,7 +359,7 @@ int abm_step(lise_ctx* c) {
 }
 
 void free_ctx(lise_ctx* c) {
-  void* ptrs[] = {c->slot[0], c->slot[1], c->D[0], c->D[1], c->D[2], c->D[3], c->P, c->M, c->PC, c->TXY,
+  void* ptrs[] = {c->slot[0], c->slot[1], c->D[0], c->D[1], c->D[2], c->D[3], c->M, c->PC, c->Q, c->R, c->TXY,
                   c->part_n, c->part_nr, c->part_ni, c->dn[0], c->dn[1], c->dnu[0], c->dnu[1], c->W,
                   c->Dl, c->v_static, c->tw, c->hxy, c->hz, c->e_site, c->err};
   for (void* q : ptrs)
@@ -451,9 +457,10 @@ int lise_create(const lise_params* p, lise_ctx** out) {
   alloc((void**)&c->slot[0], sb);
   alloc((void**)&c->slot[1], sb);
   for (int k = 0; k < 4; ++k) alloc((void**)&c->D[k], sb);
-  alloc((void**)&c->P, sb);
-  alloc((void**)&c->M, sb);
+  alloc(&c->M, (size_t)c->ns * (c->mixed ? sizeof(float2) : sizeof(double2)));
   alloc((void**)&c->PC, sb);
+  alloc((void**)&c->Q, sb);
+  alloc((void**)&c->R, sb);
   alloc(&c->TXY, (size_t)c->ns * (c->mixed ? sizeof(float2) : sizeof(double2)));
   const size_t pb = (size_t)c->n_groups * c->nxyz * sizeof(double);
   alloc((void**)&c->part_n, pb);
@@ -637,6 +644,96 @@ int lise_rhs(lise_ctx* c, const double* psi, double t, double* dpsi_out) {
   TRY(cu(cudaMemcpyAsync(dpsi_out, c->D[0], (size_t)c->ns * sizeof(double2), cudaMemcpyDeviceToHost, c->stream)));
   TRY(cu(cudaStreamSynchronize(c->stream)));
   return fetch_err(c);
+}
+
+// ---------------------------------------------------------------- checkpoint --
+namespace {
+struct CkptHeader {
+  char magic[8];        // "LISECKP1"
+  int N, n_qp, precision, y0_slot_unused;
+  double t, dt;
+  long long ns, nxyz;
+  char pad[8];
+};
+static_assert(sizeof(CkptHeader) == 64, "checkpoint header is 64 bytes");
+const int kCkptArrays = 10;
+
+void ckpt_arrays(lise_ctx* c, void* arr[kCkptArrays], size_t sz[kCkptArrays]) {
+  arr[0] = c->slot[c->y0_slot];
+  arr[1] = c->slot[1 - c->y0_slot];
+  for (int k = 0; k < 4; ++k) arr[2 + k] = c->D[k];
+  arr[6] = c->M;
+  arr[7] = c->PC;
+  arr[8] = c->Q;
+  arr[9] = c->R;
+  for (int k = 0; k < kCkptArrays; ++k) sz[k] = (size_t)c->ns * sizeof(double2);
+  sz[6] = (size_t)c->ns * (c->mixed ? sizeof(float2) : sizeof(double2));
+}
+}  // namespace
+
+size_t lise_checkpoint_bytes(const lise_ctx* c) {
+  if (!c) return 0;
+  return sizeof(CkptHeader) + (kCkptArrays - 1) * (size_t)c->ns * sizeof(double2) +
+         (size_t)c->ns * (c->mixed ? sizeof(float2) : sizeof(double2)) +
+         (size_t)c->nxyz * (sizeof(double) + sizeof(double2));
+}
+
+int lise_checkpoint_save(lise_ctx* c, void* buf, size_t bytes) {
+  if (!c || !buf) return LISE_EINVAL;
+  if (!c->ready) return LISE_ESTATE;
+  if (bytes < lise_checkpoint_bytes(c)) return LISE_EINVAL;
+  TRY(fetch_err(c));
+  CkptHeader hd;
+  std::memset(&hd, 0, sizeof(hd));
+  std::memcpy(hd.magic, "LISECKP1", 8);
+  hd.N = c->N;
+  hd.n_qp = c->p.n_qp;
+  hd.precision = c->p.precision;
+  hd.t = c->t;
+  hd.dt = c->dt;
+  hd.ns = c->ns;
+  hd.nxyz = c->nxyz;
+  char* out = static_cast<char*>(buf);
+  std::memcpy(out, &hd, sizeof(hd));
+  size_t off = sizeof(hd);
+  void* arr[kCkptArrays];
+  size_t sz[kCkptArrays];
+  ckpt_arrays(c, arr, sz);
+  for (int k = 0; k < kCkptArrays; off += sz[k], ++k)
+    TRY(cu(cudaMemcpyAsync(out + off, arr[k], sz[k], cudaMemcpyDeviceToHost, c->stream)));
+  TRY(cu(cudaMemcpyAsync(out + off, c->W, c->nxyz * sizeof(double), cudaMemcpyDeviceToHost, c->stream)));
+  off += c->nxyz * sizeof(double);
+  TRY(cu(cudaMemcpyAsync(out + off, c->Dl, c->nxyz * sizeof(double2), cudaMemcpyDeviceToHost, c->stream)));
+  return cu(cudaStreamSynchronize(c->stream));
+}
+
+int lise_checkpoint_load(lise_ctx* c, const void* buf, size_t bytes) {
+  if (!c || !buf) return LISE_EINVAL;
+  if (c->sticky) return c->sticky;
+  if (bytes < lise_checkpoint_bytes(c)) return LISE_EINVAL;
+  CkptHeader hd;
+  std::memcpy(&hd, buf, sizeof(hd));
+  if (std::memcmp(hd.magic, "LISECKP1", 8) != 0 || hd.N != c->N || hd.n_qp != c->p.n_qp ||
+      hd.precision != c->p.precision || hd.ns != c->ns || hd.nxyz != c->nxyz || !(hd.dt != 0.0))
+    return LISE_EINVAL;
+  if (cudaSetDevice(c->device) != cudaSuccess) return LISE_ECUDA;
+  c->ready = 0;
+  c->y0_slot = 0;
+  void* arr[kCkptArrays];
+  size_t sz[kCkptArrays];
+  ckpt_arrays(c, arr, sz);
+  const char* in = static_cast<const char*>(buf);
+  size_t off = sizeof(hd);
+  for (int k = 0; k < kCkptArrays; off += sz[k], ++k)
+    TRY(cu(cudaMemcpyAsync(arr[k], in + off, sz[k], cudaMemcpyHostToDevice, c->stream)));
+  TRY(cu(cudaMemcpyAsync(c->W, in + off, c->nxyz * sizeof(double), cudaMemcpyHostToDevice, c->stream)));
+  off += c->nxyz * sizeof(double);
+  TRY(cu(cudaMemcpyAsync(c->Dl, in + off, c->nxyz * sizeof(double2), cudaMemcpyHostToDevice, c->stream)));
+  TRY(cu(cudaStreamSynchronize(c->stream)));
+  c->t = hd.t;
+  c->dt = hd.dt;
+  c->ready = 1;
+  return LISE_OK;
 }
 
 int lise_profile(lise_ctx* c, int enable) {

@@ -6,13 +6,51 @@
 
 namespace lise {
 
+// binary64 <-> binary32 conversions done with integer operations on the bit
+// patterns (IEEE 754 layouts), so that they do not occupy the FP64 pipe, which
+// on this GPU runs at 1/64 of the FP32 rate and also executes F2F.
+// Round to nearest even; results below the binary32 normal range flush to a
+// signed zero (the path's values are many orders of magnitude above it).
+__device__ __forceinline__ float d2f_bits(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7FFu);
+  const unsigned m = ((hi & 0xFFFFFu) << 3) | (lo >> 29);   // top 23 fraction bits
+  const unsigned rest = lo & 0x1FFFFFFFu;                     // 29 bits below them
+  const int fe = e - 896;                                     // rebias 1023 -> 127
+  unsigned r = ((unsigned)fe << 23) + m;
+  r += (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ? 1u : 0u;  // carries into the exponent
+  if (fe <= 0) r = 0u;
+  if (fe >= 255) r = (e == 0x7FF && ((hi & 0xFFFFFu) | lo)) ? 0x7FC00000u : 0x7F800000u;
+  return __uint_as_float(sign | r);
+}
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned sign = b & 0x80000000u;
+  const unsigned e = (b >> 23) & 0xFFu;
+  const unsigned m = b & 0x7FFFFFu;
+  unsigned hi, lo;
+  if (e == 0u) {  // zero (binary32 subnormals flush to zero)
+    hi = sign;
+    lo = 0u;
+  } else if (e == 0xFFu) {
+    hi = sign | 0x7FF00000u | (m >> 3) | (m ? 0x80000u : 0u);
+    lo = m << 29;
+  } else {
+    hi = sign | ((e + 896u) << 20) | (m >> 3);
+    lo = m << 29;
+  }
+  return __hiloint2double((int)hi, (int)lo);
+}
+
 template <typename R> __device__ __forceinline__ typename Cx<R>::T to_r(double2 v);
 template <> __device__ __forceinline__ double2 to_r<double>(double2 v) { return v; }
 template <> __device__ __forceinline__ float2 to_r<float>(double2 v) {
-  return make_float2((float)v.x, (float)v.y);
+  return make_float2(d2f_bits(v.x), d2f_bits(v.y));
 }
 __device__ __forceinline__ double2 to_d(double2 v) { return v; }
-__device__ __forceinline__ double2 to_d(float2 v) { return make_double2((double)v.x, (double)v.y); }
+__device__ __forceinline__ double2 to_d(float2 v) { return make_double2(f2d_bits(v.x), f2d_bits(v.y)); }
 
 __device__ __forceinline__ double2 dadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double2 dsub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
@@ -51,9 +89,11 @@ __global__ void __launch_bounds__(NT) k_planes(PlanesArgs a) {
   const long left = a.n_planes - plane0;
   const int np = left < PB ? (int)left : PB;
   const double2* src = a.x + plane0 * N * N;
+  const T* srcr = a.xr ? reinterpret_cast<const T*>(a.xr) + plane0 * N * N : nullptr;
   for (int i = threadIdx.x; i < PB * N * N; i += NT) {
     int pl = i / (N * N), r = i % (N * N);
-    T v = pl < np ? to_r<R>(src[i]) : T{R(0), R(0)};
+    T v = T{R(0), R(0)};
+    if (pl < np) v = srcr ? srcr[i] : to_r<R>(src[i]);
     buf[pl * PS + (r / N) * NP + (r % N)] = v;
   }
   __syncthreads();
@@ -76,10 +116,12 @@ __global__ void __launch_bounds__(NT) k_planes(PlanesArgs a) {
 
 // ----------------------------------------------------------------- pencils --
 template <typename R, int N, int TX, int QB, int MODE>
-__global__ void __launch_bounds__(N * TX) k_pencils(PencilArgs a) {
+__global__ void __launch_bounds__(N * TX, (sizeof(R) == 4 && N * TX >= 384) ? 2 : 1) k_pencils(PencilArgs a) {
   using T = typename Cx<R>::T;
   constexpr int NT = N * TX;
-  constexpr int CS = N * TX;           // one component block [z][x] in shared memory
+  // one component block [z][x] in shared memory; for 8-byte elements the blocks are
+  // padded by 64 bytes so the four blocks a warp touches fall on different banks
+  constexpr int CS = N * TX + (sizeof(T) == 8 ? 8 : 0);
   constexpr int LINES = QB * 2 * TX;   // z-lines per batch
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* buf = reinterpret_cast<T*>(smem_raw);  // [QB][2][N][TX]
@@ -107,20 +149,23 @@ __global__ void __launch_bounds__(N * TX) k_pencils(PencilArgs a) {
     Dv = a.D[site];
   }
   const T* txy = reinterpret_cast<const T*>(a.txy);
+  const R Wr = (R)Wv;
+  const T Dr = to_r<R>(Dv);
   double sn = 0.0, sr = 0.0, si = 0.0;
   auto base = [](int l) { return (l / TX) * CS + (l % TX); };
   __syncthreads();
 
   for (int qb0 = q_begin; qb0 < q_end; qb0 += QB) {
-    double2 xv[QB][2];
+    T xr[QB][2];  // the operand in compute precision (FP64 values are reloaded where needed)
 #pragma unroll
     for (int j = 0; j < QB; ++j) {
       const int q = qb0 + j;
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
-        double2 v = q < q_end ? a.x[(long)(2 * q + c) * nxyz + site] : make_double2(0.0, 0.0);
-        xv[j][c] = v;
-        buf[(2 * j + c) * CS + z * TX + xl] = to_r<R>(v);
+        const long gi = (long)(2 * q + c) * nxyz + site;
+        const T v = q < q_end ? (a.xr ? reinterpret_cast<const T*>(a.xr)[gi] : to_r<R>(a.x[gi])) : T{R(0), R(0)};
+        xr[j][c] = v;
+        buf[(2 * j + c) * CS + z * TX + xl] = v;
       }
     }
     __syncthreads();
@@ -138,17 +183,18 @@ __global__ void __launch_bounds__(N * TX) k_pencils(PencilArgs a) {
       const T Tu = cadd(buf[(2 * j) * CS + z * TX + xl], txy[iu]);
       const T Tv = cadd(buf[(2 * j + 1) * CS + z * TX + xl], txy[iv]);
       if (MODE == M_ENERGY) {
-        const double2 v = xv[j][1];
+        const double2 v = a.x[iv];
         const double2 tv = to_d(Tv);
         sn += 2.0 * (v.x * tv.x + v.y * tv.y);
         continue;
       }
       // H x = [[h, Delta], [Delta*, -h*]] x with h = T + W (W real, T real-symmetric)
-      const T u = to_r<R>(xv[j][0]), v = to_r<R>(xv[j][1]);
-      const R w = (R)Wv;
-      const T d = to_r<R>(Dv);
+      const T u = xr[j][0], v = xr[j][1];
+      const R w = Wr;
+      const T d = Dr;
       const T hu = T{Tu.x + w * u.x + (d.x * v.x - d.y * v.y), Tu.y + w * u.y + (d.x * v.y + d.y * v.x)};
       const T hv = T{(d.x * u.x + d.y * u.y) - Tv.x - w * v.x, (d.x * u.y - d.y * u.x) - Tv.y - w * v.y};
+      const T fur = T{hu.y, -hu.x}, fvr = T{hv.y, -hv.x};  // -i H x, compute precision
       const double2 Hu = to_d(hu), Hv = to_d(hv);
       const double2 fu = make_double2(Hu.y, -Hu.x), fv = make_double2(Hv.y, -Hv.x);  // -i H x
 
@@ -163,8 +209,8 @@ __global__ void __launch_bounds__(N * TX) k_pencils(PencilArgs a) {
         const double2 tu = dmul(a.coef, Hu), tv = dmul(a.coef, Hv);
         a.out[iu] = tu;
         a.out[iv] = tv;
-        a.acc[iu] = dadd(xv[j][0], tu);
-        a.acc[iv] = dadd(xv[j][1], tv);
+        a.acc[iu] = dadd(a.x[iu], tu);
+        a.acc[iv] = dadd(a.x[iv], tv);
       } else if (MODE == M_TAYLOR) {
         const double2 tu = dmul(a.coef, Hu), tv = dmul(a.coef, Hv);
         a.out[iu] = tu;
@@ -174,39 +220,49 @@ __global__ void __launch_bounds__(N * TX) k_pencils(PencilArgs a) {
         a.acc[iv] = av;
         if (a.dens) dens_acc(au, av, sn, sr, si);
       } else if (MODE == M_CORRECT) {
-        // Eq. c and Eq. y
-        const double h48 = a.h / 48.0;
+        // Eq. c and Eq. y through Q, R:  y_{n+1} = Q + k1 m',  p - c = R - k2 m'
+        const R k2 = (R)(17.0 / 48.0 * a.h);
+        const R k1 = (R)(161.0 / 170.0 * 17.0 / 48.0 * a.h);
         double2 yo[2];
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
           const long i = c ? iv : iu;
-          const double2 f = c ? fv : fu;
-          const double2 half = dscale(dadd(a.y0[i], a.y1[i]), 0.5);
-          const double2 s = dadd(dadd(dscale(f, 17.0), dscale(a.d0[i], 51.0)), dadd(dscale(a.d1[i], 3.0), a.d2[i]));
-          const double2 cc = dadd(half, dscale(s, h48));
-          const double2 pmc = dsub(a.p[i], cc);
-          const double2 yn = dadd(cc, dscale(pmc, 9.0 / 170.0));
+          const T f = c ? fvr : fur;
+          const T rr = to_r<R>(a.r[i]);
+          const double2 yn = dadd(a.q[i], to_d(T{k1 * f.x, k1 * f.y}));
           a.ynew[i] = yn;
-          a.pc[i] = pmc;
+          a.pc[i] = to_d(T{rr.x - k2 * f.x, rr.y - k2 * f.y});
           yo[c] = yn;
         }
         dens_acc(yo[0], yo[1], sn, sr, si);
       } else if (MODE == M_DERIV_PREDICT) {
-        // y'_{n+1} and Eq. p, Eq. m of the next step
-        const double h48 = a.h / 48.0;
+        // y'_{n+1}; then Eq. p and Eq. m of step n+2 and that step's Q, R:
+        //   pt = h/48 (119 y'_{n+1} - 99 y'_n + 69 y'_{n-1} - 17 y'_{n-2})
+        //   ct = h/48 (51 y'_{n+1} + 3 y'_n + y'_{n-1}),  hf = (y_{n+1} + y_n)/2
+        //   m = hf + pt - (161/170) pc,  Q = hf + (161/170) ct + (9/170) pt,  R = pt - ct.
+        // The derivative combinations run in the compute precision (FP32 in the
+        // mixed path, whose y' are FP32-accurate); every sum with a state value is FP64.
+        const R h48 = (R)(a.h / 48.0);
+        const R c161 = (R)(161.0 / 170.0), c9 = (R)(9.0 / 170.0);
         double2 mo[2];
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
           const long i = c ? iv : iu;
-          const double2 f = c ? fv : fu;
-          a.dslot[i] = f;
-          const double2 half = dscale(dadd(xv[j][c], a.y0[i]), 0.5);
-          const double2 s = dadd(dsub(dscale(f, 119.0), dscale(a.d0[i], 99.0)),
-                                 dsub(dscale(a.d1[i], 69.0), dscale(a.d2[i], 17.0)));
-          const double2 pn = dadd(half, dscale(s, h48));
-          const double2 mv = dsub(pn, dscale(a.pc[i], 161.0 / 170.0));
-          a.p[i] = pn;
-          a.m[i] = mv;
+          const T f = c ? fvr : fur;
+          a.dslot[i] = c ? fv : fu;
+          const T e0 = to_r<R>(a.d0[i]), e1 = to_r<R>(a.d1[i]), e2 = to_r<R>(a.d2[i]);
+          const T pcv = to_r<R>(a.pc[i]);
+          const T pt = T{h48 * (R(119) * f.x - R(99) * e0.x + R(69) * e1.x - R(17) * e2.x),
+                         h48 * (R(119) * f.y - R(99) * e0.y + R(69) * e1.y - R(17) * e2.y)};
+          const T ct = T{h48 * (R(51) * f.x + R(3) * e0.x + e1.x), h48 * (R(51) * f.y + R(3) * e0.y + e1.y)};
+          const T X = T{pt.x - c161 * pcv.x, pt.y - c161 * pcv.y};
+          const T Y = T{c161 * ct.x + c9 * pt.x, c161 * ct.y + c9 * pt.y};
+          const T Rv = T{pt.x - ct.x, pt.y - ct.y};
+          const double2 hf = dscale(dadd(a.x[i], a.y0[i]), 0.5);
+          const double2 mv = dadd(hf, to_d(X));
+          reinterpret_cast<T*>(a.m)[i] = to_r<R>(mv);
+          a.q[i] = dadd(hf, to_d(Y));
+          a.r[i] = to_d(Rv);
           mo[c] = mv;
         }
         dens_acc(mo[0], mo[1], sn, sr, si);
@@ -267,25 +323,31 @@ __global__ void k_reduce(ReduceArgs a) {
 }
 
 // --------------------------------------------------------------- pointwise --
-// First ABM step after the start procedure: Eq. p and Eq. m, densities of m.
+// First ABM step after the start procedure: Eq. p and Eq. m, the corrector's
+// Q, R (see lise_kernels.cuh), densities of m.  FP64 in both paths.
 __global__ void k_predict(PointwiseArgs a) {
   const long s = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= a.nxyz) return;
   const int g = blockIdx.y;
   const int q_begin = g * a.qg, q_end = min(a.n_qp, q_begin + a.qg);
   const double h48 = a.h / 48.0;
+  const double c161 = 161.0 / 170.0, c9 = 9.0 / 170.0;
   double sn = 0, sr = 0, si = 0;
   for (int q = q_begin; q < q_end; ++q) {
     double2 mo[2];
     for (int c = 0; c < 2; ++c) {
       const long i = (long)(2 * q + c) * a.nxyz + s;
-      const double2 half = dscale(dadd(a.y0[i], a.y1[i]), 0.5);
-      const double2 sm = dadd(dsub(dscale(a.d0[i], 119.0), dscale(a.d1[i], 99.0)),
-                              dsub(dscale(a.d2[i], 69.0), dscale(a.d3[i], 17.0)));
-      const double2 pn = dadd(half, dscale(sm, h48));
-      const double2 mv = dsub(pn, dscale(a.pc[i], 161.0 / 170.0));
-      a.p[i] = pn;
-      a.m[i] = mv;
+      const double2 hf = dscale(dadd(a.y0[i], a.y1[i]), 0.5);
+      const double2 pt = dscale(dadd(dsub(dscale(a.d0[i], 119.0), dscale(a.d1[i], 99.0)),
+                                     dsub(dscale(a.d2[i], 69.0), dscale(a.d3[i], 17.0))), h48);
+      const double2 ct = dscale(dadd(dadd(dscale(a.d0[i], 51.0), dscale(a.d1[i], 3.0)), a.d2[i]), h48);
+      const double2 mv = dadd(hf, dsub(pt, dscale(a.pc[i], c161)));
+      if (a.mixed)
+        reinterpret_cast<float2*>(a.m)[i] = to_r<float>(mv);
+      else
+        reinterpret_cast<double2*>(a.m)[i] = mv;
+      a.q[i] = dadd(hf, dadd(dscale(ct, c161), dscale(pt, c9)));
+      a.r[i] = dsub(pt, ct);
       mo[c] = mv;
     }
     dens_acc(mo[0], mo[1], sn, sr, si);
@@ -354,7 +416,7 @@ bool supported_n(int N) {
   }
 }
 int pencil_tx(int N) { return N % 8 == 0 ? 8 : 4; }
-int pencil_qb(int, int) { return 4; }
+int pencil_qb(int N, int) { return N >= 40 ? 2 : 4; }
 
 template <typename R, int N>
 static int planes_n(const PlanesArgs& a, cudaStream_t s) {
@@ -378,8 +440,9 @@ template <typename R, int N, int MODE>
 static int pencils_nm(const PencilArgs& a, cudaStream_t s) {
   using T = typename Cx<R>::T;
   constexpr int TX = (N % 8 == 0) ? 8 : 4;
-  constexpr int QB = 4;
-  const size_t smem = (size_t)QB * 2 * N * TX * sizeof(T) + N * sizeof(T) + N * sizeof(R);
+  constexpr int QB = (N >= 40) ? 2 : 4;  // states per batch; fewer at large N to bound registers
+  constexpr int CS = N * TX + (sizeof(T) == 8 ? 8 : 0);
+  const size_t smem = (size_t)QB * 2 * CS * sizeof(T) + N * sizeof(T) + N * sizeof(R);
   auto kern = k_pencils<R, N, TX, QB, MODE>;
   static bool attr = false;
   if (!attr) {

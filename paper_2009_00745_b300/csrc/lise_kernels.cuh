@@ -24,14 +24,16 @@ enum PencilMode : int {
   M_RHS = 0,            // out = -i H x
   M_TAYLOR_FIRST = 1,   // h = H x; [dslot = -i h]; term = coef h -> out; acc = x + term
   M_TAYLOR = 2,         // term = coef H x -> out (in place); acc += term; [densities of acc]
-  M_CORRECT = 3,        // m' = -i H m; Eq. c, Eq. y -> ynew, pc; densities of ynew
-  M_DERIV_PREDICT = 4,  // d = -i H y_{n+1} -> dslot; Eq. p, Eq. m for the next step -> p, m;
-                        // densities of m
+  M_CORRECT = 3,        // m' = -i H m; Eq. c and Eq. y through Q, R -> ynew, pc; densities of ynew
+  M_DERIV_PREDICT = 4,  // d = -i H y_{n+1} -> dslot; Eq. p, Eq. m of the next step -> m, and
+                        // the corrector's precombined Q, R; densities of m
   M_ENERGY = 5,         // part_n += sum_q 2 Re(conj(v) T v)
 };
 
 struct PencilArgs {
-  const double2* x;       // operand state [q][c][z][y][x]
+  const double2* x;       // operand state [q][c][z][y][x] (complex128), unless xr is set
+  const void* xr;         // if non-null: the operand stored in the compute precision
+                          // (the modifier m of the mixed path); x is then unused
   const void* txy;        // T_xy x, complex of the compute precision
   const double* W;        // h - T = U(n) - mu + V_ext  [site]
   const double2* D;       // Delta [site]
@@ -49,9 +51,10 @@ struct PencilArgs {
   const double2* d0;      // y'_n
   const double2* d1;      // y'_{n-1}
   const double2* d2;      // y'_{n-2}
-  double2* p;             // p_{n+1} (read in M_CORRECT, written in M_DERIV_PREDICT)
+  double2* q;             // Q (read in M_CORRECT, written in M_DERIV_PREDICT), see below
+  double2* r;             // R (likewise)
   double2* pc;            // p - c (written in M_CORRECT, read in M_DERIV_PREDICT)
-  double2* m;             // m (written in M_DERIV_PREDICT)
+  void* m;                // m in the compute precision (written in M_DERIV_PREDICT)
   double2* ynew;          // y_{n+1} (written in M_CORRECT; may alias y1)
   double* part_n;         // [group][site] partial sums
   double* part_nr;
@@ -60,7 +63,8 @@ struct PencilArgs {
 };
 
 struct PlanesArgs {
-  const double2* x;       // operand state, n_planes consecutive N x N planes
+  const double2* x;       // operand state, n_planes consecutive N x N planes (complex128)
+  const void* xr;         // or, if non-null, the operand in the compute precision
   void* txy;              // output T_xy x
   const void* tw;         // forward twiddles, N entries
   const void* hxy;        // (alpha/2) k^2 / N^2, N entries
@@ -90,7 +94,9 @@ struct ReduceArgs {
 struct PointwiseArgs {
   // predictor + modifier for the first ABM step: p = Eq. p, m = Eq. m
   const double2 *y0, *y1, *d0, *d1, *d2, *d3, *pc;
-  double2 *p, *m;
+  double2 *q, *r;
+  void* m;                // m in the compute precision of the path
+  int mixed;
   double h;
   // density partials of `src` (for the plain density pass) or of m
   const double2* src;
@@ -100,6 +106,14 @@ struct PointwiseArgs {
   int n_qp, qg;
   long nxyz;
 };
+
+// The corrector of Eq. c splits as c_{n+1} = cbase_{n+1} + (17 h/48) m'_{n+1} with
+//   cbase_{n+1} = (y_n + y_{n-1})/2 + h/48 (51 y'_n + 3 y'_{n-1} + y'_{n-2}),
+// which depends only on the history known at predictor time.  With
+//   Q = (161/170) cbase + (9/170) p_{n+1},   R = p_{n+1} - cbase,
+// Eq. y becomes y_{n+1} = Q + (161/170)(17 h/48) m'_{n+1} and
+// p_{n+1} - c_{n+1} = R - (17 h/48) m'_{n+1} (algebraically identical to Eqs. c, y).
+// Q and R are formed with the predictor, so the corrector reads 2 arrays, not 6.
 
 // Host-side launchers (defined in lise_kernels.cu).
 int launch_planes(int N, int mixed, const PlanesArgs& a, cudaStream_t s);

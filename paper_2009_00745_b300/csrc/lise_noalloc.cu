@@ -164,6 +164,7 @@ extern "C" int lise_rhs_noalloc(const lise_params* p, const double* psi_dev, dou
   // T_xy psi, then z-pencils with the BdG apply: dpsi = -i H psi
   PlanesArgs pa;
   pa.x = x;
+  pa.xr = nullptr;
   pa.txy = base + o_txy;
   pa.tw = tw;
   pa.hxy = hxy;

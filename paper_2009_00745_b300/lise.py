@@ -56,6 +56,9 @@ SIGNATURES = {
     "lise_strerror": (C.c_char_p, [C.c_int]),
     "lise_destroy": (None, [C.c_void_p]),
     "lise_rhs_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_void_p]),
+    "lise_checkpoint_bytes": (C.c_size_t, [C.c_void_p]),
+    "lise_checkpoint_save": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "lise_checkpoint_load": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
 }
 
 _lib = None
@@ -217,6 +220,19 @@ class Context:
             _check(load().lise_profile_read(self._h, k, C.byref(n), C.byref(ms)), "lise_profile_read")
             out[load().lise_kernel_class_name(k).decode()] = (n.value, ms.value)
         return out
+
+    def checkpoint(self):
+        """The full ABM history as bytes (a bit-exact restart point)."""
+        n = int(load().lise_checkpoint_bytes(self._h))
+        buf = np.empty(n, dtype=np.uint8)
+        _check(load().lise_checkpoint_save(self._h, buf.ctypes.data, n), "lise_checkpoint_save")
+        return buf
+
+    def restore(self, buf):
+        """Load a checkpoint taken from a context with the same lattice, states and precision."""
+        b = np.ascontiguousarray(buf, dtype=np.uint8)
+        _check(load().lise_checkpoint_load(self._h, b.ctypes.data, b.size), "lise_checkpoint_load")
+        self.dt = float(np.frombuffer(b[32:40].tobytes(), dtype=np.float64)[0])  # header: t at 24, dt at 32
 
     def sync(self):
         _check(load().lise_sync(self._h), "lise_sync")

@@ -204,3 +204,63 @@ def test_deterministic_bitwise():
     b = run_gpu(w, 5)
     assert np.array_equal(a[0], b[0])
     assert np.array_equal(a[1], b[1])
+
+
+# ------------------------------------------------------------ checkpoint ----
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_checkpoint_bit_exact_resume(precision):
+    w = W.ufg_plane_waves(16, 20, noise_eps=0.05)
+    with L.Context.from_workload(w, precision=precision) as a:
+        a.set_state(w.initial_state(), 0.0, w.dt)
+        a.step(10)
+        ref, t_ref = a.state(), a.t
+    with L.Context.from_workload(w, precision=precision) as b:
+        b.set_state(w.initial_state(), 0.0, w.dt)
+        b.step(4)
+        ck = b.checkpoint()
+        b.step(6)
+        assert np.array_equal(b.state(), ref)
+    with L.Context.from_workload(w, precision=precision) as c:
+        c.restore(ck)
+        c.step(6)
+        assert c.t == t_ref
+        assert np.array_equal(c.state(), ref)
+
+
+def test_checkpoint_rejects_other_shapes():
+    w = W.ufg_plane_waves(8, 6)
+    with L.Context.from_workload(w) as a:
+        with pytest.raises(L.LiseError) as e:
+            a.checkpoint()
+        assert e.value.status == L.ESTATE
+        a.set_state(w.initial_state(), 0.0, w.dt)
+        ck = a.checkpoint()
+    w2 = W.ufg_plane_waves(8, 7)
+    with L.Context.from_workload(w2) as b:
+        with pytest.raises(L.LiseError) as e:
+            b.restore(np.concatenate([ck, np.zeros(1 << 16, np.uint8)]))
+        assert e.value.status == L.EINVAL
+    with L.Context.from_workload(w, precision="mixed") as b:
+        with pytest.raises(L.LiseError) as e:
+            b.restore(ck)
+        assert e.value.status == L.EINVAL
+
+
+# ------------------------------------------------------ mixed energy drift ----
+
+def test_mixed_energy_drift_vs_fp64():
+    # the driven 48^3 workload with 32 states, 400 steps: the mixed path's energy stays
+    # within 1e-6 (relative) of the FP64 trajectory at every sample
+    w = W.driven(48, 32, steps=400)
+    E = {}
+    for prec in ("fp64", "mixed"):
+        with L.Context.from_workload(w, precision=prec) as ctx:
+            ctx.set_state(w.initial_state(), 0.0, w.dt)
+            e = [ctx.energy()[0]]
+            for _ in range(8):
+                ctx.step(50)
+                e.append(ctx.energy()[0])
+            E[prec] = np.array(e)
+    dev = np.max(np.abs(E["mixed"] - E["fp64"]) / np.abs(E["fp64"]))
+    assert dev < 1e-6, dev

@@ -264,6 +264,62 @@ def run_drift(args, w):
     return 0
 
 
+def run_serve(args):
+    """A Poisson stream of evolution requests through the serving loop.
+
+    Requests arrive at --serve-rate per second (exponential gaps, seed 11); each
+    draws a lattice from {16, 24, 32, 48}^3 and a state count uniform in
+    [256, 4096], and runs 100 mixed-precision ABM steps; the server admits them
+    under a 150 GB budget.  Each request evolves the first n_qp states of its
+    lattice's 4096-state homogeneous BCS workload (built before the clock starts).
+    Latency = done - arrival (arrival = the scheduled Poisson time)."""
+    import numpy as np
+    from paper_2009_00745_b300 import lise as L
+    from paper_2009_00745_b300 import workloads as Wl
+    rng = np.random.default_rng(11)
+    R = args.serve_requests
+    gaps = rng.exponential(1.0 / args.serve_rate, R)
+    arrivals = np.cumsum(gaps) - gaps[0]
+    lattices = rng.choice([16, 24, 32, 48], R)
+    nqps = rng.integers(256, 4097, R)
+    base = {}
+    for n in sorted(set(int(x) for x in lattices)):
+        w = Wl.ufg_plane_waves(n, 4096, noise_eps=1e-3, precision="mixed", steps=args.serve_steps)
+        base[n] = (w, w.initial_state())
+    budget = int(args.serve_budget_gb * 1e9)
+    lag, sub_host, ids = [], [], []
+    with L.Server(budget, max_active=args.serve_max_active, steps_per_turn=args.serve_turn) as srv:
+        t0 = time.perf_counter()
+        for i in range(R):
+            delay = t0 + arrivals[i] - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            w, psi = base[int(lattices[i])]
+            n_qp = int(nqps[i])
+            ts = time.perf_counter()
+            lag.append(ts - (t0 + arrivals[i]))
+            ids.append(srv.submit(w.nx, n_qp, psi[:n_qp], 0.0, w.dt, args.serve_steps, a=w.a, alpha=w.alpha,
+                                  beta=w.beta, mu=w.mu, g=w.g, precision="mixed"))
+        infos = [srv.wait(i, want_state=False)[1] for i in ids]
+        st = srv.stats()
+    lat = np.array([inf["done_s"] - inf["submit_s"] + lg for inf, lg in zip(infos, lag)])
+    queue = np.array([inf["admit_s"] - inf["submit_s"] + lg for inf, lg in zip(infos, lag)])
+    units = sum(float(n) * int(l) ** 3 * args.serve_steps for n, l in zip(nqps, lattices))
+    makespan = max(inf["done_s"] for inf in infos) - min(inf["submit_s"] for inf in infos)
+    line = {"mode": "serve", "requests": R, "rate_per_s": args.serve_rate, "steps_per_request": args.serve_steps,
+            "precision": "mixed", "hbm_budget_gb": args.serve_budget_gb, "max_active": args.serve_max_active,
+            "steps_per_turn": args.serve_turn,
+            "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                          "mean": float(lat.mean()), "max": float(lat.max())},
+            "queue_wait_s": {"p50": float(np.percentile(queue, 50)), "mean": float(queue.mean())},
+            "throughput": units / makespan, "unit": UNIT, "makespan_s": makespan,
+            "peak_used_gb": st["peak_used_bytes"] / 1e9, "peak_active": st["peak_active"],
+            "all_ok": all(inf["status"] == 0 for inf in infos),
+            "mix": {"lattices": [int(x) for x in lattices], "n_qp": [int(x) for x in nqps]}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def config_of(w, args):
     return {"workload": w.name, "lattice": f"{w.nx}^3", "n_qp": w.n_qp, "dt": w.dt,
             "precision": w.precision, "steps_in_workload": w.steps,
@@ -286,6 +342,13 @@ def main():
     ap.add_argument("--drift", action="store_true",
                     help="compare mixed with FP64 over --steps steps instead of timing")
     ap.add_argument("--drift-every", type=int, default=50)
+    ap.add_argument("--serve", action="store_true", help="run a Poisson request stream through the server")
+    ap.add_argument("--serve-requests", type=int, default=16)
+    ap.add_argument("--serve-rate", type=float, default=20.0)
+    ap.add_argument("--serve-steps", type=int, default=100)
+    ap.add_argument("--serve-budget-gb", type=float, default=150.0)
+    ap.add_argument("--serve-max-active", type=int, default=8)
+    ap.add_argument("--serve-turn", type=int, default=5)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -299,6 +362,8 @@ def main():
         return run_reference(args, w)
     if args.drift:
         return run_drift(args, w)
+    if args.serve:
+        return run_serve(args)
 
     import numpy as np
     import torch

@@ -75,6 +75,9 @@ typedef struct {
   size_t hbm_budget_bytes;  /* 0 = no limit; otherwise lise_create fails with LISE_ENOMEM
                                (allocating nothing) if the footprint exceeds it */
   void *stream;             /* cudaStream_t to enqueue on, or NULL for a stream owned by the context */
+  int remove_phase;         /* 1: evolve i dpsi_k/dt = (H - eta_k) psi_k with eta_k = <psi_k|H|psi_k>
+                               (trivial-phase removal, Eq. sp_en), in the right-hand sides and the
+                               series start (eta_k of the step's starting state); 0: plain Eq. tdslda */
 } lise_params;
 
 /* Device bytes lise_create would allocate for these parameters (0 if invalid). */
@@ -133,6 +136,41 @@ int lise_checkpoint_save(lise_ctx *c, void *buf, size_t bytes);
 /* The checkpoint must come from a context with the same lattice, state count
  * and precision (else LISE_EINVAL); the physical parameters are the context's. */
 int lise_checkpoint_load(lise_ctx *c, const void *buf, size_t bytes);
+
+/* Serving: a request loop over one GPU.  Each request is an independent
+ * evolution (parameters, initial state on the host, n_steps ABM steps).  A
+ * worker thread admits queued requests in arrival order while the sum of their
+ * footprints (lise_footprint_bytes) stays within hbm_budget_bytes and fewer
+ * than max_active run; each admitted request keeps its state and ABM history
+ * resident in its own context and stream; the worker enqueues steps_per_turn
+ * steps at a time for every active request whose previous chunk finished, so
+ * the work of different requests overlaps on the GPU.  A request's result does
+ * not depend on what else runs (same deterministic kernels, own buffers). */
+typedef struct lise_server lise_server;
+typedef struct {
+  int status;       /* LISE_OK, or the error that ended the request */
+  double submit_s;  /* seconds since lise_server_create when submitted, */
+  double admit_s;   /* admitted (context created, start procedure begun), */
+  double done_s;    /* and finished (final state copied back) */
+  double t;         /* final time of the evolution */
+  double E, N;      /* energy and particle number of the final state */
+} lise_request_info;
+/* max_active >= 1, steps_per_turn >= 1, hbm_budget_bytes > 0. */
+int lise_server_create(int device, size_t hbm_budget_bytes, int max_active, int steps_per_turn,
+                       lise_server **out);
+/* Copies psi (host, layout above) and queues the request; returns at once with
+ * its id.  p->device, p->hbm_budget_bytes and p->stream are ignored (the server
+ * sets them).  LISE_ENOMEM if the request alone exceeds the budget. */
+int lise_server_submit(lise_server *s, const lise_params *p, const double *psi, double t0, double dt,
+                       int n_steps, long *id);
+/* Blocks until request id is done; copies its final state to psi_out (host;
+ * may be NULL) and its timings to info (may be NULL); forgets the request.
+ * Returns the request's status. */
+int lise_server_wait(lise_server *s, long id, double *psi_out, lise_request_info *info);
+/* Largest sum of admitted footprints and largest number of active requests seen. */
+int lise_server_stats(lise_server *s, size_t *peak_used_bytes, int *peak_active);
+/* Finishes every submitted request, stops the worker and frees the server. */
+void lise_server_destroy(lise_server *s);
 
 /* Per-launch timing.  Kernel classes of the path: */
 #define LISE_KC_PLANES 0    /* in-plane 2D FFT -> kinetic multiply -> inverse (T_xy) */

@@ -247,6 +247,24 @@ void or_apply_h(const or_params *p, const double *W, const double complex *Delta
   }
 }
 
+void or_eta(const or_params *p, const double complex *psi, const double complex *hpsi, double *eta) {
+  long nt = (long)p->nx * p->ny * p->nz;
+  double a3 = p->a * p->a * p->a;
+  for (int q = 0; q < p->n_qp; ++q) {
+    double s = 0, c = 0;
+    for (long i = (long)q * 2 * nt; i < (long)(q + 1) * 2 * nt; ++i) neumaier_add(&s, &c, creal(conj(psi[i]) * hpsi[i]));
+    eta[q] = a3 * (s + c);
+  }
+}
+
+/* hpsi_k -= eta_k psi_k for every state (the trivial-phase removal of Eq. sp_en) */
+static void subtract_eta(const or_params *p, const double *eta, const double complex *psi,
+                         double complex *hpsi) {
+  long nt = (long)p->nx * p->ny * p->nz;
+  for (int q = 0; q < p->n_qp; ++q)
+    for (long i = (long)q * 2 * nt; i < (long)(q + 1) * 2 * nt; ++i) hpsi[i] -= eta[q] * psi[i];
+}
+
 void or_rhs(const or_params *p, const double complex *psi, double t,
             double complex *dpsi) {
   long nt = (long)p->nx * p->ny * p->nz;
@@ -258,6 +276,12 @@ void or_rhs(const or_params *p, const double complex *psi, double t,
   or_densities(p, psi, n, nu);
   or_potentials(p, n, nu, t, W, D);
   or_apply_h(p, W, D, psi, dpsi);
+  if (p->remove_phase) {
+    double *eta = (double *)malloc(sizeof(double) * p->n_qp);
+    or_eta(p, psi, dpsi, eta);
+    subtract_eta(p, eta, psi, dpsi);
+    free(eta);
+  }
   for (long i = 0; i < ns; ++i) dpsi[i] *= -I; /* i dpsi/dt = H psi (hbar = 1) */
   free(n); free(W); free(nu); free(D);
 }
@@ -312,16 +336,26 @@ void or_destroy(or_solver *s) {
 static void taylor4(const or_params *p, const double *W, const double complex *D,
                     const double complex *psi, double dt, double complex *out,
                     double complex *term, double complex *hterm, long ns) {
+  /* with phase removal the generator of state k is H - eta_k, eta_k = <psi_k|H|psi_k>
+   * of the step's starting state and this series' Hamiltonian */
+  double *eta = NULL;
+  if (p->remove_phase) {
+    eta = (double *)malloc(sizeof(double) * p->n_qp);
+    or_apply_h(p, W, D, psi, hterm);
+    or_eta(p, psi, hterm, eta);
+  }
   memcpy(out, psi, sizeof(double complex) * ns);
   memcpy(term, psi, sizeof(double complex) * ns);
   for (int j = 1; j <= 4; ++j) {
     or_apply_h(p, W, D, term, hterm);
+    if (eta) subtract_eta(p, eta, term, hterm);
     double complex f = -I * dt / (double)j;
     for (long i = 0; i < ns; ++i) {
       term[i] = f * hterm[i];
       out[i] += term[i];
     }
   }
+  free(eta);
 }
 
 void or_series_step(const or_params *p, const double complex *psi, double t,

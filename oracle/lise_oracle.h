@@ -45,6 +45,7 @@ typedef struct {
   const double *v_static;  /* [nz][ny][nx] static external potential, or NULL */
   double drive_A;          /* V_ext += A sin(Omega t) z_c */
   double drive_Omega;
+  int remove_phase;        /* 1: i dpsi_k/dt = (H - eta_k) psi_k, eta_k = <psi_k|H|psi_k> (Eq. sp_en) */
 } or_params;
 
 /* 1D DFT of length n (any n >= 1), out-of-place, unnormalised.
@@ -78,7 +79,12 @@ void or_potentials(const or_params *p, const double *n, const double complex *nu
 void or_apply_h(const or_params *p, const double *W, const double complex *Delta,
                 const double complex *psi, double complex *hpsi);
 
-/* dpsi = f(t, psi) = -i H[psi](t) psi (potentials from the densities of psi). */
+/* eta_k = <psi_k|hpsi_k> = a^3 sum_r [conj(u) (H psi)_u + conj(v) (H psi)_v], real part
+ * (H is Hermitian), compensated sums; eta has n_qp entries. */
+void or_eta(const or_params *p, const double complex *psi, const double complex *hpsi, double *eta);
+
+/* dpsi = f(t, psi) = -i H[psi](t) psi (potentials from the densities of psi);
+ * with remove_phase, -i (H - eta_k) psi_k. */
 void or_rhs(const or_params *p, const double complex *psi, double t,
             double complex *dpsi);
 

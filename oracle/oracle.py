@@ -54,6 +54,7 @@ def lib():
         L.or_abm_modifier.argtypes = [C.c_long, vp, vp, vp]
         L.or_abm_corrector.argtypes = [C.c_long, d, vp, vp, vp, vp, vp, vp, vp]
         L.or_abm_final.argtypes = [C.c_long, vp, vp, vp, vp]
+        L.or_eta.argtypes = [vp, vp, vp, vp]
         _lib = L
     return _lib
 
@@ -62,30 +63,31 @@ class _Params(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("a", C.c_double),
                 ("n_qp", C.c_int), ("alpha", C.c_double), ("beta", C.c_double),
                 ("mu", C.c_double), ("g", C.c_double), ("v_static", C.c_void_p),
-                ("drive_A", C.c_double), ("drive_Omega", C.c_double)]
+                ("drive_A", C.c_double), ("drive_Omega", C.c_double), ("remove_phase", C.c_int)]
 
 
 class Params:
     """Physical and lattice parameters (ħ = m = 1)."""
 
     def __init__(self, nx, ny, nz, a=1.0, n_qp=1, alpha=1.0, beta=0.0, mu=0.0, g=0.0,
-                 v_static=None, drive_A=0.0, drive_Omega=0.0):
+                 v_static=None, drive_A=0.0, drive_Omega=0.0, remove_phase=False):
         self.nx, self.ny, self.nz, self.a, self.n_qp = int(nx), int(ny), int(nz), float(a), int(n_qp)
         self.alpha, self.beta, self.mu, self.g = float(alpha), float(beta), float(mu), float(g)
         self.v_static = None if v_static is None else np.ascontiguousarray(v_static, dtype=np.float64).reshape(nz, ny, nx)
         self.drive_A, self.drive_Omega = float(drive_A), float(drive_Omega)
+        self.remove_phase = bool(remove_phase)
 
     def with_(self, **kw):
         d = dict(nx=self.nx, ny=self.ny, nz=self.nz, a=self.a, n_qp=self.n_qp, alpha=self.alpha,
                  beta=self.beta, mu=self.mu, g=self.g, v_static=self.v_static,
-                 drive_A=self.drive_A, drive_Omega=self.drive_Omega)
+                 drive_A=self.drive_A, drive_Omega=self.drive_Omega, remove_phase=self.remove_phase)
         d.update(kw)
         return Params(**d)
 
     def _c(self):
         s = _Params(self.nx, self.ny, self.nz, self.a, self.n_qp, self.alpha, self.beta, self.mu,
                     self.g, None if self.v_static is None else self.v_static.ctypes.data,
-                    self.drive_A, self.drive_Omega)
+                    self.drive_A, self.drive_Omega, int(self.remove_phase))
         return s
 
     @property
@@ -172,6 +174,16 @@ def series_step(p: Params, psi, t, dt):
     out = np.empty_like(psi)
     ps = p._c()
     lib().or_series_step(C.byref(ps), psi.ctypes.data, float(t), float(dt), out.ctypes.data)
+    return out
+
+
+def eta(p: Params, psi, hpsi):
+    """eta_k = <psi_k|H psi_k> (real part), one value per state (Eq. sp_en)."""
+    psi = _c128(psi, p.shape)
+    hpsi = _c128(hpsi, p.shape)
+    out = np.empty(p.n_qp)
+    ps = p._c()
+    lib().or_eta(C.byref(ps), psi.ctypes.data, hpsi.ctypes.data, out.ctypes.data)
     return out
 
 

@@ -55,6 +55,10 @@ struct lise_ctx {
   int ready = 0;
   int sticky = LISE_OK;
   double* host_e = nullptr;
+  // trivial-phase removal: eta per state and its per-block partial sums
+  double* eta = nullptr;
+  double* eta_part = nullptr;
+  int n_blocks_x = 0;
   // per-launch timing (lise_profile)
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -104,6 +108,7 @@ Footprint footprint(const lise_params* p) {
   f.small = (size_t)nxyz * (2 * sizeof(double) + 2 * sizeof(double2) + sizeof(double) + sizeof(double2) +
                             sizeof(double) + 2 * sizeof(double)) +
             3 * (size_t)N * sizeof(double2) + 256;
+  if (p->remove_phase) f.small += (size_t)p->n_qp * (1 + pencil_blocks_x((int)N)) * sizeof(double);
   f.total = f.state + f.txy + f.partials + f.small;
   return f;
 }
@@ -152,6 +157,7 @@ PencilArgs pencil_base(const lise_ctx* c) {
   a.part_n = c->part_n;
   a.part_nr = c->part_nr;
   a.part_ni = c->part_ni;
+  a.eta = c->p.remove_phase ? c->eta : nullptr;
   return a;
 }
 
@@ -169,6 +175,22 @@ int run_planes(lise_ctx* c, const double2* x, const void* xr = nullptr) {
 int run_pencils(lise_ctx* c, int mode, const PencilArgs& a) {
   return timed(c, LISE_KC_PENCILS,
                [&] { return launch_pencils(c->N, c->mixed, mode, a, c->stream) ? LISE_ECUDA : LISE_OK; });
+}
+
+// eta_q = <x_q|H x_q> with the current potentials (T_xy x must be in the scratch);
+// a no-op without trivial-phase removal.
+int run_eta(lise_ctx* c, const double2* x, const void* xr = nullptr) {
+  if (!c->p.remove_phase) return LISE_OK;
+  PencilArgs a = pencil_base(c);
+  a.eta = nullptr;
+  a.x = x;
+  a.xr = xr;
+  a.eta_part = c->eta_part;
+  TRY(run_pencils(c, M_ETA, a));
+  const double a3 = c->p.dx * c->p.dx * c->p.dx;
+  return timed(c, LISE_KC_REDUCE, [&] {
+    return launch_eta_reduce(c->eta_part, c->p.n_qp, c->n_blocks_x, a3, c->eta, c->stream) ? LISE_ECUDA : LISE_OK;
+  });
 }
 
 // Reduce the density partials; optionally average with (avg_n, avg_nu); write
@@ -219,6 +241,7 @@ double2 cx(double re, double im) { return make_double2(re, im); }
 // start procedure fills only at its end.
 int taylor4(lise_ctx* c, const double2* psi_in, double2* psi_out, double2* dslot, double dt) {
   TRY(run_planes(c, psi_in));
+  TRY(run_eta(c, psi_in));  // eta of the starting state with this series' Hamiltonian
   PencilArgs a = pencil_base(c);
   a.x = psi_in;
   a.out = c->Q;
@@ -277,6 +300,7 @@ int start_procedure(lise_ctx* c, double t0, double dt) {
   }
   // cur = y_3, nxt = y_2; y'_3 = f(t_3, y_3) into D[0]
   TRY(run_planes(c, cur));
+  TRY(run_eta(c, cur));
   PencilArgs a = pencil_base(c);
   a.x = cur;
   a.out = c->D[0];
@@ -320,6 +344,7 @@ int abm_step(lise_ctx* c) {
   // RHS #1 on m_{n+1} (stored in the compute precision): Eq. c, Eq. y through Q, R;
   // y_{n+1} replaces y_{n-1}
   TRY(run_planes(c, nullptr, c->M));
+  TRY(run_eta(c, nullptr, c->M));
   PencilArgs a = pencil_base(c);
   a.xr = c->M;
   a.h = h;
@@ -332,6 +357,7 @@ int abm_step(lise_ctx* c) {
   TRY(run_reduce(c, 1, nullptr, nullptr, true, t1));
   // RHS #2 on y_{n+1}: y'_{n+1} into the y'_{n-3} slot, then Eq. p and Eq. m of step n+2
   TRY(run_planes(c, ynm1));
+  TRY(run_eta(c, ynm1));
   PencilArgs b = pencil_base(c);
   b.x = ynm1;
   b.h = h;
@@ -359,7 +385,7 @@ int abm_step(lise_ctx* c) {
 }
 
 void free_ctx(lise_ctx* c) {
-  void* ptrs[] = {c->slot[0], c->slot[1], c->D[0], c->D[1], c->D[2], c->D[3], c->M, c->PC, c->Q, c->R, c->TXY,
+  void* ptrs[] = {c->eta, c->eta_part, c->slot[0], c->slot[1], c->D[0], c->D[1], c->D[2], c->D[3], c->M, c->PC, c->Q, c->R, c->TXY,
                   c->part_n, c->part_nr, c->part_ni, c->dn[0], c->dn[1], c->dnu[0], c->dnu[1], c->W,
                   c->Dl, c->v_static, c->tw, c->hxy, c->hz, c->e_site, c->err};
   for (void* q : ptrs)
@@ -478,6 +504,11 @@ int lise_create(const lise_params* p, lise_ctx** out) {
   alloc(&c->hxy, c->N * rs);
   alloc(&c->hz, c->N * rs);
   alloc((void**)&c->e_site, 2 * c->nxyz * sizeof(double));
+  c->n_blocks_x = pencil_blocks_x(c->N);
+  if (p->remove_phase) {
+    alloc((void**)&c->eta, (size_t)p->n_qp * sizeof(double));
+    alloc((void**)&c->eta_part, (size_t)p->n_qp * c->n_blocks_x * sizeof(double));
+  }
   alloc((void**)&c->err, sizeof(int));
   c->host_e = (double*)std::malloc(2 * c->nxyz * sizeof(double));
   if (rc == LISE_OK && !c->host_e) rc = LISE_ENOMEM;
@@ -600,6 +631,7 @@ int lise_energy(lise_ctx* c, double* E, double* Nout) {
   TRY(run_reduce(c, 0, nullptr, nullptr, false, c->t));
   TRY(run_planes(c, y));
   PencilArgs a = pencil_base(c);
+  a.eta = nullptr;
   a.x = y;
   a.dens = 1;
   TRY(run_pencils(c, M_ENERGY, a));
@@ -637,6 +669,7 @@ int lise_rhs(lise_ctx* c, const double* psi, double t, double* dpsi_out) {
   TRY(run_density(c, x));
   TRY(run_reduce(c, 0, nullptr, nullptr, true, t));
   TRY(run_planes(c, x));
+  TRY(run_eta(c, x));
   PencilArgs a = pencil_base(c);
   a.x = x;
   a.out = c->D[0];

@@ -156,6 +156,9 @@ __global__ void __launch_bounds__(N * TX, (sizeof(R) == 4 && N * TX >= 384) ? 2 
   __syncthreads();
 
   for (int qb0 = q_begin; qb0 < q_end; qb0 += QB) {
+    double eta_acc[QB];
+#pragma unroll
+    for (int j = 0; j < QB; ++j) eta_acc[j] = 0.0;
     T xr[QB][2];  // the operand in compute precision (FP64 values are reloaded where needed)
 #pragma unroll
     for (int j = 0; j < QB; ++j) {
@@ -188,12 +191,19 @@ __global__ void __launch_bounds__(N * TX, (sizeof(R) == 4 && N * TX >= 384) ? 2 
         sn += 2.0 * (v.x * tv.x + v.y * tv.y);
         continue;
       }
-      // H x = [[h, Delta], [Delta*, -h*]] x with h = T + W (W real, T real-symmetric)
+      // H x = [[h, Delta], [Delta*, -h*]] x with h = T + W (W real, T real-symmetric);
+      // with trivial-phase removal (Eq. sp_en) the generator is H - eta_q
       const T u = xr[j][0], v = xr[j][1];
-      const R w = Wr;
+      const R w = a.eta ? Wr - (R)a.eta[q] : Wr;
+      const R w2 = a.eta ? Wr + (R)a.eta[q] : Wr;  // -(h + eta) on the v component
       const T d = Dr;
       const T hu = T{Tu.x + w * u.x + (d.x * v.x - d.y * v.y), Tu.y + w * u.y + (d.x * v.y + d.y * v.x)};
-      const T hv = T{(d.x * u.x + d.y * u.y) - Tv.x - w * v.x, (d.x * u.y - d.y * u.x) - Tv.y - w * v.y};
+      const T hv = T{(d.x * u.x + d.y * u.y) - Tv.x - w2 * v.x, (d.x * u.y - d.y * u.x) - Tv.y - w2 * v.y};
+      if (MODE == M_ETA) {
+        const double2 du = to_d(u), dv = to_d(v), Hu_ = to_d(hu), Hv_ = to_d(hv);
+        eta_acc[j] += (du.x * Hu_.x + du.y * Hu_.y) + (dv.x * Hv_.x + dv.y * Hv_.y);
+        continue;
+      }
       const T fur = T{hu.y, -hu.x}, fvr = T{hv.y, -hv.x};  // -i H x, compute precision
       const double2 Hu = to_d(hu), Hv = to_d(hv);
       const double2 fu = make_double2(Hu.y, -Hu.x), fv = make_double2(Hv.y, -Hv.x);  // -i H x
@@ -266,6 +276,19 @@ __global__ void __launch_bounds__(N * TX, (sizeof(R) == 4 && N * TX >= 384) ? 2 
           mo[c] = mv;
         }
         dens_acc(mo[0], mo[1], sn, sr, si);
+      }
+    }
+    if constexpr (MODE == M_ETA) {
+      // deterministic block sums (any block size): every thread stores its value,
+      // thread j adds the NT values of state j in thread order
+      __shared__ double red[QB][NT];
+#pragma unroll
+      for (int j = 0; j < QB; ++j) red[j][threadIdx.x] = eta_acc[j];
+      __syncthreads();
+      if ((int)threadIdx.x < QB && qb0 + (int)threadIdx.x < q_end) {
+        double t = 0.0;
+        for (int k = 0; k < NT; ++k) t += red[threadIdx.x][k];
+        a.eta_part[(long)(qb0 + threadIdx.x) * gridDim.x + blockIdx.x] = t;
       }
     }
     __syncthreads();  // the batch buffer is reused
@@ -399,6 +422,14 @@ __global__ void k_energy_sites(const double* part, int n_groups, const double* n
   out[nxyz + s] = a3 * n;
 }
 
+__global__ void k_eta_reduce(const double* part, int n_qp, int n_blocks, double a3, double* eta) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n_qp) return;
+  double s = 0, c = 0;
+  for (int b = 0; b < n_blocks; ++b) neumaier(s, c, part[(long)q * n_blocks + b]);
+  eta[q] = a3 * (s + c);
+}
+
 __global__ void k_finite(const double2* x, long count, int* err) {
   int bad = 0;
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long)gridDim.x * blockDim.x) {
@@ -464,6 +495,7 @@ static int pencils_n(int mode, const PencilArgs& a, cudaStream_t s) {
     case M_CORRECT: return pencils_nm<R, N, M_CORRECT>(a, s);
     case M_DERIV_PREDICT: return pencils_nm<R, N, M_DERIV_PREDICT>(a, s);
     case M_ENERGY: return pencils_nm<R, N, M_ENERGY>(a, s);
+    case M_ETA: return pencils_nm<R, N, M_ETA>(a, s);
     default: return 1;
   }
 }
@@ -520,6 +552,13 @@ int launch_energy_sites(const double* part_ekin, int n_groups, const double* n, 
                                                                   drive, beta, g, N, a, e_site);
   return cudaGetLastError() == cudaSuccess ? 0 : 3;
 }
+
+int launch_eta_reduce(const double* eta_part, int n_qp, int n_blocks, double a3, double* eta, cudaStream_t s) {
+  k_eta_reduce<<<(n_qp + 127) / 128, 128, 0, s>>>(eta_part, n_qp, n_blocks, a3, eta);
+  return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}
+
+int pencil_blocks_x(int N) { return (N / pencil_tx(N)) * N; }
 
 int launch_finite_check(const double2* x, long count, int* err, cudaStream_t s) {
   k_finite<<<148 * 4, 256, 0, s>>>(x, count, err);

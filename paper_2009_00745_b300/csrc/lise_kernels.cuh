@@ -28,6 +28,7 @@ enum PencilMode : int {
   M_DERIV_PREDICT = 4,  // d = -i H y_{n+1} -> dslot; Eq. p, Eq. m of the next step -> m, and
                         // the corrector's precombined Q, R; densities of m
   M_ENERGY = 5,         // part_n += sum_q 2 Re(conj(v) T v)
+  M_ETA = 6,            // eta_part[q][block] = sum over the block's sites of Re(conj(x) . H x)
 };
 
 struct PencilArgs {
@@ -60,6 +61,8 @@ struct PencilArgs {
   double* part_nr;
   double* part_ni;
   int dens;               // accumulate density partials of the mode's output state
+  const double* eta;      // if non-null: apply H - eta_q (trivial-phase removal), eta per state
+  double* eta_part;       // M_ETA output: [state][block] partial sums
 };
 
 struct PlanesArgs {
@@ -125,6 +128,9 @@ int launch_energy_sites(const double* part_ekin, int n_groups, const double* n, 
                         const double* v_static, double drive, double beta, double g, int N,
                         double a, double* e_site, cudaStream_t s);
 int launch_finite_check(const double2* x, long count, int* err, cudaStream_t s);
+// eta[q] = a^3 * sum over the pencil blocks of eta_part[q][block] (compensated).
+int launch_eta_reduce(const double* eta_part, int n_qp, int n_blocks, double a3, double* eta, cudaStream_t s);
+int pencil_blocks_x(int N);
 // Tile width (x values per pencil block) and group width for a lattice.
 int pencil_tx(int N);
 int pencil_qb(int N, int mixed);

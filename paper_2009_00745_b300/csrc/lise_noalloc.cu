@@ -92,6 +92,9 @@ extern "C" int lise_rhs_noalloc(const lise_params* p, const double* psi_dev, dou
   const size_t o_v = off;      off += up256(p->v_static ? (size_t)nxyz * sizeof(double) : 0);
   const size_t o_tab = off;    off += up256(4 * (size_t)N * rs);
   const size_t o_err = off;    off += up256(sizeof(int));
+  const int nbx = pencil_blocks_x(N);
+  const size_t o_eta = off;    off += up256(p->remove_phase ? (size_t)p->n_qp * sizeof(double) : 0);
+  const size_t o_etap = off;   off += up256(p->remove_phase ? (size_t)p->n_qp * nbx * sizeof(double) : 0);
   if (off > (size_t)LISE_NOALLOC_SCRATCH_BYTES) return LISE_ENOMEM;
 
   if (cudaSetDevice(p->device) != cudaSuccess) return LISE_ECUDA;
@@ -181,6 +184,15 @@ extern "C" int lise_rhs_noalloc(const lise_params* p, const double* psi_dev, dou
   ka.n_qp = p->n_qp;
   ka.qg = qg;
   ka.out = reinterpret_cast<double2*>(dpsi_dev);
+  if (p->remove_phase) {  // eta_q = <psi_q|H psi_q> first, then -i (H - eta_q) psi_q
+    PencilArgs ea = ka;
+    ea.out = nullptr;
+    ea.eta_part = reinterpret_cast<double*>(base + o_etap);
+    if (launch_pencils(N, mixed, M_ETA, ea, s)) return LISE_ECUDA;
+    if (launch_eta_reduce(ea.eta_part, p->n_qp, nbx, p->dx * p->dx * p->dx, reinterpret_cast<double*>(base + o_eta), s))
+      return LISE_ECUDA;
+    ka.eta = reinterpret_cast<const double*>(base + o_eta);
+  }
   if (launch_pencils(N, mixed, M_RHS, ka, s)) return LISE_ECUDA;
 
   int h_err = 0;

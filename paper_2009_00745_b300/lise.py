@@ -33,7 +33,8 @@ class _Params(C.Structure):
                 ("n_qp", C.c_int), ("alpha", C.c_double), ("beta", C.c_double),
                 ("mu", C.c_double), ("g", C.c_double), ("v_static", C.c_void_p),
                 ("drive_A", C.c_double), ("drive_Omega", C.c_double), ("precision", C.c_int),
-                ("device", C.c_int), ("hbm_budget_bytes", C.c_size_t), ("stream", C.c_void_p)]
+                ("device", C.c_int), ("hbm_budget_bytes", C.c_size_t), ("stream", C.c_void_p),
+                ("remove_phase", C.c_int)]
 
 
 # Exported functions with their ctypes signatures (mirrors include/lise.h).
@@ -59,6 +60,12 @@ SIGNATURES = {
     "lise_checkpoint_bytes": (C.c_size_t, [C.c_void_p]),
     "lise_checkpoint_save": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "lise_checkpoint_load": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "lise_server_create": (C.c_int, [C.c_int, C.c_size_t, C.c_int, C.c_int, C.c_void_p]),
+    "lise_server_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_int,
+                                     C.POINTER(C.c_long)]),
+    "lise_server_wait": (C.c_int, [C.c_void_p, C.c_long, C.c_void_p, C.c_void_p]),
+    "lise_server_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t), C.POINTER(C.c_int)]),
+    "lise_server_destroy": (None, [C.c_void_p]),
 }
 
 _lib = None
@@ -89,7 +96,7 @@ def _check(rc, where):
 
 
 def _params(N, n_qp, a, alpha, beta, mu, g, v_static, drive_A, drive_Omega, precision, device,
-            hbm_budget_bytes, stream):
+            hbm_budget_bytes, stream, remove_phase=False):
     prec = {"fp64": FP64, "mixed": MIXED}.get(precision, precision)
     vs = None
     if v_static is not None:
@@ -98,7 +105,7 @@ def _params(N, n_qp, a, alpha, beta, mu, g, v_static, drive_A, drive_Omega, prec
             raise ValueError("v_static must hold N^3 values")
     p = _Params(N, N, N, float(a), int(n_qp), float(alpha), float(beta), float(mu), float(g),
                 None if vs is None else vs.ctypes.data, float(drive_A), float(drive_Omega),
-                int(prec), int(device), int(hbm_budget_bytes), stream)
+                int(prec), int(device), int(hbm_budget_bytes), stream, int(bool(remove_phase)))
     return p, vs
 
 
@@ -131,10 +138,10 @@ class Context:
 
     def __init__(self, N, n_qp, *, a=1.0, alpha=1.0, beta=0.0, mu=0.0, g=0.0, v_static=None,
                  drive_A=0.0, drive_Omega=0.0, precision="fp64", device=0, hbm_budget_bytes=0,
-                 stream=None):
+                 stream=None, remove_phase=False):
         self.N, self.n_qp = int(N), int(n_qp)
         self._p, self._vs = _params(N, n_qp, a, alpha, beta, mu, g, v_static, drive_A, drive_Omega,
-                                    precision, device, hbm_budget_bytes, stream)
+                                    precision, device, hbm_budget_bytes, stream, remove_phase)
         h = C.c_void_p()
         _check(load().lise_create(C.byref(self._p), C.byref(h)), "lise_create")
         self._h = h
@@ -236,3 +243,69 @@ class Context:
 
     def sync(self):
         _check(load().lise_sync(self._h), "lise_sync")
+
+
+class RequestInfo(C.Structure):
+    _fields_ = [("status", C.c_int), ("submit_s", C.c_double), ("admit_s", C.c_double),
+                ("done_s", C.c_double), ("t", C.c_double), ("E", C.c_double), ("N", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Server:
+    """Request loop over one GPU (lise_server_*): admission under an HBM budget,
+    overlapping step chunks of the active requests."""
+
+    def __init__(self, hbm_budget_bytes, *, device=0, max_active=8, steps_per_turn=4):
+        h = C.c_void_p()
+        _check(load().lise_server_create(int(device), int(hbm_budget_bytes), int(max_active),
+                                         int(steps_per_turn), C.byref(h)), "lise_server_create")
+        self._h = h
+        self._shapes = {}
+
+    def submit(self, N, n_qp, psi, t0, dt, n_steps, *, a=1.0, alpha=1.0, beta=0.0, mu=0.0, g=0.0,
+               v_static=None, drive_A=0.0, drive_Omega=0.0, precision="fp64"):
+        p, vs = _params(N, n_qp, a, alpha, beta, mu, g, v_static, drive_A, drive_Omega, precision, 0, 0, None)
+        ptr, dev, keep = _ptr(psi, count=n_qp * 2 * N ** 3)
+        if dev:
+            raise ValueError("the server takes host states")
+        rid = C.c_long()
+        _check(load().lise_server_submit(self._h, C.byref(p), ptr, float(t0), float(dt), int(n_steps),
+                                         C.byref(rid)), "lise_server_submit")
+        self._shapes[rid.value] = (n_qp, 2, N, N, N)
+        return rid.value
+
+    def submit_workload(self, w, psi=None, n_steps=None, precision=None):
+        return self.submit(w.nx, w.n_qp, w.initial_state() if psi is None else psi, 0.0, w.dt,
+                           w.steps if n_steps is None else n_steps, a=w.a, alpha=w.alpha, beta=w.beta,
+                           mu=w.mu, g=w.g, v_static=w.v_static, drive_A=w.drive_A,
+                           drive_Omega=w.drive_Omega, precision=precision or w.precision)
+
+    def wait(self, rid, want_state=True):
+        shape = self._shapes.pop(rid)
+        out = np.empty(shape, dtype=np.complex128) if want_state else None
+        info = RequestInfo()
+        rc = load().lise_server_wait(self._h, int(rid), None if out is None else out.ctypes.data,
+                                     C.byref(info))
+        _check(rc, "lise_server_wait")
+        return out, info.as_dict()
+
+    def stats(self):
+        u, a = C.c_size_t(), C.c_int()
+        _check(load().lise_server_stats(self._h, C.byref(u), C.byref(a)), "lise_server_stats")
+        return {"peak_used_bytes": u.value, "peak_active": a.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().lise_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

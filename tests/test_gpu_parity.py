@@ -264,3 +264,44 @@ def test_mixed_energy_drift_vs_fp64():
             E[prec] = np.array(e)
     dev = np.max(np.abs(E["mixed"] - E["fp64"]) / np.abs(E["fp64"]))
     assert dev < 1e-6, dev
+
+
+# ---------------------------------------------------- trivial-phase removal ----
+
+@pytest.mark.parametrize("N,precision,tol", [(16, "fp64", TOL_FP64_RHS), (16, "mixed", 2e-6),
+                                             (12, "fp64", TOL_FP64_RHS), (20, "fp64", TOL_FP64_RHS),
+                                             (48, "fp64", TOL_FP64_RHS)])
+def test_rhs_phase_removal(N, precision, tol):
+    n_qp = 7
+    psi = random_state(N, n_qp, seed=21, kmax=5)
+    kw = dict(alpha=1.1, beta=-0.5, mu=0.2, g=0.9)
+    with L.Context(N, n_qp, precision=precision, remove_phase=True, **kw) as ctx:
+        got = ctx.rhs(psi, 0.4)
+    ref = O.rhs(O.Params(N, N, N, n_qp=n_qp, remove_phase=True, **kw), psi, 0.4)
+    assert rel(got, ref) < tol
+
+
+def test_run_phase_removal():
+    w = W.ufg_plane_waves(12, 9, noise_eps=0.1, steps=8)
+    with L.Context.from_workload(w, remove_phase=True) as ctx:
+        ctx.set_state(w.initial_state(), 0.0, w.dt)
+        ctx.step(w.steps)
+        got = ctx.state()
+        n, nu = ctx.densities()
+    s = O.Solver(oracle_params(w, remove_phase=True))
+    s.set_state(w.initial_state(), 0.0, w.dt)
+    s.step(w.steps)
+    assert rel(got, s.state()) < TOL_FP64_RUN
+    on, onu = s.densities()
+    assert rel(n, on) < TOL_FP64_RUN and rel(nu, onu) < TOL_FP64_RUN
+
+
+def test_phase_removal_keeps_stationary_state():
+    w = W.ufg_plane_waves(8, 24, noise_eps=0.0, delta0=0.5)
+    U_, V_ = w.amps[:, 0], w.amps[:, 1]
+    g_sc = -w.delta0 / (np.sum(U_ * V_) / (w.nxyz * w.a ** 3))
+    with L.Context(8, 24, alpha=w.alpha, beta=w.beta, mu=w.mu, g=g_sc, remove_phase=True) as ctx:
+        ctx.set_state(w.initial_state(), 0.0, 0.01)
+        ctx.step(40)
+        got = ctx.state()
+    assert rel(got, w.initial_state()) < 1e-13

@@ -60,3 +60,20 @@ def test_noalloc_rejects_oversized_problem():
     p, _ = L._params(N, n_qp, 1.0, 1.0, 0.0, 0.0, 0.0, None, 0.0, 0.0, "fp64", 0, 0, None)
     x = torch.zeros(1, dtype=torch.complex128, device="cuda:0")
     assert _noalloc(p, x, 0.0, x) == L.ENOMEM
+
+
+def test_noalloc_phase_removal_matches_context():
+    import torch
+    N, n_qp = 12, 10
+    kw = dict(a=1.0, alpha=1.0, beta=-0.5, mu=0.3, g=0.9)
+    psi = random_state(N, n_qp, seed=31, kmax=4)
+    with L.Context(N, n_qp, remove_phase=True, **kw) as ctx:
+        ref = ctx.rhs(psi, 0.7)
+    p, keep = L._params(N, n_qp, kw["a"], kw["alpha"], kw["beta"], kw["mu"], kw["g"], None, 0.0, 0.0, "fp64",
+                        0, 0, None, True)
+    x = torch.from_numpy(psi).to("cuda:0")
+    out = torch.empty_like(x)
+    for _ in range(2):
+        out.fill_(float("nan"))
+        assert _noalloc(p, x, 0.7, out) == L.OK
+        assert rel(out.cpu().numpy(), ref) < TOL_RHS

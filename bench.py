@@ -52,22 +52,35 @@ def algorithmic_per_qp_site(N, mixed):
     """Algorithmic flops and HBM bytes per (state, site) of each kernel class
     for one ABM step (two right-hand sides), for the kernels as designed:
 
-    planes   read the operand, write T_xy (both components);
-    pencils  (corrector launch) read m, T_xy, Q, R; write y_{n+1}, p - c;
-             (derivative/predictor launch) read y_{n+1}, T_xy, y_n, y'_n,
-             y'_{n-1}, y'_{n-2}, p - c; write y'_{n+1}, m, Q, R.
+    planes     read the operand, write T_xy (both components);
+    pencils    corrector launch: read m, T_xy, Q, R; write y_{n+1}, p - c.
+               FP64 derivative/predictor launch: read y_{n+1}, T_xy, y_n,
+               y'_n, y'_{n-1}, y'_{n-2}, p - c; write y'_{n+1}, m, Q, R.
+               Mixed derivative launch: read y_{n+1}, T_xy; write y'_{n+1}.
+    pointwise  (mixed only) predictor: read y_{n+1}, y_n, y'_{n+1}..y'_{n-2},
+               p - c; write m, Q, R.
     complex128 = 16 B per component; in the mixed path T_xy and m are complex64.
     FFT convention: 5 n log2 n real flops per complex length-n transform."""
     L = log2(N)
     c16, cr = 16, (8 if mixed else 16)   # complex128 / compute-precision component
     planes_bytes = 2 * (cr + cr) + 2 * (c16 + cr)          # operand m, then operand y_{n+1}
     correct_bytes = 2 * (cr + cr + 2 * c16) + 2 * (2 * c16)
-    deriv_bytes = 2 * (c16 + cr + 5 * c16) + 2 * (3 * c16 + cr)
+    fft_bdg = 2 * (2 * 5 * L + 4) + 24                     # z fwd+inv + multiply/add, BdG apply
     planes_flops = 2 * 2 * (2 * 2 * 5 * L + 3)              # 2 launches x 2 comps: 2D fwd+inv, multiply
-    pencils_flops = 2 * (2 * (2 * 5 * L + 4) + 24) + (16 + 13) + (92 + 13)
+    predict_flops = 92 + 13                                 # Eq. p/m, Q, R, densities of m
+    if mixed:
+        deriv_bytes = 2 * (c16 + cr) + 2 * c16
+        predict_bytes = 2 * 7 * c16 + 2 * (cr + 2 * c16)
+        pencils_flops = 2 * fft_bdg + (16 + 13)
+        pointwise = {"flops": predict_flops, "bytes": predict_bytes, "launches_per_step": 1}
+    else:
+        deriv_bytes = 2 * (c16 + cr + 5 * c16) + 2 * (3 * c16 + cr)
+        pencils_flops = 2 * fft_bdg + (16 + 13) + predict_flops
+        pointwise = {"flops": 0.0, "bytes": 0, "launches_per_step": 0}
     return {
         "planes": {"flops": planes_flops, "bytes": planes_bytes, "launches_per_step": 2},
         "pencils": {"flops": pencils_flops, "bytes": correct_bytes + deriv_bytes, "launches_per_step": 2},
+        "pointwise": pointwise,
     }
 
 
@@ -417,7 +430,8 @@ def main():
 
     # ---- roofline of the dominant kernel class, from the live event timings
     alg = algorithmic_per_qp_site(w.nx, mixed)
-    dom = max(("planes", "pencils"), key=lambda k: prof[k][1])
+    dom = max((k for k in ("planes", "pencils", "pointwise") if alg[k]["launches_per_step"]),
+              key=lambda k: prof[k][1])
     launches, tot_ms = prof[dom]
     per_launch_ms = tot_ms / max(launches, 1)
     qp_sites = float(w.n_qp) * w.nxyz

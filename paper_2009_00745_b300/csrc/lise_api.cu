@@ -9,7 +9,7 @@
 // plus per-group density partial sums, reduced densities and the potentials
 // W = U(n) - mu + V_ext and Delta of the operand of the next right-hand side.
 //
-// One ABM step (Eqs. p, m, c, y) is 6 launches:
+// One ABM step (Eqs. p, m, c, y) is 6 launches (7 in the mixed path, see abm_step):
 //   planes(m), pencils[CORRECT]        m' = -iHm; y_{n+1} = Q + k1 m', p - c; densities of y_{n+1}
 //   reduce                             W, Delta of y_{n+1} at t_{n+1}
 //   planes(y_{n+1}), pencils[DERIV_PREDICT]
@@ -278,6 +278,42 @@ int fetch_err(lise_ctx* c) {
   return LISE_OK;
 }
 
+PointwiseArgs predict_args(lise_ctx* c, const double2* y0, const double2* y1, const double2* d0,
+                           const double2* d1, const double2* d2, const double2* d3, double h) {
+  PointwiseArgs w;
+  std::memset(&w, 0, sizeof(w));
+  w.y0 = y0;
+  w.y1 = y1;
+  w.d0 = d0;
+  w.d1 = d1;
+  w.d2 = d2;
+  w.d3 = d3;
+  w.pc = c->PC;
+  w.q = c->Q;
+  w.r = c->R;
+  w.m = c->M;
+  w.mixed = c->mixed;
+  w.h = h;
+  w.part_n = c->part_n;
+  w.part_nr = c->part_nr;
+  w.part_ni = c->part_ni;
+  w.n_qp = c->p.n_qp;
+  w.qg = c->qg;
+  w.nxyz = c->nxyz;
+  return w;
+}
+
+// y_{n+1} (in the y_{n-1} slot) becomes y_n; y'_{n+1} (in D[3]) becomes D[0]
+void rotate_history(lise_ctx* c, double t1) {
+  c->y0_slot = 1 - c->y0_slot;
+  double2* d3 = c->D[3];
+  c->D[3] = c->D[2];
+  c->D[2] = c->D[1];
+  c->D[1] = c->D[0];
+  c->D[0] = d3;
+  c->t = t1;
+}
+
 int start_procedure(lise_ctx* c, double t0, double dt) {
   // y_0 is in slot[0]; densities and potentials of y_0 at t0 into dn[0]
   double2* cur = c->slot[0];
@@ -308,26 +344,8 @@ int start_procedure(lise_ctx* c, double t0, double dt) {
   c->y0_slot = (cur == c->slot[0]) ? 0 : 1;
   // p_3 - c_3 := 0; predictor and modifier of the first ABM step
   TRY(cu(cudaMemsetAsync(c->PC, 0, (size_t)c->ns * sizeof(double2), c->stream)));
-  PointwiseArgs w;
-  std::memset(&w, 0, sizeof(w));
-  w.y0 = c->slot[c->y0_slot];
-  w.y1 = c->slot[1 - c->y0_slot];
-  w.d0 = c->D[0];
-  w.d1 = c->D[1];
-  w.d2 = c->D[2];
-  w.d3 = c->D[3];
-  w.pc = c->PC;
-  w.q = c->Q;
-  w.r = c->R;
-  w.m = c->M;
-  w.mixed = c->mixed;
-  w.h = dt;
-  w.part_n = c->part_n;
-  w.part_nr = c->part_nr;
-  w.part_ni = c->part_ni;
-  w.n_qp = c->p.n_qp;
-  w.qg = c->qg;
-  w.nxyz = c->nxyz;
+  PointwiseArgs w = predict_args(c, c->slot[c->y0_slot], c->slot[1 - c->y0_slot], c->D[0], c->D[1], c->D[2],
+                                 c->D[3], dt);
   TRY(timed(c, LISE_KC_POINTWISE, [&] { return launch_predict(w, c->stream) ? LISE_ECUDA : LISE_OK; }));
   const double t3 = t0 + 3 * dt;
   TRY(run_reduce(c, 1, nullptr, nullptr, true, t3 + dt));
@@ -358,6 +376,19 @@ int abm_step(lise_ctx* c) {
   // RHS #2 on y_{n+1}: y'_{n+1} into the y'_{n-3} slot, then Eq. p and Eq. m of step n+2
   TRY(run_planes(c, ynm1));
   TRY(run_eta(c, ynm1));
+  if (c->mixed) {
+    // memory-bound path: the pencils launch writes y'_{n+1} only; a streaming kernel then
+    // forms m, Q, R and the densities of m from the history
+    PencilArgs b = pencil_base(c);
+    b.x = ynm1;
+    b.out = c->D[3];
+    TRY(run_pencils(c, M_RHS, b));
+    PointwiseArgs w = predict_args(c, ynm1, yn, c->D[3], c->D[0], c->D[1], c->D[2], h);
+    TRY(timed(c, LISE_KC_POINTWISE, [&] { return launch_predict(w, c->stream) ? LISE_ECUDA : LISE_OK; }));
+    TRY(run_reduce(c, 1, nullptr, nullptr, true, t1 + h));
+    rotate_history(c, t1);
+    return LISE_OK;
+  }
   PencilArgs b = pencil_base(c);
   b.x = ynm1;
   b.h = h;
@@ -373,14 +404,7 @@ int abm_step(lise_ctx* c) {
   b.dens = 1;
   TRY(run_pencils(c, M_DERIV_PREDICT, b));
   TRY(run_reduce(c, 1, nullptr, nullptr, true, t1 + h));
-  // rotate the history
-  c->y0_slot = 1 - c->y0_slot;
-  double2* d3 = c->D[3];
-  c->D[3] = c->D[2];
-  c->D[2] = c->D[1];
-  c->D[1] = c->D[0];
-  c->D[0] = d3;
-  c->t = t1;
+  rotate_history(c, t1);
   return LISE_OK;
 }
 

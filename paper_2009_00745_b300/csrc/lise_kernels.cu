@@ -346,31 +346,39 @@ __global__ void k_reduce(ReduceArgs a) {
 }
 
 // --------------------------------------------------------------- pointwise --
-// First ABM step after the start procedure: Eq. p and Eq. m, the corrector's
-// Q, R (see lise_kernels.cuh), densities of m.  FP64 in both paths.
+// Eq. p, Eq. m and the corrector's Q, R (see lise_kernels.cuh) from the history
+//   y0 = y_{k}, y1 = y_{k-1}, d0..d3 = y'_{k}..y'_{k-3}, pc = p_k - c_k,
+// plus the densities of m.  Used after the start procedure (k = 3) and, in the
+// mixed path, as the second half of every derivative/predictor step.  As in the
+// fused epilogue, the derivative combinations run in the compute precision R and
+// every sum with a state value in FP64.
+template <typename R>
 __global__ void k_predict(PointwiseArgs a) {
+  using T = typename Cx<R>::T;
   const long s = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= a.nxyz) return;
   const int g = blockIdx.y;
   const int q_begin = g * a.qg, q_end = min(a.n_qp, q_begin + a.qg);
-  const double h48 = a.h / 48.0;
-  const double c161 = 161.0 / 170.0, c9 = 9.0 / 170.0;
+  const R h48 = (R)(a.h / 48.0);
+  const R c161 = (R)(161.0 / 170.0), c9 = (R)(9.0 / 170.0);
   double sn = 0, sr = 0, si = 0;
   for (int q = q_begin; q < q_end; ++q) {
     double2 mo[2];
+#pragma unroll
     for (int c = 0; c < 2; ++c) {
       const long i = (long)(2 * q + c) * a.nxyz + s;
+      const T e0 = to_r<R>(a.d0[i]), e1 = to_r<R>(a.d1[i]), e2 = to_r<R>(a.d2[i]), e3 = to_r<R>(a.d3[i]);
+      const T pcv = to_r<R>(a.pc[i]);
+      const T pt = T{h48 * (R(119) * e0.x - R(99) * e1.x + R(69) * e2.x - R(17) * e3.x),
+                     h48 * (R(119) * e0.y - R(99) * e1.y + R(69) * e2.y - R(17) * e3.y)};
+      const T ct = T{h48 * (R(51) * e0.x + R(3) * e1.x + e2.x), h48 * (R(51) * e0.y + R(3) * e1.y + e2.y)};
+      const T X = T{pt.x - c161 * pcv.x, pt.y - c161 * pcv.y};
+      const T Y = T{c161 * ct.x + c9 * pt.x, c161 * ct.y + c9 * pt.y};
       const double2 hf = dscale(dadd(a.y0[i], a.y1[i]), 0.5);
-      const double2 pt = dscale(dadd(dsub(dscale(a.d0[i], 119.0), dscale(a.d1[i], 99.0)),
-                                     dsub(dscale(a.d2[i], 69.0), dscale(a.d3[i], 17.0))), h48);
-      const double2 ct = dscale(dadd(dadd(dscale(a.d0[i], 51.0), dscale(a.d1[i], 3.0)), a.d2[i]), h48);
-      const double2 mv = dadd(hf, dsub(pt, dscale(a.pc[i], c161)));
-      if (a.mixed)
-        reinterpret_cast<float2*>(a.m)[i] = to_r<float>(mv);
-      else
-        reinterpret_cast<double2*>(a.m)[i] = mv;
-      a.q[i] = dadd(hf, dadd(dscale(ct, c161), dscale(pt, c9)));
-      a.r[i] = dsub(pt, ct);
+      const double2 mv = dadd(hf, to_d(X));
+      reinterpret_cast<T*>(a.m)[i] = to_r<R>(mv);
+      a.q[i] = dadd(hf, to_d(Y));
+      a.r[i] = to_d(T{pt.x - ct.x, pt.y - ct.y});
       mo[c] = mv;
     }
     dens_acc(mo[0], mo[1], sn, sr, si);
@@ -532,7 +540,10 @@ int launch_reduce(const ReduceArgs& a, cudaStream_t s) {
 int launch_predict(const PointwiseArgs& a, cudaStream_t s) {
   const int nt = 256;
   dim3 grid((unsigned)((a.nxyz + nt - 1) / nt), (a.n_qp + a.qg - 1) / a.qg);
-  k_predict<<<grid, nt, 0, s>>>(a);
+  if (a.mixed)
+    k_predict<float><<<grid, nt, 0, s>>>(a);
+  else
+    k_predict<double><<<grid, nt, 0, s>>>(a);
   return cudaGetLastError() == cudaSuccess ? 0 : 3;
 }
 

@@ -78,6 +78,13 @@ typedef struct {
   int remove_phase;         /* 1: evolve i dpsi_k/dt = (H - eta_k) psi_k with eta_k = <psi_k|H|psi_k>
                                (trivial-phase removal, Eq. sp_en), in the right-hand sides and the
                                series start (eta_k of the step's starting state); 0: plain Eq. tdslda */
+  double pair_alpha;        /* Eq. g0: g0(r) = g (1 - pair_alpha n(r) / pair_n0); 0 = constant g */
+  double pair_n0;           /* reference density of Eq. g0 (> 0 when pair_alpha != 0) */
+  int pair_lattice;         /* 1: lattice renormalisation of Eq. geff_3D,
+                               1/g_eff = 1/g0(r) - meff (pi/dx) K / (4 pi^2), meff = 1/alpha,
+                               K = 2.442749607806335; 0: g_eff = g0(r).  Delta = -g_eff nu; with a
+                               density-dependent g_eff, U gains (d g_eff/dn) |nu|^2 and
+                               E_pair = g_eff(n) |nu|^2 (Eq. pairing) */
 } lise_params;
 
 /* Device bytes lise_create would allocate for these parameters (0 if invalid). */
@@ -112,7 +119,7 @@ int lise_get_time(lise_ctx *c, double *t);
 int lise_densities(lise_ctx *c, double *n_out, double *nu_out);
 
 /* Energy and particle number of the current state at the current time:
- *   E = a^3 sum_r [(alpha/2) tau + (3/10) beta (3 pi^2)^(2/3) n^(5/3) + g |nu|^2 + V_ext n],
+ *   E = a^3 sum_r [(alpha/2) tau + (3/10) beta (3 pi^2)^(2/3) n^(5/3) + g_eff(n) |nu|^2 + V_ext n],
  *   tau = 2 sum_k |grad v_k|^2 (spectral, same Laplacian as the step; Eq. pairing
  *   gives the + g |nu|^2 term), N = a^3 sum_r n.  FP64 with compensated sums.
  * Synchronises. */

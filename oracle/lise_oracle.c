@@ -206,6 +206,20 @@ double or_vext(const or_params *p, int ix, int iy, int iz, double t) {
   return v;
 }
 
+void or_geff(const or_params *p, double n, double *geff, double *dgeff_dn) {
+  double g0 = p->g, dg0 = 0.0;
+  if (p->pair_alpha != 0.0) { /* Eq. g0 */
+    g0 = p->g * (1.0 - p->pair_alpha * n / p->pair_n0);
+    dg0 = -p->g * p->pair_alpha / p->pair_n0;
+  }
+  double c = 0.0;
+  if (p->pair_lattice) /* Eq. geff_3D with hbar = 1, m* = 1/alpha, dx = a */
+    c = (1.0 / p->alpha) / (4.0 * OR_PI * OR_PI) * (OR_PI / p->a) * OR_GEFF_K;
+  double den = 1.0 - c * g0;
+  *geff = g0 / den;
+  *dgeff_dn = dg0 / (den * den);
+}
+
 void or_potentials(const or_params *p, const double *n, const double complex *nu,
                    double t, double *W, double complex *Delta) {
   int nx = p->nx, ny = p->ny, nz = p->nz;
@@ -214,8 +228,11 @@ void or_potentials(const or_params *p, const double *n, const double complex *nu
       for (int x = 0; x < nx; ++x) {
         long r = ((long)z * ny + y) * nx + x;
         double U = 0.5 * p->beta * pow(3.0 * OR_PI * OR_PI * n[r], 2.0 / 3.0);
-        W[r] = U - p->mu + or_vext(p, x, y, z, t);
-        Delta[r] = -p->g * nu[r];
+        double geff, dgeff;
+        or_geff(p, n[r], &geff, &dgeff);
+        double nu2 = creal(nu[r]) * creal(nu[r]) + cimag(nu[r]) * cimag(nu[r]);
+        W[r] = U + dgeff * nu2 - p->mu + or_vext(p, x, y, z, t);
+        Delta[r] = -geff * nu[r];
       }
 }
 
@@ -518,8 +535,10 @@ void or_energy_of(const or_params *p, const double complex *psi, double t,
       for (int x = 0; x < p->nx; ++x) {
         long r = ((long)z * p->ny + y) * p->nx + x;
         double nr = n[r];
-        /* Eq. pairing: E_pair = +g |nu|^2 (with Delta = -g nu, Eq. pairingfield) */
-        double e = cint * pow(nr, 5.0 / 3.0) + p->g * (creal(nu[r]) * creal(nu[r]) + cimag(nu[r]) * cimag(nu[r])) +
+        /* Eq. pairing: E_pair = +g_eff |nu|^2 (with Delta = -g_eff nu, Eq. pairingfield) */
+        double geff, dgeff;
+        or_geff(p, nr, &geff, &dgeff);
+        double e = cint * pow(nr, 5.0 / 3.0) + geff * (creal(nu[r]) * creal(nu[r]) + cimag(nu[r]) * cimag(nu[r])) +
                    or_vext(p, x, y, z, t) * nr;
         neumaier_add(&es, &ec, a3 * e);
         neumaier_add(&ns_, &nc, a3 * nr);

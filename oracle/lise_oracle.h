@@ -46,7 +46,18 @@ typedef struct {
   double drive_A;          /* V_ext += A sin(Omega t) z_c */
   double drive_Omega;
   int remove_phase;        /* 1: i dpsi_k/dt = (H - eta_k) psi_k, eta_k = <psi_k|H|psi_k> (Eq. sp_en) */
+  double pair_alpha;       /* Eq. g0: g0(r) = g (1 - pair_alpha n(r) / pair_n0); 0 = constant g */
+  double pair_n0;
+  int pair_lattice;        /* 1: Eq. geff_3D, 1/g_eff = 1/g0(r) - meff (pi/a) K / (4 pi^2 hbar^2), meff = 1/alpha */
 } or_params;
+
+/* K of Eq. geff_3D (the value printed with it). */
+#define OR_GEFF_K 2.442749607806335
+
+/* Effective coupling and its density derivative at density n:
+ * g_eff = g0 / (1 - c g0) (the same as 1/g_eff = 1/g0 - c), c = K / (4 pi a alpha)
+ * with the lattice renormalisation, else 0; dgeff_dn = (dg0/dn) / (1 - c g0)^2. */
+void or_geff(const or_params *p, double n, double *geff, double *dgeff_dn);
 
 /* 1D DFT of length n (any n >= 1), out-of-place, unnormalised.
  * sign = -1: sum_j x_j exp(-2 pi i j k / n); sign = +1: exp(+...). */
@@ -69,8 +80,9 @@ void or_densities(const or_params *p, const double complex *psi, double *n,
 /* V_ext(r, t) = v_static(r) + A sin(Omega t) (i_z - nz/2) a. */
 double or_vext(const or_params *p, int ix, int iy, int iz, double t);
 
-/* W(r) = beta (3 pi^2 n)^(2/3)/2 - mu + V_ext(r, t) (the diagonal of h besides T);
- * Delta(r) = -g nu(r). */
+/* W(r) = beta (3 pi^2 n)^(2/3)/2 + (d g_eff/dn) |nu|^2 - mu + V_ext(r, t) (the diagonal
+ * of h besides T; the middle term is dE_pair/dn and vanishes for a constant
+ * coupling); Delta(r) = -g_eff(n(r)) nu(r). */
 void or_potentials(const or_params *p, const double *n, const double complex *nu,
                    double t, double *W, double complex *Delta);
 
@@ -100,7 +112,7 @@ int or_step(or_solver *s, int n_steps);
 void or_get_state(const or_solver *s, double complex *psi_out);
 double or_time(const or_solver *s);
 void or_get_densities(const or_solver *s, double *n, double complex *nu);
-/* E = a^3 sum_r [(alpha/2) tau + (3/10) beta (3 pi^2)^(2/3) n^(5/3) + g |nu|^2
+/* E = a^3 sum_r [(alpha/2) tau + (3/10) beta (3 pi^2)^(2/3) n^(5/3) + g_eff(n) |nu|^2
  *     + V_ext n],  tau = 2 sum_k |grad v_k|^2 (spectral);  N = a^3 sum_r n.
  * The pairing term has the sign of Eq. pairing (E_pair = g_eff |kappa|^2 with
  * Delta = -g_eff kappa); U = dE/dn gives the beta term of h. */

@@ -78,6 +78,8 @@ int check_params(const lise_params* p) {
   if (!std::isfinite(p->alpha) || !std::isfinite(p->beta) || !std::isfinite(p->mu) ||
       !std::isfinite(p->g) || !std::isfinite(p->drive_A) || !std::isfinite(p->drive_Omega))
     return LISE_EINVAL;
+  if (p->pair_lattice && !(p->alpha > 0.0)) return LISE_EINVAL;
+  if (p->pair_alpha != 0.0 && !(std::isfinite(p->pair_alpha) && p->pair_n0 > 0.0)) return LISE_EINVAL;
   return LISE_OK;
 }
 
@@ -215,6 +217,8 @@ int run_reduce(lise_ctx* c, int dslot, const double* avg_n, const double2* avg_n
   r.beta = c->p.beta;
   r.mu = c->p.mu;
   r.g = c->p.g;
+  r.pair_alpha_n0 = c->p.pair_alpha != 0.0 ? c->p.pair_alpha / c->p.pair_n0 : 0.0;
+  r.pair_c = c->p.pair_lattice ? pairing_lattice_c(c->p.dx, c->p.alpha) : 0.0;
   r.err = c->err;
   return timed(c, LISE_KC_REDUCE, [&] { return launch_reduce(r, c->stream) ? LISE_ECUDA : LISE_OK; });
 }
@@ -660,7 +664,9 @@ int lise_energy(lise_ctx* c, double* E, double* Nout) {
   a.dens = 1;
   TRY(run_pencils(c, M_ENERGY, a));
   TRY(launch_energy_sites(c->part_n, c->n_groups, c->dn[0], c->dnu[0], c->v_static, drive_at(c, c->t), c->p.beta,
-                          c->p.g, c->N, c->p.dx, c->e_site, c->stream)
+                          c->p.g, c->p.pair_alpha != 0.0 ? c->p.pair_alpha / c->p.pair_n0 : 0.0,
+                          c->p.pair_lattice ? pairing_lattice_c(c->p.dx, c->p.alpha) : 0.0, c->N, c->p.dx,
+                          c->e_site, c->stream)
           ? LISE_ECUDA
           : LISE_OK);
   TRY(cu(cudaMemcpyAsync(c->host_e, c->e_site, 2 * c->nxyz * sizeof(double), cudaMemcpyDeviceToHost, c->stream)));

@@ -185,11 +185,13 @@ __device__ __forceinline__ void fft_phase1(typename Cx<R>::T* buf, Base base, in
 #pragma unroll
       for (int j1 = 0; j1 < N1; ++j1) a[j1] = p[j1 * N2 * es];
       Dft<N1, S, R>::run(a);
+      if (j2 != 0) {  // the j2 = 0 twiddles are 1 (warp-uniform: lines are the fast index)
 #pragma unroll
-      for (int k1 = 1; k1 < N1; ++k1) {
-        T w = tw[j2 * N1 + k1];
-        if (S > 0) w.y = -w.y;
-        a[k1] = cmul(a[k1], w);
+        for (int k1 = 1; k1 < N1; ++k1) {
+          T w = tw[j2 * N1 + k1];
+          if (S > 0) w.y = -w.y;
+          a[k1] = cmul(a[k1], w);
+        }
       }
 #pragma unroll
       for (int k1 = 0; k1 < N1; ++k1) p[k1 * N2 * es] = a[k1];

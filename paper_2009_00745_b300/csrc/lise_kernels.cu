@@ -49,6 +49,13 @@ template <> __device__ __forceinline__ double2 to_r<double>(double2 v) { return 
 template <> __device__ __forceinline__ float2 to_r<float>(double2 v) {
   return make_float2(d2f_bits(v.x), d2f_bits(v.y));
 }
+// Conversion on the hardware path (F2F, executed by the FP64 pipe): used where that
+// pipe is otherwise idle (the planes kernel), to spare the integer pipe.
+template <typename R> __device__ __forceinline__ typename Cx<R>::T to_r_hw(double2 v);
+template <> __device__ __forceinline__ double2 to_r_hw<double>(double2 v) { return v; }
+template <> __device__ __forceinline__ float2 to_r_hw<float>(double2 v) {
+  return make_float2(__double2float_rn(v.x), __double2float_rn(v.y));
+}
 __device__ __forceinline__ double2 to_d(double2 v) { return v; }
 __device__ __forceinline__ double2 to_d(float2 v) { return make_double2(f2d_bits(v.x), f2d_bits(v.y)); }
 
@@ -65,6 +72,19 @@ __device__ __forceinline__ void dens_acc(double2 u, double2 v, double& sn, doubl
   sr += u.x * v.x + u.y * v.y;
   si += u.y * v.x - u.x * v.y;
 }
+
+// Asynchronous global -> shared copies (no register staging).  Each thread copies
+// and later reads only its own elements, so its own wait suffices.
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem, int bytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  if (bytes == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_but_last() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
 // Padded-plane tile count per block for the planes kernel.
 template <int N> struct PlanesPB { static constexpr int v = N <= 8 ? 8 : (N <= 16 ? 4 : (N <= 32 ? 2 : 1)); };
@@ -93,7 +113,7 @@ __global__ void __launch_bounds__(NT) k_planes(PlanesArgs a) {
   for (int i = threadIdx.x; i < PB * N * N; i += NT) {
     int pl = i / (N * N), r = i % (N * N);
     T v = T{R(0), R(0)};
-    if (pl < np) v = srcr ? srcr[i] : to_r<R>(src[i]);
+    if (pl < np) v = srcr ? srcr[i] : to_r_hw<R>(src[i]);
     buf[pl * PS + (r / N) * NP + (r % N)] = v;
   }
   __syncthreads();
@@ -115,8 +135,21 @@ __global__ void __launch_bounds__(NT) k_planes(PlanesArgs a) {
 }
 
 // ----------------------------------------------------------------- pencils --
+// Byte offset of the prefetch staging area in the pencils kernel's shared memory
+// (after the FFT buffer, the twiddles and the kinetic factors), 16-byte aligned.
+template <typename T, int N, int TX, int QB>
+__host__ __device__ constexpr int pencil_stage_offset() {
+  return (((QB * 2 * (N * TX + (sizeof(T) == 8 ? 8 : 0)) + N) * (int)sizeof(T) + N * (int)sizeof(T) / 2) + 15) / 16 * 16;
+}
+template <typename T, int N, int TX, int QB>
+__host__ __device__ constexpr int pencil_smem_bytes() {
+  // staging only for the FP32 compute precision (see kPrefetch in k_pencils): the next
+  // batch's operand and T_xy, and this batch's Q and R (corrector)
+  return pencil_stage_offset<T, N, TX, QB>() + (sizeof(T) == 8 ? QB * 2 * N * TX * (16 + (int)sizeof(T) + 32) : 0);
+}
+
 template <typename R, int N, int TX, int QB, int MODE>
-__global__ void __launch_bounds__(N * TX, (sizeof(R) == 4 && N * TX >= 384) ? 2 : 1) k_pencils(PencilArgs a) {
+__global__ void __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N * TX == 256 ? 2 : 1) k_pencils(PencilArgs a) {
   using T = typename Cx<R>::T;
   constexpr int NT = N * TX;
   // one component block [z][x] in shared memory; for 8-byte elements the blocks are
@@ -127,6 +160,12 @@ __global__ void __launch_bounds__(N * TX, (sizeof(R) == 4 && N * TX >= 384) ? 2 
   T* buf = reinterpret_cast<T*>(smem_raw);  // [QB][2][N][TX]
   T* tw = buf + QB * 2 * CS;
   R* hz = reinterpret_cast<R*>(tw + N);
+  // prefetch staging for the next batch, [QB * 2][NT] per array: the operand as
+  // stored (complex128, or the compute precision when a.xr is set) and T_xy
+  double2* xstage = reinterpret_cast<double2*>(smem_raw + pencil_stage_offset<T, N, TX, QB>());
+  T* tstage = reinterpret_cast<T*>(xstage + QB * 2 * NT);
+  double2* qstage = reinterpret_cast<double2*>(tstage + QB * 2 * NT);  // Q then R of this batch
+  double2* rstage = qstage + QB * 2 * NT;
   const T* twg = reinterpret_cast<const T*>(a.tw);
   const R* hg = reinterpret_cast<const R*>(a.hz);
   for (int i = threadIdx.x; i < N; i += NT) {
@@ -153,6 +192,30 @@ __global__ void __launch_bounds__(N * TX, (sizeof(R) == 4 && N * TX >= 384) ? 2 
   const T Dr = to_r<R>(Dv);
   double sn = 0.0, sr = 0.0, si = 0.0;
   auto base = [](int l) { return (l / TX) * CS + (l % TX); };
+  // issue the asynchronous copies of one batch's operand and T_xy (own site only)
+  auto prefetch = [&](int qb) {
+#pragma unroll
+    for (int j = 0; j < QB; ++j) {
+      const int q = qb + j;
+      if (q < q_end) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const long gi = (long)(2 * q + c) * nxyz + site;
+          const int si_ = (2 * j + c) * NT + threadIdx.x;
+          if (a.xr)
+            cp_async(reinterpret_cast<T*>(xstage) + si_, reinterpret_cast<const T*>(a.xr) + gi, (int)sizeof(T));
+          else
+            cp_async(xstage + si_, a.x + gi, 16);
+          cp_async(tstage + si_, txy + gi, (int)sizeof(T));
+        }
+      }
+    }
+    cp_async_commit();
+  };
+  // the prefetch pays in the memory-bound mixed path; the FP64 path is FP64-pipe bound and
+  // keeps its registers for occupancy (plain loads)
+  constexpr bool kPrefetch = sizeof(R) == 4;
+  if (kPrefetch && q_begin < q_end) prefetch(q_begin);
   __syncthreads();
 
   for (int qb0 = q_begin; qb0 < q_end; qb0 += QB) {
@@ -160,31 +223,80 @@ __global__ void __launch_bounds__(N * TX, (sizeof(R) == 4 && N * TX >= 384) ? 2 
 #pragma unroll
     for (int j = 0; j < QB; ++j) eta_acc[j] = 0.0;
     T xr[QB][2];  // the operand in compute precision (FP64 values are reloaded where needed)
+    T tr[QB][2];  // T_xy of this batch (prefetch path)
+    if constexpr (kPrefetch) {
+      cp_async_wait_all();
 #pragma unroll
-    for (int j = 0; j < QB; ++j) {
-      const int q = qb0 + j;
+      for (int j = 0; j < QB; ++j) {
+        const int q = qb0 + j;
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        const long gi = (long)(2 * q + c) * nxyz + site;
-        const T v = q < q_end ? (a.xr ? reinterpret_cast<const T*>(a.xr)[gi] : to_r<R>(a.x[gi])) : T{R(0), R(0)};
-        xr[j][c] = v;
-        buf[(2 * j + c) * CS + z * TX + xl] = v;
+        for (int c = 0; c < 2; ++c) {
+          const int si_ = (2 * j + c) * NT + threadIdx.x;
+          T v = T{R(0), R(0)}, t = T{R(0), R(0)};
+          if (q < q_end) {
+            v = a.xr ? reinterpret_cast<const T*>(xstage)[si_] : to_r<R>(xstage[si_]);
+            t = tstage[si_];
+          }
+          xr[j][c] = v;
+          tr[j][c] = t;
+          buf[(2 * j + c) * CS + z * TX + xl] = v;
+        }
       }
+      __syncthreads();  // also orders the staging reads above before the next batch's copies
+      if constexpr (MODE == M_CORRECT) {
+        // this batch's Q and R: committed before the next batch's operand so that
+        // waiting for all but the last group finds them complete
+#pragma unroll
+        for (int j = 0; j < QB; ++j) {
+          const int q = qb0 + j;
+          if (q < q_end) {
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+              const long gi = (long)(2 * q + c) * nxyz + site;
+              const int si_ = (2 * j + c) * NT + threadIdx.x;
+              cp_async(qstage + si_, a.q + gi, 16);
+              cp_async(rstage + si_, a.r + gi, 16);
+            }
+          }
+        }
+        cp_async_commit();
+      }
+      // the staging buffers are free again: fetch the next batch while this one computes
+      if (qb0 + QB < q_end) prefetch(qb0 + QB);
+    } else {
+#pragma unroll
+      for (int j = 0; j < QB; ++j) {
+        const int q = qb0 + j;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const long gi = (long)(2 * q + c) * nxyz + site;
+          const T v = q < q_end ? (a.xr ? reinterpret_cast<const T*>(a.xr)[gi] : to_r<R>(a.x[gi])) : T{R(0), R(0)};
+          xr[j][c] = v;
+          buf[(2 * j + c) * CS + z * TX + xl] = v;
+        }
+      }
+      __syncthreads();
     }
-    __syncthreads();
     fft_lines<N, -1, R, LINES, NT>(buf, base, TX, tw, [&](int, int k, T v) {
       R f = hz[k];
       return T{v.x * f, v.y * f};
     });
     fft_lines<N, +1, R, LINES, NT>(buf, base, TX, tw, Identity());
+    if constexpr (kPrefetch && MODE == M_CORRECT) {
+      // Q, R of this batch (own elements); the next batch's copies may still be in flight
+      if (qb0 + QB < q_end)
+        cp_async_wait_but_last();
+      else
+        cp_async_wait_all();
+    }
 
 #pragma unroll
     for (int j = 0; j < QB; ++j) {
       const int q = qb0 + j;
       if (q >= q_end) break;
       const long iu = (long)(2 * q) * nxyz + site, iv = iu + nxyz;
-      const T Tu = cadd(buf[(2 * j) * CS + z * TX + xl], txy[iu]);
-      const T Tv = cadd(buf[(2 * j + 1) * CS + z * TX + xl], txy[iv]);
+      const T Tu = cadd(buf[(2 * j) * CS + z * TX + xl], kPrefetch ? tr[j][0] : txy[iu]);
+      const T Tv = cadd(buf[(2 * j + 1) * CS + z * TX + xl], kPrefetch ? tr[j][1] : txy[iv]);
       if (MODE == M_ENERGY) {
         const double2 v = a.x[iv];
         const double2 tv = to_d(Tv);
@@ -238,8 +350,9 @@ __global__ void __launch_bounds__(N * TX, (sizeof(R) == 4 && N * TX >= 384) ? 2 
         for (int c = 0; c < 2; ++c) {
           const long i = c ? iv : iu;
           const T f = c ? fvr : fur;
-          const T rr = to_r<R>(a.r[i]);
-          const double2 yn = dadd(a.q[i], to_d(T{k1 * f.x, k1 * f.y}));
+          const int si_ = (2 * j + c) * NT + threadIdx.x;
+          const T rr = to_r<R>(kPrefetch ? rstage[si_] : a.r[i]);
+          const double2 yn = dadd(kPrefetch ? qstage[si_] : a.q[i], to_d(T{k1 * f.x, k1 * f.y}));
           a.ynew[i] = yn;
           a.pc[i] = to_d(T{rr.x - k2 * f.x, rr.y - k2 * f.y});
           yo[c] = yn;
@@ -341,8 +454,10 @@ __global__ void k_reduce(ReduceArgs a) {
   const int iz = (int)(s / ((long)a.N * a.N));
   double v = a.v_static ? a.v_static[s] : 0.0;
   v += a.drive * ((iz - a.N / 2) * a.a);
-  a.W[s] = 0.5 * a.beta * cb * cb - a.mu + v;  // U(n) - mu + V_ext
-  a.D[s] = make_double2(-a.g * r, -a.g * i);   // Delta = -g nu
+  double geff, dgeff;
+  pairing_geff(a.g, a.pair_alpha_n0, a.pair_c, n, &geff, &dgeff);
+  a.W[s] = 0.5 * a.beta * cb * cb + dgeff * (r * r + i * i) - a.mu + v;  // U(n) + dE_pair/dn - mu + V_ext
+  a.D[s] = make_double2(-geff * r, -geff * i);                            // Delta = -g_eff nu
 }
 
 // --------------------------------------------------------------- pointwise --
@@ -409,8 +524,8 @@ __global__ void k_density(PointwiseArgs a) {
 // E = a^3 sum_r [(alpha/2) tau + (3/10) beta (3 pi^2)^(2/3) n^(5/3) + g |nu|^2 + V n]
 // (Eq. pairing has + g_eff |kappa|^2); part holds sum_k 2 Re(v_k^* T v_k).
 __global__ void k_energy_sites(const double* part, int n_groups, const double* nd, const double2* nu,
-                               const double* v_static, double drive, double beta, double g, int N,
-                               double a, double* out) {
+                               const double* v_static, double drive, double beta, double g, double pair_alpha_n0,
+                               double pair_c, int N, double a, double* out) {
   const long nxyz = (long)N * N * N;
   const long s = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= nxyz) return;
@@ -426,7 +541,9 @@ __global__ void k_energy_sites(const double* part, int n_groups, const double* n
   v += drive * ((iz - N / 2) * a);
   const double2 w = nu[s];
   const double a3 = a * a * a;
-  out[s] = a3 * (ek + 0.3 * beta * cb * cb * n * cn * cn + g * (w.x * w.x + w.y * w.y) + v * n);
+  double geff, dgeff;
+  pairing_geff(g, pair_alpha_n0, pair_c, n, &geff, &dgeff);
+  out[s] = a3 * (ek + 0.3 * beta * cb * cb * n * cn * cn + geff * (w.x * w.x + w.y * w.y) + v * n);
   out[nxyz + s] = a3 * n;
 }
 
@@ -455,7 +572,7 @@ bool supported_n(int N) {
   }
 }
 int pencil_tx(int N) { return N % 8 == 0 ? 8 : 4; }
-int pencil_qb(int N, int) { return N >= 40 ? 2 : 4; }
+int pencil_qb(int N, int mixed) { return (N >= 40 || (mixed && N >= 32)) ? 2 : 4; }
 
 template <typename R, int N>
 static int planes_n(const PlanesArgs& a, cudaStream_t s) {
@@ -479,9 +596,9 @@ template <typename R, int N, int MODE>
 static int pencils_nm(const PencilArgs& a, cudaStream_t s) {
   using T = typename Cx<R>::T;
   constexpr int TX = (N % 8 == 0) ? 8 : 4;
-  constexpr int QB = (N >= 40) ? 2 : 4;  // states per batch; fewer at large N to bound registers
-  constexpr int CS = N * TX + (sizeof(T) == 8 ? 8 : 0);
-  const size_t smem = (size_t)QB * 2 * CS * sizeof(T) + N * sizeof(T) + N * sizeof(R);
+  // states per batch: fewer at large N (registers) and for the FP32 path from N = 32 (staging)
+  constexpr int QB = (N >= 40 || (sizeof(R) == 4 && N >= 32)) ? 2 : 4;
+  const size_t smem = (size_t)pencil_smem_bytes<T, N, TX, QB>();
   auto kern = k_pencils<R, N, TX, QB, MODE>;
   static bool attr = false;
   if (!attr) {
@@ -554,13 +671,19 @@ int launch_density(const PointwiseArgs& a, cudaStream_t s) {
   return cudaGetLastError() == cudaSuccess ? 0 : 3;
 }
 
+double pairing_lattice_c(double a, double alpha) {
+  const double PI = 3.14159265358979323846;
+  const double K = 2.442749607806335;  // Eq. geff_3D
+  return (1.0 / alpha) / (4.0 * PI * PI) * (PI / a) * K;
+}
+
 int launch_energy_sites(const double* part_ekin, int n_groups, const double* n, const double2* nu,
-                        const double* v_static, double drive, double beta, double g, int N,
-                        double a, double* e_site, cudaStream_t s) {
+                        const double* v_static, double drive, double beta, double g, double pair_alpha_n0,
+                        double pair_c, int N, double a, double* e_site, cudaStream_t s) {
   const int nt = 256;
   const long nxyz = (long)N * N * N;
-  k_energy_sites<<<(unsigned)((nxyz + nt - 1) / nt), nt, 0, s>>>(part_ekin, n_groups, n, nu, v_static,
-                                                                  drive, beta, g, N, a, e_site);
+  k_energy_sites<<<(unsigned)((nxyz + nt - 1) / nt), nt, 0, s>>>(part_ekin, n_groups, n, nu, v_static, drive, beta, g,
+                                                                  pair_alpha_n0, pair_c, N, a, e_site);
   return cudaGetLastError() == cudaSuccess ? 0 : 3;
 }
 

@@ -91,8 +91,19 @@ struct ReduceArgs {
   const double* v_static; // may be null
   double drive;           // A sin(Omega t)
   double beta, mu, g;
+  double pair_alpha_n0;   // Eq. g0: g0 = g (1 - pair_alpha_n0 * n), pair_alpha_n0 = alpha_p / n0
+  double pair_c;          // Eq. geff_3D: g_eff = g0 / (1 - pair_c g0); 0 without renormalisation
   int* err;               // set bit 0 if a density is not finite
 };
+
+// Effective pairing coupling and its density derivative (Eqs. g0, geff_3D).
+__host__ __device__ inline void pairing_geff(double g, double alpha_n0, double c, double n, double* geff,
+                                             double* dgeff) {
+  const double g0 = g * (1.0 - alpha_n0 * n);
+  const double den = 1.0 - c * g0;
+  *geff = g0 / den;
+  *dgeff = (-g * alpha_n0) / (den * den);
+}
 
 struct PointwiseArgs {
   // predictor + modifier for the first ABM step: p = Eq. p, m = Eq. m
@@ -125,8 +136,10 @@ int launch_reduce(const ReduceArgs& a, cudaStream_t s);
 int launch_predict(const PointwiseArgs& a, cudaStream_t s);
 int launch_density(const PointwiseArgs& a, cudaStream_t s);
 int launch_energy_sites(const double* part_ekin, int n_groups, const double* n, const double2* nu,
-                        const double* v_static, double drive, double beta, double g, int N,
-                        double a, double* e_site, cudaStream_t s);
+                        const double* v_static, double drive, double beta, double g, double pair_alpha_n0,
+                        double pair_c, int N, double a, double* e_site, cudaStream_t s);
+// pair_c of Eq. geff_3D for lattice constant a and kinetic coefficient alpha (meff = 1/alpha).
+double pairing_lattice_c(double a, double alpha);
 int launch_finite_check(const double2* x, long count, int* err, cudaStream_t s);
 // eta[q] = a^3 * sum over the pencil blocks of eta_part[q][block] (compensated).
 int launch_eta_reduce(const double* eta_part, int n_qp, int n_blocks, double a3, double* eta, cudaStream_t s);

@@ -66,6 +66,8 @@ extern "C" int lise_rhs_noalloc(const lise_params* p, const double* psi_dev, dou
   if (p->nx != p->ny || p->ny != p->nz || !supported_n(p->nx) || !(p->dx > 0.0) || p->n_qp < 1) return LISE_EINVAL;
   if (p->precision != LISE_FP64 && p->precision != LISE_MIXED) return LISE_EINVAL;
   if (p->device < 0 || p->device >= kMaxDevices) return LISE_EINVAL;
+  if (p->pair_lattice && !(p->alpha > 0.0)) return LISE_EINVAL;
+  if (p->pair_alpha != 0.0 && !(p->pair_n0 > 0.0)) return LISE_EINVAL;
   const int N = p->nx;
   const long nxyz = (long)N * N * N;
   const long ns = (long)p->n_qp * 2 * nxyz;
@@ -161,6 +163,8 @@ extern "C" int lise_rhs_noalloc(const lise_params* p, const double* psi_dev, dou
   r.beta = p->beta;
   r.mu = p->mu;
   r.g = p->g;
+  r.pair_alpha_n0 = p->pair_alpha != 0.0 ? p->pair_alpha / p->pair_n0 : 0.0;
+  r.pair_c = p->pair_lattice ? pairing_lattice_c(p->dx, p->alpha) : 0.0;
   r.err = err;
   if (launch_reduce(r, s)) return LISE_ECUDA;
 

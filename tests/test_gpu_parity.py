@@ -305,3 +305,32 @@ def test_phase_removal_keeps_stationary_state():
         ctx.step(40)
         got = ctx.state()
     assert rel(got, w.initial_state()) < 1e-13
+
+
+# -------------------------------------------- pairing coupling (Eqs. g0, geff_3D) ----
+
+def test_rhs_density_dependent_renormalised_pairing():
+    N, n_qp = 16, 6
+    psi = random_state(N, n_qp, seed=41, kmax=5)
+    kw = dict(alpha=1.0, beta=-0.5, mu=0.25, g=-1.2, pair_alpha=0.5, pair_n0=0.02, pair_lattice=True)
+    with L.Context(N, n_qp, **kw) as ctx:
+        got = ctx.rhs(psi, 0.0)
+    ref = O.rhs(O.Params(N, N, N, n_qp=n_qp, **kw), psi, 0.0)
+    assert rel(got, ref) < TOL_FP64_RHS
+
+
+def test_run_density_dependent_renormalised_pairing():
+    w = W.ufg_plane_waves(12, 10, noise_eps=0.2, g=-0.9, steps=6)
+    n0 = 2 * np.sum(w.amps[:, 1] ** 2) / (w.nxyz * w.a ** 3)
+    kw = dict(pair_alpha=0.4, pair_n0=n0, pair_lattice=True)
+    with L.Context.from_workload(w, **kw) as ctx:
+        ctx.set_state(w.initial_state(), 0.0, w.dt)
+        ctx.step(w.steps)
+        got = ctx.state()
+        E, N = ctx.energy()
+    s = O.Solver(oracle_params(w, **kw))
+    s.set_state(w.initial_state(), 0.0, w.dt)
+    s.step(w.steps)
+    assert rel(got, s.state()) < TOL_FP64_RUN
+    Eo, No = s.energy()
+    assert E == pytest.approx(Eo, rel=1e-11)

@@ -59,6 +59,13 @@ struct lise_ctx {
   double* eta = nullptr;
   double* eta_part = nullptr;
   int n_blocks_x = 0;
+  // CUDA graphs of kGraphSteps ABM steps, one per history configuration (y-slot
+  // parity x position of the derivative ring), replayed by lise_step
+  cudaGraphExec_t graph[2][4] = {};
+  double* drive_dev = nullptr;  // drive amplitudes of the reductions of one replay
+  double drive_host_t[16] = {};  // offsets (t - t_start) of those reductions, recorded at capture
+  int capturing = 0;            // > 0 while capturing: index of the next reduction
+  double2* D_base[4] = {nullptr, nullptr, nullptr, nullptr};  // the ring's allocations in ring order
   // per-launch timing (lise_profile)
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -214,6 +221,12 @@ int run_reduce(lise_ctx* c, int dslot, const double* avg_n, const double2* avg_n
   r.D = potentials ? c->Dl : nullptr;
   r.v_static = c->v_static;
   r.drive = drive_at(c, t);
+  r.drive_ptr = nullptr;
+  if (c->capturing) {  // inside a graph: the amplitude is refreshed before every replay
+    if (c->p.drive_A != 0.0) r.drive_ptr = c->drive_dev + (c->capturing - 1);
+    c->drive_host_t[c->capturing - 1] = t;
+    ++c->capturing;
+  }
   r.beta = c->p.beta;
   r.mu = c->p.mu;
   r.g = c->p.g;
@@ -412,8 +425,70 @@ int abm_step(lise_ctx* c) {
   return LISE_OK;
 }
 
+constexpr int kGraphSteps = 4;  // the history configuration repeats every 4 steps
+
+int ring_position(const lise_ctx* c) {
+  for (int k = 0; k < 4; ++k)
+    if (c->D[0] == c->D_base[k]) return k;
+  return -1;
+}
+
+void drop_graphs(lise_ctx* c) {
+  for (auto& row : c->graph)
+    for (auto& g : row)
+      if (g) {
+        cudaGraphExecDestroy(g);
+        g = nullptr;
+      }
+}
+
+// Capture kGraphSteps ABM steps from the current configuration into a graph.  The
+// host-side history state (t, slot parity, ring) is restored afterwards; the
+// caller launches the graph and then advances it.
+int capture_graph(lise_ctx* c, cudaGraphExec_t* out) {
+  const double t0 = c->t;
+  const int slot0 = c->y0_slot;
+  double2* d0[4] = {c->D[0], c->D[1], c->D[2], c->D[3]};
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return LISE_ECUDA;
+  c->capturing = 1;
+  int rc = LISE_OK;
+  for (int k = 0; k < kGraphSteps && rc == LISE_OK; ++k) rc = abm_step(c);
+  for (int k = 0; k < c->capturing - 1; ++k) c->drive_host_t[k] -= t0;
+  c->capturing = 0;
+  cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+  c->t = t0;
+  c->y0_slot = slot0;
+  for (int k = 0; k < 4; ++k) c->D[k] = d0[k];
+  if (rc != LISE_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess || !g) return LISE_ECUDA;
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  return e == cudaSuccess ? LISE_OK : LISE_ECUDA;
+}
+
+// kGraphSteps steps by one graph replay (capturing it on first use).
+int graph_steps(lise_ctx* c) {
+  const int rp = ring_position(c);
+  if (rp < 0) return LISE_ECUDA;
+  cudaGraphExec_t& g = c->graph[c->y0_slot][rp];
+  if (!g) TRY(capture_graph(c, &g));
+  if (c->p.drive_A != 0.0) {
+    double amp[2 * kGraphSteps];
+    for (int k = 0; k < 2 * kGraphSteps; ++k) amp[k] = drive_at(c, c->t + c->drive_host_t[k]);
+    TRY(cu(cudaMemcpyAsync(c->drive_dev, amp, sizeof(amp), cudaMemcpyHostToDevice, c->stream)));
+  }
+  TRY(cu(cudaGraphLaunch(g, c->stream)));
+  for (int k = 0; k < kGraphSteps; ++k) rotate_history(c, c->t + c->dt);
+  return LISE_OK;
+}
+
 void free_ctx(lise_ctx* c) {
-  void* ptrs[] = {c->eta, c->eta_part, c->slot[0], c->slot[1], c->D[0], c->D[1], c->D[2], c->D[3], c->M, c->PC, c->Q, c->R, c->TXY,
+  drop_graphs(c);
+  void* ptrs[] = {c->drive_dev, c->eta, c->eta_part, c->slot[0], c->slot[1], c->D[0], c->D[1], c->D[2], c->D[3], c->M, c->PC, c->Q, c->R, c->TXY,
                   c->part_n, c->part_nr, c->part_ni, c->dn[0], c->dn[1], c->dnu[0], c->dnu[1], c->W,
                   c->Dl, c->v_static, c->tw, c->hxy, c->hz, c->e_site, c->err};
   for (void* q : ptrs)
@@ -511,6 +586,8 @@ int lise_create(const lise_params* p, lise_ctx** out) {
   alloc((void**)&c->slot[0], sb);
   alloc((void**)&c->slot[1], sb);
   for (int k = 0; k < 4; ++k) alloc((void**)&c->D[k], sb);
+  for (int k = 0; k < 4; ++k) c->D_base[k] = c->D[k];
+  alloc((void**)&c->drive_dev, 2 * kGraphSteps * sizeof(double));
   alloc(&c->M, (size_t)c->ns * (c->mixed ? sizeof(float2) : sizeof(double2)));
   alloc((void**)&c->PC, sb);
   alloc((void**)&c->Q, sb);
@@ -580,6 +657,7 @@ static int set_state_common(lise_ctx* c, const double* psi, double t0, double dt
     TRY(cu(cudaStreamSynchronize(c->stream)));
     return LISE_ENONFINITE;
   }
+  if (dt != c->dt) drop_graphs(c);  // the step is baked into the captured kernels
   int rc = start_procedure(c, t0, dt);
   if (rc != LISE_OK) {
     c->sticky = rc;
@@ -604,8 +682,18 @@ int lise_step(lise_ctx* c, int n_steps, double dt) {
   if (!c->ready) return LISE_ESTATE;
   if (dt != c->dt) return LISE_EINVAL;
   if (cudaSetDevice(c->device) != cudaSuccess) return LISE_ECUDA;
-  for (int k = 0; k < n_steps; ++k) {
-    int rc = abm_step(c);
+  int k = 0;
+  while (k < n_steps) {
+    int rc;
+    // replay captured graphs for runs of kGraphSteps steps (plain launches while profiling,
+    // so that every kernel is bracketed by its own events)
+    if (!c->prof && n_steps - k >= kGraphSteps) {
+      rc = graph_steps(c);
+      k += kGraphSteps;
+    } else {
+      rc = abm_step(c);
+      ++k;
+    }
     if (rc != LISE_OK) {
       c->sticky = rc;
       return rc;
@@ -793,6 +881,7 @@ int lise_checkpoint_load(lise_ctx* c, const void* buf, size_t bytes) {
   off += c->nxyz * sizeof(double);
   TRY(cu(cudaMemcpyAsync(c->Dl, in + off, c->nxyz * sizeof(double2), cudaMemcpyHostToDevice, c->stream)));
   TRY(cu(cudaStreamSynchronize(c->stream)));
+  if (hd.dt != c->dt) drop_graphs(c);
   c->t = hd.t;
   c->dt = hd.dt;
   c->ready = 1;

@@ -453,7 +453,7 @@ __global__ void k_reduce(ReduceArgs a) {
   const double cb = cbrt(3.0 * PI * PI * n);
   const int iz = (int)(s / ((long)a.N * a.N));
   double v = a.v_static ? a.v_static[s] : 0.0;
-  v += a.drive * ((iz - a.N / 2) * a.a);
+  v += (a.drive_ptr ? *a.drive_ptr : a.drive) * ((iz - a.N / 2) * a.a);
   double geff, dgeff;
   pairing_geff(a.g, a.pair_alpha_n0, a.pair_c, n, &geff, &dgeff);
   a.W[s] = 0.5 * a.beta * cb * cb + dgeff * (r * r + i * i) - a.mu + v;  // U(n) + dE_pair/dn - mu + V_ext

@@ -90,6 +90,7 @@ struct ReduceArgs {
   double2* D;
   const double* v_static; // may be null
   double drive;           // A sin(Omega t)
+  const double* drive_ptr;  // if non-null, the drive amplitude is read from here (graph replays)
   double beta, mu, g;
   double pair_alpha_n0;   // Eq. g0: g0 = g (1 - pair_alpha_n0 * n), pair_alpha_n0 = alpha_p / n0
   double pair_c;          // Eq. geff_3D: g_eff = g0 / (1 - pair_c g0); 0 without renormalisation

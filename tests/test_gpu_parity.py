@@ -334,3 +334,23 @@ def test_run_density_dependent_renormalised_pairing():
     assert rel(got, s.state()) < TOL_FP64_RUN
     Eo, No = s.energy()
     assert E == pytest.approx(Eo, rel=1e-11)
+
+
+# ------------------------------------------------------------ CUDA graphs ----
+
+@pytest.mark.parametrize("workload", ["ufg", "drive"])
+def test_graph_replay_matches_plain_launches(workload):
+    # lise_step replays captured 4-step graphs; with per-launch profiling on it launches
+    # every kernel itself.  Both must give the same bits (13 steps = 3 replays + 1 plain).
+    w = W.ufg_plane_waves(16, 20, noise_eps=0.05) if workload == "ufg" else W.driven(16, 20, A=0.05)
+    out = []
+    for profiled in (False, True):
+        with L.Context.from_workload(w) as ctx:
+            ctx.set_state(w.initial_state(), 0.0, w.dt)
+            if profiled:
+                ctx.profile(True)
+            ctx.step(13)
+            ctx.step(8)  # graphs replayed again from another ring position
+            out.append((ctx.state(), ctx.t))
+    assert out[0][1] == out[1][1]
+    assert np.array_equal(out[0][0], out[1][0])

@@ -59,22 +59,24 @@ def algorithmic_per_qp_site(N, mixed):
                Mixed derivative launch: read y_{n+1}, T_xy; write y'_{n+1}.
     pointwise  (mixed only) predictor: read y_{n+1}, y_n, y'_{n+1}..y'_{n-2},
                p - c; write m, Q, R.
-    complex128 = 16 B per component; in the mixed path T_xy and m are complex64.
+    complex128 = 16 B per component.  The states y and Q are complex128; T_xy,
+    m, the y' ring, R and p - c are kept in the compute precision (complex64
+    in the mixed path).
     FFT convention: 5 n log2 n real flops per complex length-n transform."""
     L = log2(N)
     c16, cr = 16, (8 if mixed else 16)   # complex128 / compute-precision component
     planes_bytes = 2 * (cr + cr) + 2 * (c16 + cr)          # operand m, then operand y_{n+1}
-    correct_bytes = 2 * (cr + cr + 2 * c16) + 2 * (2 * c16)
+    correct_bytes = 2 * (cr + cr + c16 + cr) + 2 * (c16 + cr)
     fft_bdg = 2 * (2 * 5 * L + 4) + 24                     # z fwd+inv + multiply/add, BdG apply
     planes_flops = 2 * 2 * (2 * 2 * 5 * L + 3)              # 2 launches x 2 comps: 2D fwd+inv, multiply
     predict_flops = 92 + 13                                 # Eq. p/m, Q, R, densities of m
     if mixed:
-        deriv_bytes = 2 * (c16 + cr) + 2 * c16
-        predict_bytes = 2 * 7 * c16 + 2 * (cr + 2 * c16)
+        deriv_bytes = 2 * (c16 + cr) + 2 * cr
+        predict_bytes = 2 * (2 * c16 + 5 * cr) + 2 * (cr + c16 + cr)
         pencils_flops = 2 * fft_bdg + (16 + 13)
         pointwise = {"flops": predict_flops, "bytes": predict_bytes, "launches_per_step": 1}
     else:
-        deriv_bytes = 2 * (c16 + cr + 5 * c16) + 2 * (3 * c16 + cr)
+        deriv_bytes = 2 * (2 * c16 + 5 * cr) + 2 * (c16 + 3 * cr)
         pencils_flops = 2 * fft_bdg + (16 + 13) + predict_flops
         pointwise = {"flops": 0.0, "bytes": 0, "launches_per_step": 0}
     return {
@@ -333,11 +335,84 @@ def run_serve(args):
     return 0
 
 
+def run_batch(args):
+    """A batch of independent evolutions of uneven size through the serving loop.
+
+    --batch-evolutions evolutions (default 64, seed 7): lattice from {16, 24, 32, 40}^3,
+    state count uniform in [128, 4096], drive amplitude A uniform in [0, 0.05]
+    (Omega 0.3), mixed precision, --batch-steps ABM steps each.  All are ready at
+    t = 0; their summed device footprint is far above one GPU's memory, so the
+    server admits them in arrival order as budget frees up (waves).  The client
+    keeps at most --batch-host-gb of request states outstanding on the host
+    (queued or running), submitting the next evolution when one returns.
+    Reported: aggregate throughput, makespan and the admission schedule."""
+    import numpy as np
+    from paper_2009_00745_b300 import lise as L
+    from paper_2009_00745_b300 import workloads as Wl
+    rng = np.random.default_rng(7)
+    R = args.batch_evolutions
+    lattices = rng.choice([16, 24, 32, 40], R)
+    nqps = rng.integers(128, 4097, R)
+    amps = rng.uniform(0.0, 0.05, R)
+    base = {}
+    for n in sorted(set(int(x) for x in lattices)):
+        q = int(max(nq for nq, l in zip(nqps, lattices) if l == n))
+        w = Wl.ufg_plane_waves(n, q, noise_eps=1e-3, precision="mixed", steps=args.batch_steps)
+        base[n] = (w, w.initial_state())
+    budget = int(args.batch_budget_gb * 1e9)
+    host_cap = args.batch_host_gb * 1e9
+    fps = [L.footprint_bytes(int(l), int(nq), precision="mixed") for l, nq in zip(lattices, nqps)]
+    host_bytes = [32.0 * int(nq) * int(l) ** 3 for l, nq in zip(lattices, nqps)]
+    infos = [None] * R
+    with L.Server(budget, max_active=args.batch_max_active, steps_per_turn=args.serve_turn) as srv:
+        t0 = time.perf_counter()
+        pending = []  # (request index, server id)
+        nxt, held = 0, 0.0
+        while nxt < R or pending:
+            while nxt < R and (not pending or held + host_bytes[nxt] <= host_cap):
+                w, psi = base[int(lattices[nxt])]
+                nq = int(nqps[nxt])
+                rid = srv.submit(w.nx, nq, psi[:nq], 0.0, w.dt, args.batch_steps, a=w.a, alpha=w.alpha,
+                                 beta=w.beta, mu=w.mu, g=w.g, drive_A=float(amps[nxt]), drive_Omega=0.3,
+                                 precision="mixed")
+                pending.append((nxt, rid))
+                held += host_bytes[nxt]
+                nxt += 1
+            i, rid = pending.pop(0)  # arrival order: the oldest finishes no later than its successors start
+            infos[i] = srv.wait(rid, want_state=False)[1]
+            held -= host_bytes[i]
+        st = srv.stats()
+        wall = time.perf_counter() - t0
+    units = sum(float(nq) * int(l) ** 3 * args.batch_steps for nq, l in zip(nqps, lattices))
+    start = min(inf["submit_s"] for inf in infos)
+    makespan = max(inf["done_s"] for inf in infos) - start
+    # the admission schedule and, at 20 instants, how many evolutions (and GB) were resident
+    events = sorted((inf["admit_s"] - start, inf["done_s"] - start, i) for i, inf in enumerate(infos))
+    schedule = [{"i": int(i), "N": int(lattices[i]), "n_qp": int(nqps[i]), "A": round(float(amps[i]), 4),
+                 "footprint_gb": round(fps[i] / 1e9, 2), "admit_s": round(a, 3), "done_s": round(d, 3)}
+                for a, d, i in events]
+    timeline = []
+    for k in range(20):
+        tk = (k + 0.5) * makespan / 20
+        live = [i for a, d, i in events if a <= tk < d]
+        timeline.append({"t_s": round(tk, 2), "active": len(live),
+                         "resident_gb": round(sum(fps[i] for i in live) / 1e9, 1)})
+    line = {"mode": "batch", "evolutions": R, "steps_per_evolution": args.batch_steps, "precision": "mixed",
+            "hbm_budget_gb": args.batch_budget_gb, "max_active": args.batch_max_active,
+            "steps_per_turn": args.serve_turn, "sum_footprint_gb": round(sum(fps) / 1e9, 1),
+            "throughput": units / makespan, "unit": UNIT, "makespan_s": makespan, "wall_s": wall,
+            "peak_used_gb": st["peak_used_bytes"] / 1e9, "peak_active": st["peak_active"],
+            "all_ok": all(inf["status"] == 0 for inf in infos),
+            "active_timeline": timeline, "schedule": schedule}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def config_of(w, args):
     return {"workload": w.name, "lattice": f"{w.nx}^3", "n_qp": w.n_qp, "dt": w.dt,
             "precision": w.precision, "steps_in_workload": w.steps,
             "l2": "inputs larger than L2 (state + ABM history %.1f GB, no flush)" % (
-                10 * 16 * w.n_qp * 2 * w.nxyz / 1e9)}
+                (10 * 16 if w.precision == "fp64" else 3 * 16 + 7 * 8) * w.n_qp * 2 * w.nxyz / 1e9)}
 
 
 def main():
@@ -362,6 +437,13 @@ def main():
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     ap.add_argument("--serve-max-active", type=int, default=8)
     ap.add_argument("--serve-turn", type=int, default=5)
+    ap.add_argument("--batch", action="store_true",
+                    help="run a batch of uneven evolutions through the server in HBM-budgeted waves")
+    ap.add_argument("--batch-evolutions", type=int, default=64)
+    ap.add_argument("--batch-steps", type=int, default=500)
+    ap.add_argument("--batch-budget-gb", type=float, default=200.0)
+    ap.add_argument("--batch-host-gb", type=float, default=80.0)
+    ap.add_argument("--batch-max-active", type=int, default=16)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -377,6 +459,8 @@ def main():
         return run_drift(args, w)
     if args.serve:
         return run_serve(args)
+    if args.batch:
+        return run_batch(args)
 
     import numpy as np
     import torch

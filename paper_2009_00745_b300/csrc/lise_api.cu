@@ -1,11 +1,13 @@
 // lise_api.cu -- host side of the C ABI declared in include/lise.h.
 //
 // A context owns the ABM history on the device:
-//   y_n, y_{n-1}             two state slots (swapped every step)
-//   y'_n .. y'_{n-3}         a ring of four derivative slots
-//   m_{n+1}, p_n - c_n       modifier (Eq. m) and the difference it uses
-//   Q, R                     the corrector's precombined history (lise_kernels.cuh)
+//   y_n, y_{n-1}             two state slots (swapped every step), complex128
+//   y'_n .. y'_{n-3}         a ring of four derivative slots, compute precision
+//   m_{n+1}, p_n - c_n       modifier (Eq. m) and the difference it uses, compute precision
+//   Q (complex128), R        the corrector's precombined history (lise_kernels.cuh)
 //   T_xy scratch             the in-plane kinetic part of the current operand
+// (the compute precision is FP64, or FP32 in the mixed path; values kept in it are
+// formed in it, so they are stored without rounding)
 // plus per-group density partial sums, reduced densities and the potentials
 // W = U(n) - mu + V_ext and Delta of the operand of the next right-hand side.
 //
@@ -38,9 +40,13 @@ struct lise_ctx {
   int qg = 0, n_groups = 0;
   double2* slot[2] = {nullptr, nullptr};
   int y0_slot = 0;                 // slot holding y_n
-  double2* D[4] = {nullptr, nullptr, nullptr, nullptr};  // D[k] = y'_{n-k}
+  void* D[4] = {nullptr, nullptr, nullptr, nullptr};  // D[k] = y'_{n-k}, compute precision
   void* M = nullptr;  // m_{n+1}, complex of the compute precision (only an H psi operand)
-  double2 *PC = nullptr, *Q = nullptr, *R = nullptr;
+  double2* Q = nullptr;
+  // R and p - c (compute precision) share one allocation, R first; during the start
+  // procedure the block holds the complex128 predictor state instead
+  void* RPC = nullptr;
+  void *R = nullptr, *PC = nullptr;
   void* TXY = nullptr;
   double *part_n = nullptr, *part_nr = nullptr, *part_ni = nullptr;
   double* dn[2] = {nullptr, nullptr};
@@ -49,6 +55,8 @@ struct lise_ctx {
   double2* Dl = nullptr;
   double* v_static = nullptr;
   void *tw = nullptr, *hxy = nullptr, *hz = nullptr;
+  uint32_t* ozb = nullptr;  // FP64 tensor-core kinetic operator: D2 digit fragments
+  int oz_sD = 0;
   double* e_site = nullptr;
   int* err = nullptr;
   double t = 0.0, dt = 0.0;
@@ -65,7 +73,7 @@ struct lise_ctx {
   double* drive_dev = nullptr;  // drive amplitudes of the reductions of one replay
   double drive_host_t[16] = {};  // offsets (t - t_start) of those reductions, recorded at capture
   int capturing = 0;            // > 0 while capturing: index of the next reduction
-  double2* D_base[4] = {nullptr, nullptr, nullptr, nullptr};  // the ring's allocations in ring order
+  void* D_base[4] = {nullptr, nullptr, nullptr, nullptr};  // the ring's allocations in ring order
   // per-launch timing (lise_profile)
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -110,8 +118,9 @@ Footprint footprint(const lise_params* p) {
   const long ns = (long)p->n_qp * 2 * nxyz;
   int qg, ng;
   choose_groups((int)N, p->n_qp, &qg, &ng);
-  // 2 y slots, 4 y', P-C, Q, R in complex128; m in the compute precision
-  f.state = 9 * (size_t)ns * sizeof(double2) + (size_t)ns * (p->precision == LISE_MIXED ? sizeof(float2) : sizeof(double2));
+  // 2 y slots and Q in complex128; 4 y', m, R and P-C in the compute precision
+  const size_t rc = p->precision == LISE_MIXED ? sizeof(float2) : sizeof(double2);
+  f.state = 3 * (size_t)ns * sizeof(double2) + 7 * (size_t)ns * rc;
   f.txy = (size_t)ns * (p->precision == LISE_MIXED ? sizeof(float2) : sizeof(double2));
   f.partials = 3 * (size_t)ng * nxyz * sizeof(double);
   f.small = (size_t)nxyz * (2 * sizeof(double) + 2 * sizeof(double2) + sizeof(double) + sizeof(double2) +
@@ -161,6 +170,8 @@ PencilArgs pencil_base(const lise_ctx* c) {
   a.D = c->Dl;
   a.tw = c->tw;
   a.hz = c->hz;
+  a.ozb = c->ozb;
+  a.oz_sD = c->oz_sD;
   a.n_qp = c->p.n_qp;
   a.qg = c->qg;
   a.part_n = c->part_n;
@@ -177,6 +188,8 @@ int run_planes(lise_ctx* c, const double2* x, const void* xr = nullptr) {
   a.txy = c->TXY;
   a.tw = c->tw;
   a.hxy = c->hxy;
+  a.ozb = c->ozb;
+  a.oz_sD = c->oz_sD;
   a.n_planes = (long)c->p.n_qp * 2 * c->N;
   return timed(c, LISE_KC_PLANES, [&] { return launch_planes(c->N, c->mixed, a, c->stream) ? LISE_ECUDA : LISE_OK; });
 }
@@ -256,7 +269,7 @@ double2 cx(double re, double im) { return make_double2(re, im); }
 // -i H psi_in there.  The last term's kernel accumulates the densities of
 // psi_out into the partials.  The series term lives in the Q array, which the
 // start procedure fills only at its end.
-int taylor4(lise_ctx* c, const double2* psi_in, double2* psi_out, double2* dslot, double dt) {
+int taylor4(lise_ctx* c, const double2* psi_in, double2* psi_out, void* dslot, double dt) {
   TRY(run_planes(c, psi_in));
   TRY(run_eta(c, psi_in));  // eta of the starting state with this series' Hamiltonian
   PencilArgs a = pencil_base(c);
@@ -295,8 +308,8 @@ int fetch_err(lise_ctx* c) {
   return LISE_OK;
 }
 
-PointwiseArgs predict_args(lise_ctx* c, const double2* y0, const double2* y1, const double2* d0,
-                           const double2* d1, const double2* d2, const double2* d3, double h) {
+PointwiseArgs predict_args(lise_ctx* c, const double2* y0, const double2* y1, const void* d0, const void* d1,
+                           const void* d2, const void* d3, double h) {
   PointwiseArgs w;
   std::memset(&w, 0, sizeof(w));
   w.y0 = y0;
@@ -323,7 +336,7 @@ PointwiseArgs predict_args(lise_ctx* c, const double2* y0, const double2* y1, co
 // y_{n+1} (in the y_{n-1} slot) becomes y_n; y'_{n+1} (in D[3]) becomes D[0]
 void rotate_history(lise_ctx* c, double t1) {
   c->y0_slot = 1 - c->y0_slot;
-  double2* d3 = c->D[3];
+  void* d3 = c->D[3];
   c->D[3] = c->D[2];
   c->D[2] = c->D[1];
   c->D[1] = c->D[0];
@@ -339,9 +352,9 @@ int start_procedure(lise_ctx* c, double t0, double dt) {
   TRY(run_reduce(c, 0, nullptr, nullptr, true, t0));
   for (int s = 0; s < 3; ++s) {
     const double ts = t0 + s * dt;
-    // predictor with H(t_s): psi_pre into R (free until the end of the start);
-    // y'_s = -i H(t_s) y_s into D[3 - s]
-    TRY(taylor4(c, cur, c->R, c->D[3 - s], dt));
+    // predictor with H(t_s): psi_pre into the R/P-C block (free until the end of the
+    // start); y'_s = -i H(t_s) y_s into D[3 - s]
+    TRY(taylor4(c, cur, static_cast<double2*>(c->RPC), c->D[3 - s], dt));
     // corrector densities (n_pre + n(t_s)) / 2, potentials at t_s + dt/2
     TRY(run_reduce(c, 1, c->dn[0], c->dnu[0], true, ts + 0.5 * dt));
     // psi(t_s + dt) = exp(-i H_cor dt) psi(t_s), densities into dn[0] at t_{s+1}
@@ -356,11 +369,12 @@ int start_procedure(lise_ctx* c, double t0, double dt) {
   TRY(run_eta(c, cur));
   PencilArgs a = pencil_base(c);
   a.x = cur;
-  a.out = c->D[0];
+  a.out = nullptr;
+  a.dslot = c->D[0];
   TRY(run_pencils(c, M_RHS, a));
   c->y0_slot = (cur == c->slot[0]) ? 0 : 1;
   // p_3 - c_3 := 0; predictor and modifier of the first ABM step
-  TRY(cu(cudaMemsetAsync(c->PC, 0, (size_t)c->ns * sizeof(double2), c->stream)));
+  TRY(cu(cudaMemsetAsync(c->PC, 0, (size_t)c->ns * (c->mixed ? sizeof(float2) : sizeof(double2)), c->stream)));
   PointwiseArgs w = predict_args(c, c->slot[c->y0_slot], c->slot[1 - c->y0_slot], c->D[0], c->D[1], c->D[2],
                                  c->D[3], dt);
   TRY(timed(c, LISE_KC_POINTWISE, [&] { return launch_predict(w, c->stream) ? LISE_ECUDA : LISE_OK; }));
@@ -398,7 +412,8 @@ int abm_step(lise_ctx* c) {
     // forms m, Q, R and the densities of m from the history
     PencilArgs b = pencil_base(c);
     b.x = ynm1;
-    b.out = c->D[3];
+    b.out = nullptr;
+    b.dslot = c->D[3];
     TRY(run_pencils(c, M_RHS, b));
     PointwiseArgs w = predict_args(c, ynm1, yn, c->D[3], c->D[0], c->D[1], c->D[2], h);
     TRY(timed(c, LISE_KC_POINTWISE, [&] { return launch_predict(w, c->stream) ? LISE_ECUDA : LISE_OK; }));
@@ -448,7 +463,7 @@ void drop_graphs(lise_ctx* c) {
 int capture_graph(lise_ctx* c, cudaGraphExec_t* out) {
   const double t0 = c->t;
   const int slot0 = c->y0_slot;
-  double2* d0[4] = {c->D[0], c->D[1], c->D[2], c->D[3]};
+  void* d0[4] = {c->D[0], c->D[1], c->D[2], c->D[3]};
   cudaGraph_t g = nullptr;
   if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return LISE_ECUDA;
   c->capturing = 1;
@@ -488,9 +503,9 @@ int graph_steps(lise_ctx* c) {
 
 void free_ctx(lise_ctx* c) {
   drop_graphs(c);
-  void* ptrs[] = {c->drive_dev, c->eta, c->eta_part, c->slot[0], c->slot[1], c->D[0], c->D[1], c->D[2], c->D[3], c->M, c->PC, c->Q, c->R, c->TXY,
+  void* ptrs[] = {c->drive_dev, c->eta, c->eta_part, c->slot[0], c->slot[1], c->D[0], c->D[1], c->D[2], c->D[3], c->M, c->RPC, c->Q, c->TXY,
                   c->part_n, c->part_nr, c->part_ni, c->dn[0], c->dn[1], c->dnu[0], c->dnu[1], c->W,
-                  c->Dl, c->v_static, c->tw, c->hxy, c->hz, c->e_site, c->err};
+                  c->Dl, c->v_static, c->tw, c->hxy, c->hz, c->ozb, c->e_site, c->err};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -585,13 +600,17 @@ int lise_create(const lise_params* p, lise_ctx** out) {
   };
   alloc((void**)&c->slot[0], sb);
   alloc((void**)&c->slot[1], sb);
-  for (int k = 0; k < 4; ++k) alloc((void**)&c->D[k], sb);
+  const size_t sr = (size_t)c->ns * (c->mixed ? sizeof(float2) : sizeof(double2));  // compute-precision array
+  for (int k = 0; k < 4; ++k) alloc(&c->D[k], sr);
   for (int k = 0; k < 4; ++k) c->D_base[k] = c->D[k];
   alloc((void**)&c->drive_dev, 2 * kGraphSteps * sizeof(double));
-  alloc(&c->M, (size_t)c->ns * (c->mixed ? sizeof(float2) : sizeof(double2)));
-  alloc((void**)&c->PC, sb);
+  alloc(&c->M, sr);
   alloc((void**)&c->Q, sb);
-  alloc((void**)&c->R, sb);
+  alloc(&c->RPC, 2 * sr);  // R, P-C; at least one complex128 state (start procedure)
+  if (c->RPC) {
+    c->R = c->RPC;
+    c->PC = static_cast<char*>(c->RPC) + sr;
+  }
   alloc(&c->TXY, (size_t)c->ns * (c->mixed ? sizeof(float2) : sizeof(double2)));
   const size_t pb = (size_t)c->n_groups * c->nxyz * sizeof(double);
   alloc((void**)&c->part_n, pb);
@@ -609,6 +628,12 @@ int lise_create(const lise_params* p, lise_ctx** out) {
   alloc(&c->hxy, c->N * rs);
   alloc(&c->hz, c->N * rs);
   alloc((void**)&c->e_site, 2 * c->nxyz * sizeof(double));
+  std::vector<uint32_t> ozt;
+  if (ozaki_path(c->N, c->mixed)) {
+    ozt.resize(ozaki_table_words(c->N));
+    c->oz_sD = ozaki_table(c->N, p->dx, p->alpha, ozt.data());
+    alloc((void**)&c->ozb, ozt.size() * sizeof(uint32_t));
+  }
   c->n_blocks_x = pencil_blocks_x(c->N);
   if (p->remove_phase) {
     alloc((void**)&c->eta, (size_t)p->n_qp * sizeof(double));
@@ -627,6 +652,8 @@ int lise_create(const lise_params* p, lise_ctx** out) {
     rc = cu(cudaMemcpyAsync(c->tw, tw.data(), tw.size(), cudaMemcpyHostToDevice, c->stream));
     if (rc == LISE_OK) rc = cu(cudaMemcpyAsync(c->hxy, hxy.data(), hxy.size(), cudaMemcpyHostToDevice, c->stream));
     if (rc == LISE_OK) rc = cu(cudaMemcpyAsync(c->hz, hz.data(), hz.size(), cudaMemcpyHostToDevice, c->stream));
+    if (rc == LISE_OK && c->ozb)
+      rc = cu(cudaMemcpyAsync(c->ozb, ozt.data(), ozt.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, c->stream));
     if (rc == LISE_OK && p->v_static)
       rc = cu(cudaMemcpyAsync(c->v_static, p->v_static, c->nxyz * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     if (rc == LISE_OK) rc = cu(cudaMemsetAsync(c->err, 0, sizeof(int), c->stream));
@@ -790,9 +817,9 @@ int lise_rhs(lise_ctx* c, const double* psi, double t, double* dpsi_out) {
   TRY(run_eta(c, x));
   PencilArgs a = pencil_base(c);
   a.x = x;
-  a.out = c->D[0];
+  a.out = c->slot[1];
   TRY(run_pencils(c, M_RHS, a));
-  TRY(cu(cudaMemcpyAsync(dpsi_out, c->D[0], (size_t)c->ns * sizeof(double2), cudaMemcpyDeviceToHost, c->stream)));
+  TRY(cu(cudaMemcpyAsync(dpsi_out, c->slot[1], (size_t)c->ns * sizeof(double2), cudaMemcpyDeviceToHost, c->stream)));
   TRY(cu(cudaStreamSynchronize(c->stream)));
   return fetch_err(c);
 }
@@ -800,7 +827,7 @@ int lise_rhs(lise_ctx* c, const double* psi, double t, double* dpsi_out) {
 // ---------------------------------------------------------------- checkpoint --
 namespace {
 struct CkptHeader {
-  char magic[8];        // "LISECKP1"
+  char magic[8];        // "LISECKP2"
   int N, n_qp, precision, y0_slot_unused;
   double t, dt;
   long long ns, nxyz;
@@ -817,15 +844,17 @@ void ckpt_arrays(lise_ctx* c, void* arr[kCkptArrays], size_t sz[kCkptArrays]) {
   arr[7] = c->PC;
   arr[8] = c->Q;
   arr[9] = c->R;
-  for (int k = 0; k < kCkptArrays; ++k) sz[k] = (size_t)c->ns * sizeof(double2);
-  sz[6] = (size_t)c->ns * (c->mixed ? sizeof(float2) : sizeof(double2));
+  // y_n, y_{n-1} and Q are complex128; the y' ring, m, P-C and R the compute precision
+  const size_t sr = (size_t)c->ns * (c->mixed ? sizeof(float2) : sizeof(double2));
+  for (int k = 0; k < kCkptArrays; ++k) sz[k] = sr;
+  sz[0] = sz[1] = sz[8] = (size_t)c->ns * sizeof(double2);
 }
 }  // namespace
 
 size_t lise_checkpoint_bytes(const lise_ctx* c) {
   if (!c) return 0;
-  return sizeof(CkptHeader) + (kCkptArrays - 1) * (size_t)c->ns * sizeof(double2) +
-         (size_t)c->ns * (c->mixed ? sizeof(float2) : sizeof(double2)) +
+  return sizeof(CkptHeader) + 3 * (size_t)c->ns * sizeof(double2) +
+         (kCkptArrays - 3) * (size_t)c->ns * (c->mixed ? sizeof(float2) : sizeof(double2)) +
          (size_t)c->nxyz * (sizeof(double) + sizeof(double2));
 }
 
@@ -836,7 +865,7 @@ int lise_checkpoint_save(lise_ctx* c, void* buf, size_t bytes) {
   TRY(fetch_err(c));
   CkptHeader hd;
   std::memset(&hd, 0, sizeof(hd));
-  std::memcpy(hd.magic, "LISECKP1", 8);
+  std::memcpy(hd.magic, "LISECKP2", 8);
   hd.N = c->N;
   hd.n_qp = c->p.n_qp;
   hd.precision = c->p.precision;
@@ -864,7 +893,7 @@ int lise_checkpoint_load(lise_ctx* c, const void* buf, size_t bytes) {
   if (bytes < lise_checkpoint_bytes(c)) return LISE_EINVAL;
   CkptHeader hd;
   std::memcpy(&hd, buf, sizeof(hd));
-  if (std::memcmp(hd.magic, "LISECKP1", 8) != 0 || hd.N != c->N || hd.n_qp != c->p.n_qp ||
+  if (std::memcmp(hd.magic, "LISECKP2", 8) != 0 || hd.N != c->N || hd.n_qp != c->p.n_qp ||
       hd.precision != c->p.precision || hd.ns != c->ns || hd.nxyz != c->nxyz || !(hd.dt != 0.0))
     return LISE_EINVAL;
   if (cudaSetDevice(c->device) != cudaSuccess) return LISE_ECUDA;

@@ -1,8 +1,13 @@
 // lise_kernels.cu -- device kernels of the two-component TDSLDA step and their
 // launchers.  See lise_kernels.cuh for the operator split and the modes.
+#include <algorithm>
+#include <cmath>
 #include <cstdio>
+#include <cstring>
+#include <vector>
 
 #include "lise_kernels.cuh"
+#include "lise_ozaki.cuh"
 
 namespace lise {
 
@@ -72,6 +77,14 @@ __device__ __forceinline__ void dens_acc(double2 u, double2 v, double& sn, doubl
   sr += u.x * v.x + u.y * v.y;
   si += u.y * v.x - u.x * v.y;
 }
+// The same from FP32 operands (the mixed path, whose densities only set the potentials
+// of its FP32 H psi): products in FP32 (relative rounding 2^-24, the level of the FP32
+// potentials themselves), sums in FP64.
+__device__ __forceinline__ void dens_acc(float2 u, float2 v, double& sn, double& sr, double& si) {
+  sn += f2d_bits(2.0f * fmaf(v.x, v.x, v.y * v.y));
+  sr += f2d_bits(fmaf(u.x, v.x, u.y * v.y));
+  si += f2d_bits(fmaf(u.y, v.x, -(u.x * v.y)));
+}
 
 // Asynchronous global -> shared copies (no register staging).  Each thread copies
 // and later reads only its own elements, so its own wait suffices.
@@ -134,6 +147,196 @@ __global__ void __launch_bounds__(NT) k_planes(PlanesArgs a) {
   }
 }
 
+// --------------------------------------------------------- planes, FP64 MMA --
+// T_xy x = T_x x + T_y x on PB planes per block with the FP64-accurate tensor-core
+// product of lise_ozaki.cuh.  Groups of lines sharing one exponent: (plane, re/im).
+//   T_x: Out[y][x] = sum_x' X[y][x'] D2[x][x']   (data rows y, K = x')
+//   T_y: Out[y][x] = sum_y' D2[y][y'] X[y'][x]    (data rows x via a transposed load, K = y')
+// Both are exact 64-bit integer sums of one scale, added in shared memory, then
+// converted to FP64 once.
+template <int N> struct OzPlanes {
+  static constexpr int PB = N <= 16 ? 4 : (N <= 32 ? 2 : 1);
+  static constexpr int RS = N + 8;  // padded digit row (bf16): conflict-free ldmatrix rows
+  static constexpr int G = PB * 2;  // exponent groups
+  static constexpr size_t dig_bytes = (size_t)oz::S * G * N * RS * 2;
+  static constexpr size_t smem = dig_bytes + (size_t)G * N * N * 8;
+};
+
+template <int N>
+__global__ void __launch_bounds__(256) k_planes_oz(PlanesArgs a) {
+  using P = OzPlanes<N>;
+  constexpr int PB = P::PB, RS = P::RS, G = P::G;
+  constexpr int NT = 256, NW = NT / 32;
+  constexpr int KS = N / 16, NTILE = N / 8, MT = G * N / 16;
+  constexpr int EPT = PB * N * N / NT;  // elements per thread
+  static_assert(PB * N * N % NT == 0, "plane block size");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned short* dig = reinterpret_cast<unsigned short*>(smem_raw);  // [S][G][N][RS]
+  long long* acc64 = reinterpret_cast<long long*>(smem_raw + P::dig_bytes);  // [G][N][N]
+  __shared__ unsigned ered[NW][G];
+  __shared__ unsigned Eg[G];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const long plane0 = (long)blockIdx.x * PB;
+  const long left = a.n_planes - plane0;
+  const int np = left < PB ? (int)left : PB;
+  // the operand: x, or xr when the operand is stored in the compute precision (here FP64)
+  const double2* src = (a.xr ? reinterpret_cast<const double2*>(a.xr) : a.x) + plane0 * N * N;
+
+  // 1. the operand and the largest exponent of each (plane, re/im) group
+  double2 v[EPT];
+  unsigned em[G];
+#pragma unroll
+  for (int g = 0; g < G; ++g) em[g] = 0;
+#pragma unroll
+  for (int r = 0; r < EPT; ++r) {
+    const int i = tid + r * NT;
+    const int pl = (r * NT) / (N * N);  // the same for the whole block at this r
+    v[r] = pl < np ? src[i] : make_double2(0.0, 0.0);
+    em[2 * pl] = max(em[2 * pl], oz::exp_field(v[r].x));
+    em[2 * pl + 1] = max(em[2 * pl + 1], oz::exp_field(v[r].y));
+  }
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    const unsigned m = oz::warp_max(em[g]);
+    if (lane == 0) ered[w][g] = m;
+  }
+  __syncthreads();
+  if (tid < G) {
+    unsigned m = 0;
+#pragma unroll
+    for (int k = 0; k < NW; ++k) m = max(m, ered[k][tid]);
+    Eg[tid] = m;
+  }
+  __syncthreads();
+
+  // 2. digits: dig[d][g][y][x]
+#pragma unroll
+  for (int r = 0; r < EPT; ++r) {
+    const int i = tid + r * NT;
+    const int pl = i / (N * N), rem = i % (N * N);
+    const int y = rem / N, x = rem % N;
+#pragma unroll
+    for (int ri = 0; ri < 2; ++ri) {
+      const int g = 2 * pl + ri;
+      unsigned short d[oz::S];
+      oz::split(ri ? v[r].y : v[r].x, Eg[g], d);
+#pragma unroll
+      for (int k = 0; k < oz::S; ++k) dig[((k * G + g) * N + y) * RS + x] = d[k];
+    }
+  }
+  __syncthreads();
+
+  const int gq = lane >> 2, t4 = lane & 3;
+  const int mi = lane >> 3, r8 = lane & 7;
+  // 3a. T_x: data rows (g, y), K = x'
+  for (int job = w; job < MT * NTILE; job += NW) {
+    const int mt = job / NTILE, nt = job % NTILE;
+    const int g = mt / (N / 16), y0 = (mt % (N / 16)) * 16;
+    uint32_t b[oz::S][KS][2];
+    oz::load_b<KS>(b, a.ozb, nt, NTILE);
+    int iacc[oz::S][4];
+    oz::tile_levels<KS, false>(iacc, b, [&](int k, int ks) {
+      return dig + ((k * G + g) * N + y0 + r8 + 8 * (mi & 1)) * RS + ks * 16 + 8 * (mi >> 1);
+    });
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      int lv[oz::S];
+#pragma unroll
+      for (int L = 0; L < oz::S; ++L) lv[L] = iacc[L][e];
+      const int y = y0 + gq + 8 * (e >> 1), x = nt * 8 + 2 * t4 + (e & 1);
+      acc64[(g * N + y) * N + x] = oz::combine(lv);
+    }
+  }
+  __syncthreads();
+  // 3b. T_y: data rows (g, x) by a transposed load of dig[.][g][y'][x], K = y'
+  for (int job = w; job < MT * NTILE; job += NW) {
+    const int mt = job / NTILE, nt = job % NTILE;
+    const int g = mt / (N / 16), x0 = (mt % (N / 16)) * 16;
+    uint32_t b[oz::S][KS][2];
+    oz::load_b<KS>(b, a.ozb, nt, NTILE);
+    int iacc[oz::S][4];
+    oz::tile_levels<KS, true>(iacc, b, [&](int k, int ks) {
+      return dig + ((k * G + g) * N + ks * 16 + 8 * (mi >> 1) + r8) * RS + x0 + 8 * (mi & 1);
+    });
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      int lv[oz::S];
+#pragma unroll
+      for (int L = 0; L < oz::S; ++L) lv[L] = iacc[L][e];
+      const int x = x0 + gq + 8 * (e >> 1), y = nt * 8 + 2 * t4 + (e & 1);
+      acc64[(g * N + y) * N + x] += oz::combine(lv);
+    }
+  }
+  __syncthreads();
+
+  // 4. FP64 values, coalesced store of T_xy x
+  double2* dst = reinterpret_cast<double2*>(a.txy) + plane0 * N * N;
+  for (int i = tid; i < np * N * N; i += NT) {
+    const int pl = i / (N * N), rem = i % (N * N);
+    const double re = oz::to_double(acc64[(2 * pl) * N * N + rem], oz::out_scale(a.oz_sD, Eg[2 * pl]));
+    const double im = oz::to_double(acc64[(2 * pl + 1) * N * N + rem], oz::out_scale(a.oz_sD, Eg[2 * pl + 1]));
+    dst[i] = make_double2(re, im);
+  }
+}
+
+// T_z x on the tensor cores for one pencils batch (FP64 path, N % 16 == 0):
+// operand xr[j][c] of this thread's site (z, xl); result T_z x into buf[(2j + c) CS + z TX + xl].
+// Exponent groups: (state j, component c, re/im) over the block's (z, x) tile; data
+// rows: columns col = group TX + xl of dig[d][col][z'], K = z'.
+template <int N, int TX, int QB, int CS>
+__device__ __forceinline__ void oz_pencils_tz(const double2 (&xr)[QB][2], double2* buf, unsigned short* dig,
+                                              unsigned* ered, unsigned* Eg, const uint32_t* ozb, int sD, int z,
+                                              int xl) {
+  constexpr int NT = N * TX, NW = NT / 32, NE = QB * 4, RS = N + 8;
+  constexpr int KS = N / 16, NTILE = N / 8, NCOL = NE * TX, MT = NCOL / 16;
+  static_assert(NCOL % 16 == 0, "pencil columns");
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+#pragma unroll
+  for (int g = 0; g < NE; ++g) {
+    const double2 v = xr[g >> 2][(g >> 1) & 1];
+    const unsigned m = oz::warp_max(oz::exp_field((g & 1) ? v.y : v.x));
+    if (lane == 0) ered[w * NE + g] = m;
+  }
+  __syncthreads();
+  if (tid < NE) {
+    unsigned m = 0;
+#pragma unroll
+    for (int k = 0; k < NW; ++k) m = max(m, ered[k * NE + tid]);
+    Eg[tid] = m;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int g = 0; g < NE; ++g) {
+    const double2 v = xr[g >> 2][(g >> 1) & 1];
+    unsigned short d[oz::S];
+    oz::split((g & 1) ? v.y : v.x, Eg[g], d);
+#pragma unroll
+    for (int k = 0; k < oz::S; ++k) dig[(k * NCOL + g * TX + xl) * RS + z] = d[k];
+  }
+  __syncthreads();
+  const int gq = lane >> 2, t4 = lane & 3, mi = lane >> 3, r8 = lane & 7;
+  double* out = reinterpret_cast<double*>(buf);
+  for (int job = w; job < MT * NTILE; job += NW) {
+    const int mt = job / NTILE, nt = job % NTILE;
+    uint32_t b[oz::S][KS][2];
+    oz::load_b<KS>(b, ozb, nt, NTILE);
+    int iacc[oz::S][4];
+    oz::tile_levels<KS, false>(iacc, b, [&](int k, int ks) {
+      return dig + (k * NCOL + mt * 16 + r8 + 8 * (mi & 1)) * RS + ks * 16 + 8 * (mi >> 1);
+    });
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      int lv[oz::S];
+#pragma unroll
+      for (int L = 0; L < oz::S; ++L) lv[L] = iacc[L][e];
+      const int col = mt * 16 + gq + 8 * (e >> 1), zz = nt * 8 + 2 * t4 + (e & 1);
+      const int g = col / TX, x2 = col % TX;
+      out[2 * ((g >> 1) * CS + zz * TX + x2) + (g & 1)] = oz::to_double(oz::combine(lv), oz::out_scale(sD, Eg[g]));
+    }
+  }
+  __syncthreads();
+}
+
 // ----------------------------------------------------------------- pencils --
 // Byte offset of the prefetch staging area in the pencils kernel's shared memory
 // (after the FFT buffer, the twiddles and the kinetic factors), 16-byte aligned.
@@ -141,11 +344,17 @@ template <typename T, int N, int TX, int QB>
 __host__ __device__ constexpr int pencil_stage_offset() {
   return (((QB * 2 * (N * TX + (sizeof(T) == 8 ? 8 : 0)) + N) * (int)sizeof(T) + N * (int)sizeof(T) / 2) + 15) / 16 * 16;
 }
+// FP64 tensor-core path (lise_ozaki.cuh) on lattices with N % 16 == 0
+template <typename R, int N>
+__host__ __device__ constexpr bool pencil_oz() { return sizeof(R) == 8 && N % 16 == 0; }
 template <typename T, int N, int TX, int QB>
 __host__ __device__ constexpr int pencil_smem_bytes() {
   // staging only for the FP32 compute precision (see kPrefetch in k_pencils): the next
-  // batch's operand and T_xy, and this batch's Q and R (corrector)
-  return pencil_stage_offset<T, N, TX, QB>() + (sizeof(T) == 8 ? QB * 2 * N * TX * (16 + (int)sizeof(T) + 32) : 0);
+  // batch's operand and T_xy, and this batch's Q (complex128) and R (compute precision);
+  // digit planes [7][QB * 4 * TX][N + 8] (bf16) for the FP64 tensor-core path
+  return pencil_stage_offset<T, N, TX, QB>() +
+         (sizeof(T) == 8 ? QB * 2 * N * TX * (16 + (int)sizeof(T) + 16 + (int)sizeof(T))
+                         : (N % 16 == 0 ? oz::S * QB * 4 * TX * (N + 8) * 2 : 0));
 }
 
 template <typename R, int N, int TX, int QB, int MODE>
@@ -165,7 +374,10 @@ __global__ void __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N
   double2* xstage = reinterpret_cast<double2*>(smem_raw + pencil_stage_offset<T, N, TX, QB>());
   T* tstage = reinterpret_cast<T*>(xstage + QB * 2 * NT);
   double2* qstage = reinterpret_cast<double2*>(tstage + QB * 2 * NT);  // Q then R of this batch
-  double2* rstage = qstage + QB * 2 * NT;
+  T* rstage = reinterpret_cast<T*>(qstage + QB * 2 * NT);
+  constexpr bool kOz = pencil_oz<R, N>();
+  unsigned short* dig = reinterpret_cast<unsigned short*>(smem_raw + pencil_stage_offset<T, N, TX, QB>());
+  __shared__ unsigned oz_e[(N * TX / 32 + 1) * QB * 4];
   const T* twg = reinterpret_cast<const T*>(a.tw);
   const R* hg = reinterpret_cast<const R*>(a.hz);
   for (int i = threadIdx.x; i < N; i += NT) {
@@ -255,7 +467,7 @@ __global__ void __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N
               const long gi = (long)(2 * q + c) * nxyz + site;
               const int si_ = (2 * j + c) * NT + threadIdx.x;
               cp_async(qstage + si_, a.q + gi, 16);
-              cp_async(rstage + si_, a.r + gi, 16);
+              cp_async(rstage + si_, reinterpret_cast<const T*>(a.r) + gi, (int)sizeof(T));
             }
           }
         }
@@ -272,16 +484,20 @@ __global__ void __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N
           const long gi = (long)(2 * q + c) * nxyz + site;
           const T v = q < q_end ? (a.xr ? reinterpret_cast<const T*>(a.xr)[gi] : to_r<R>(a.x[gi])) : T{R(0), R(0)};
           xr[j][c] = v;
-          buf[(2 * j + c) * CS + z * TX + xl] = v;
+          if (!kOz) buf[(2 * j + c) * CS + z * TX + xl] = v;
         }
       }
-      __syncthreads();
+      if (!kOz) __syncthreads();
     }
-    fft_lines<N, -1, R, LINES, NT>(buf, base, TX, tw, [&](int, int k, T v) {
-      R f = hz[k];
-      return T{v.x * f, v.y * f};
-    });
-    fft_lines<N, +1, R, LINES, NT>(buf, base, TX, tw, Identity());
+    if constexpr (kOz) {
+      oz_pencils_tz<N, TX, QB, CS>(xr, buf, dig, oz_e, oz_e + (NT / 32) * QB * 4, a.ozb, a.oz_sD, z, xl);
+    } else {
+      fft_lines<N, -1, R, LINES, NT>(buf, base, TX, tw, [&](int, int k, T v) {
+        R f = hz[k];
+        return T{v.x * f, v.y * f};
+      });
+      fft_lines<N, +1, R, LINES, NT>(buf, base, TX, tw, Identity());
+    }
     if constexpr (kPrefetch && MODE == M_CORRECT) {
       // Q, R of this batch (own elements); the next batch's copies may still be in flight
       if (qb0 + QB < q_end)
@@ -320,13 +536,20 @@ __global__ void __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N
       const double2 Hu = to_d(hu), Hv = to_d(hv);
       const double2 fu = make_double2(Hu.y, -Hu.x), fv = make_double2(Hv.y, -Hv.x);  // -i H x
 
+      T* dslot = reinterpret_cast<T*>(a.dslot);
       if (MODE == M_RHS) {
-        a.out[iu] = fu;
-        a.out[iv] = fv;
+        if (a.out) {
+          a.out[iu] = fu;
+          a.out[iv] = fv;
+        }
+        if (dslot) {
+          dslot[iu] = fur;
+          dslot[iv] = fvr;
+        }
       } else if (MODE == M_TAYLOR_FIRST) {
-        if (a.dslot) {
-          a.dslot[iu] = fu;
-          a.dslot[iv] = fv;
+        if (dslot) {
+          dslot[iu] = fur;
+          dslot[iv] = fvr;
         }
         const double2 tu = dmul(a.coef, Hu), tv = dmul(a.coef, Hv);
         a.out[iu] = tu;
@@ -345,17 +568,17 @@ __global__ void __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N
         // Eq. c and Eq. y through Q, R:  y_{n+1} = Q + k1 m',  p - c = R - k2 m'
         const R k2 = (R)(17.0 / 48.0 * a.h);
         const R k1 = (R)(161.0 / 170.0 * 17.0 / 48.0 * a.h);
-        double2 yo[2];
+        T yo[2];  // y_{n+1} in the compute precision, for its densities
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
           const long i = c ? iv : iu;
           const T f = c ? fvr : fur;
           const int si_ = (2 * j + c) * NT + threadIdx.x;
-          const T rr = to_r<R>(kPrefetch ? rstage[si_] : a.r[i]);
+          const T rr = kPrefetch ? rstage[si_] : reinterpret_cast<const T*>(a.r)[i];
           const double2 yn = dadd(kPrefetch ? qstage[si_] : a.q[i], to_d(T{k1 * f.x, k1 * f.y}));
           a.ynew[i] = yn;
-          a.pc[i] = to_d(T{rr.x - k2 * f.x, rr.y - k2 * f.y});
-          yo[c] = yn;
+          reinterpret_cast<T*>(a.pc)[i] = T{rr.x - k2 * f.x, rr.y - k2 * f.y};
+          yo[c] = to_r<R>(yn);
         }
         dens_acc(yo[0], yo[1], sn, sr, si);
       } else if (MODE == M_DERIV_PREDICT) {
@@ -372,9 +595,10 @@ __global__ void __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N
         for (int c = 0; c < 2; ++c) {
           const long i = c ? iv : iu;
           const T f = c ? fvr : fur;
-          a.dslot[i] = c ? fv : fu;
-          const T e0 = to_r<R>(a.d0[i]), e1 = to_r<R>(a.d1[i]), e2 = to_r<R>(a.d2[i]);
-          const T pcv = to_r<R>(a.pc[i]);
+          dslot[i] = f;
+          const T e0 = reinterpret_cast<const T*>(a.d0)[i], e1 = reinterpret_cast<const T*>(a.d1)[i],
+                  e2 = reinterpret_cast<const T*>(a.d2)[i];
+          const T pcv = reinterpret_cast<const T*>(a.pc)[i];
           const T pt = T{h48 * (R(119) * f.x - R(99) * e0.x + R(69) * e1.x - R(17) * e2.x),
                          h48 * (R(119) * f.y - R(99) * e0.y + R(69) * e1.y - R(17) * e2.y)};
           const T ct = T{h48 * (R(51) * f.x + R(3) * e0.x + e1.x), h48 * (R(51) * f.y + R(3) * e0.y + e1.y)};
@@ -385,7 +609,7 @@ __global__ void __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N
           const double2 mv = dadd(hf, to_d(X));
           reinterpret_cast<T*>(a.m)[i] = to_r<R>(mv);
           a.q[i] = dadd(hf, to_d(Y));
-          a.r[i] = to_d(Rv);
+          reinterpret_cast<T*>(a.r)[i] = Rv;
           mo[c] = mv;
         }
         dens_acc(mo[0], mo[1], sn, sr, si);
@@ -478,23 +702,37 @@ __global__ void k_predict(PointwiseArgs a) {
   const R c161 = (R)(161.0 / 170.0), c9 = (R)(9.0 / 170.0);
   double sn = 0, sr = 0, si = 0;
   for (int q = q_begin; q < q_end; ++q) {
-    double2 mo[2];
+    T mo[2];  // m in the compute precision, for its densities
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
       const long i = (long)(2 * q + c) * a.nxyz + s;
-      const T e0 = to_r<R>(a.d0[i]), e1 = to_r<R>(a.d1[i]), e2 = to_r<R>(a.d2[i]), e3 = to_r<R>(a.d3[i]);
-      const T pcv = to_r<R>(a.pc[i]);
+      const T e0 = reinterpret_cast<const T*>(a.d0)[i], e1 = reinterpret_cast<const T*>(a.d1)[i],
+              e2 = reinterpret_cast<const T*>(a.d2)[i], e3 = reinterpret_cast<const T*>(a.d3)[i];
+      const T pcv = reinterpret_cast<const T*>(a.pc)[i];
       const T pt = T{h48 * (R(119) * e0.x - R(99) * e1.x + R(69) * e2.x - R(17) * e3.x),
                      h48 * (R(119) * e0.y - R(99) * e1.y + R(69) * e2.y - R(17) * e3.y)};
       const T ct = T{h48 * (R(51) * e0.x + R(3) * e1.x + e2.x), h48 * (R(51) * e0.y + R(3) * e1.y + e2.y)};
       const T X = T{pt.x - c161 * pcv.x, pt.y - c161 * pcv.y};
       const T Y = T{c161 * ct.x + c9 * pt.x, c161 * ct.y + c9 * pt.y};
-      const double2 hf = dscale(dadd(a.y0[i], a.y1[i]), 0.5);
-      const double2 mv = dadd(hf, to_d(X));
-      reinterpret_cast<T*>(a.m)[i] = to_r<R>(mv);
-      a.q[i] = dadd(hf, to_d(Y));
-      a.r[i] = to_d(T{pt.x - ct.x, pt.y - ct.y});
-      mo[c] = mv;
+      const double2 y0 = a.y0[i], y1 = a.y1[i];
+      if constexpr (sizeof(R) == 4) {
+        // Q = (y0 + y1)/2 + Y in FP64 (two FMAs); m = Q + (X - Y) only needs FP32,
+        // the precision it is stored and used in
+        const double2 Yd = to_d(Y);
+        const double2 qv = make_double2(fma(0.5, y0.x, fma(0.5, y1.x, Yd.x)), fma(0.5, y0.y, fma(0.5, y1.y, Yd.y)));
+        a.q[i] = qv;
+        const T qr = to_r<R>(qv);
+        const T mr = T{qr.x + (X.x - Y.x), qr.y + (X.y - Y.y)};
+        reinterpret_cast<T*>(a.m)[i] = mr;
+        mo[c] = mr;
+      } else {
+        const double2 hf = dscale(dadd(y0, y1), 0.5);
+        const double2 mv = dadd(hf, to_d(X));
+        reinterpret_cast<T*>(a.m)[i] = to_r<R>(mv);
+        a.q[i] = dadd(hf, to_d(Y));
+        mo[c] = to_r<R>(mv);
+      }
+      reinterpret_cast<T*>(a.r)[i] = T{pt.x - ct.x, pt.y - ct.y};
     }
     dens_acc(mo[0], mo[1], sn, sr, si);
   }
@@ -574,9 +812,26 @@ bool supported_n(int N) {
 int pencil_tx(int N) { return N % 8 == 0 ? 8 : 4; }
 int pencil_qb(int N, int mixed) { return (N >= 40 || (mixed && N >= 32)) ? 2 : 4; }
 
+template <int N>
+static int planes_oz_n(const PlanesArgs& a, cudaStream_t s) {
+  using P = OzPlanes<N>;
+  auto kern = k_planes_oz<N>;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P::smem) != cudaSuccess) return 3;
+    attr = true;
+  }
+  const long blocks = (a.n_planes + P::PB - 1) / P::PB;
+  if (blocks <= 0) return 0;
+  if (!a.ozb) return 1;
+  kern<<<(unsigned)blocks, 256, P::smem, s>>>(a);
+  return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}
+
 template <typename R, int N>
 static int planes_n(const PlanesArgs& a, cudaStream_t s) {
   using T = typename Cx<R>::T;
+  if constexpr (pencil_oz<R, N>()) return planes_oz_n<N>(a, s);
   constexpr int PB = PlanesPB<N>::v;
   constexpr int NT = 256;
   const size_t smem = (size_t)PB * N * (N + 1) * sizeof(T) + N * sizeof(T) + N * sizeof(R);
@@ -600,6 +855,7 @@ static int pencils_nm(const PencilArgs& a, cudaStream_t s) {
   constexpr int QB = (N >= 40 || (sizeof(R) == 4 && N >= 32)) ? 2 : 4;
   const size_t smem = (size_t)pencil_smem_bytes<T, N, TX, QB>();
   auto kern = k_pencils<R, N, TX, QB, MODE>;
+  if (pencil_oz<R, N>() && !a.ozb) return 1;
   static bool attr = false;
   if (!attr) {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 3;
@@ -669,6 +925,64 @@ int launch_density(const PointwiseArgs& a, cudaStream_t s) {
   dim3 grid((unsigned)((a.nxyz + nt - 1) / nt), (a.n_qp + a.qg - 1) / a.qg);
   k_density<<<grid, nt, 0, s>>>(a);
   return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}
+
+bool ozaki_path(int N, int mixed) { return !mixed && N % 16 == 0 && supported_n(N); }
+
+size_t ozaki_table_words(int N) { return (size_t)oz::S * (N / 8) * (N / 16) * 32 * 2; }
+
+// D2[n][k] = (1/N) sum_j (alpha/2) k_j^2 cos(k_j (n - k) a), k_j = 2 pi (j or j - N) / (N a),
+// as balanced base-256 digits of I_D = round(D2 2^-sD) (|I_D| <= 2^55), laid out as the
+// B fragments of mma.m16n8k16 (B[k][n] = D2[n][k]) for each digit, 8-wide output tile,
+// k-step and lane: {B[2t][g], B[2t+1][g]}, {B[2t+8][g], B[2t+9][g]}, g = lane / 4, t = lane % 4.
+int ozaki_table(int N, double a, double alpha, uint32_t* out) {
+  const long double PI = 3.141592653589793238462643383279502884L;
+  if (N > 64) return 0;
+  long double d[64];  // fixed storage: no heap use (the no-allocation path calls this)
+  long double dmax = 0;
+  for (int m = 0; m < N; ++m) {
+    long double acc = 0;
+    for (int j = 0; j < N; ++j) {
+      const long double kj = 2.0L * PI * (long double)(j < N / 2 ? j : j - N) / ((long double)N * a);
+      acc += 0.5L * alpha * kj * kj * cosl(kj * (long double)m * a);
+    }
+    d[m] = acc / N;
+    dmax = std::max(dmax, fabsl(d[m]));
+  }
+  int eD = 0;
+  while (ldexpl(1.0L, eD) < dmax) ++eD;
+  while (eD > -1000 && ldexpl(1.0L, eD - 1) >= dmax) --eD;
+  const int sD = eD - 55;
+  // digits of every circulant entry
+  int dig[oz::S * 64];
+  for (int m = 0; m < N; ++m) {
+    long long I = llroundl(ldexpl(d[m], -sD));
+    int carry = 0;
+    for (int k = oz::S - 1; k >= 1; --k) {
+      const int byte = (int)((unsigned long long)I >> (8 * (oz::S - 1 - k)) & 0xFFu) + carry;
+      carry = (byte + 128) >> 8;
+      dig[(size_t)k * N + m] = byte - (carry << 8);
+    }
+    dig[m] = (int)(I >> 48) + carry;
+  }
+  auto bf16 = [](int v) -> uint32_t {  // small integer -> bf16 bits (exact)
+    const float f = (float)v;
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    return u >> 16;
+  };
+  auto D = [&](int l, int n, int k) { return dig[(size_t)l * N + ((n - k) % N + N) % N]; };
+  const int KS = N / 16, NTL = N / 8;
+  for (int l = 0; l < oz::S; ++l)
+    for (int nt = 0; nt < NTL; ++nt)
+      for (int ks = 0; ks < KS; ++ks)
+        for (int lane = 0; lane < 32; ++lane) {
+          const int g = lane / 4, t = lane % 4, n = nt * 8 + g, k0 = ks * 16 + 2 * t;
+          uint32_t* o = out + ((((size_t)l * NTL + nt) * KS + ks) * 32 + lane) * 2;
+          o[0] = bf16(D(l, n, k0)) | (bf16(D(l, n, k0 + 1)) << 16);
+          o[1] = bf16(D(l, n, k0 + 8)) | (bf16(D(l, n, k0 + 9)) << 16);
+        }
+  return sD;
 }
 
 double pairing_lattice_c(double a, double alpha) {

@@ -40,21 +40,23 @@ struct PencilArgs {
   const double2* D;       // Delta [site]
   const void* tw;         // forward twiddles of the compute precision, N entries
   const void* hz;         // (alpha/2) kz^2 / N, N entries, compute precision
+  const uint32_t* ozb;    // FP64 tensor-core path: digit fragments of D2 (lise_ozaki.cuh)
+  int oz_sD;              //   and their scale exponent
   int n_qp;
   int qg;                 // states per density group (one grid row per group)
-  double2* out;
+  double2* out;           // complex128 output (M_RHS, Taylor terms); may be null in M_RHS
   double2* acc;
-  double2* dslot;
+  void* dslot;            // y' ring slot, compute precision (M_RHS, M_TAYLOR_FIRST, M_DERIV_PREDICT)
   double2 coef;
   double h;               // time step
   const double2* y0;      // y_n
   const double2* y1;      // y_{n-1} (M_CORRECT)
-  const double2* d0;      // y'_n
-  const double2* d1;      // y'_{n-1}
-  const double2* d2;      // y'_{n-2}
-  double2* q;             // Q (read in M_CORRECT, written in M_DERIV_PREDICT), see below
-  double2* r;             // R (likewise)
-  double2* pc;            // p - c (written in M_CORRECT, read in M_DERIV_PREDICT)
+  const void* d0;         // y'_n      (compute precision, like every y' slot)
+  const void* d1;         // y'_{n-1}
+  const void* d2;         // y'_{n-2}
+  double2* q;             // Q, complex128 (read in M_CORRECT, written in M_DERIV_PREDICT), see below
+  void* r;                // R, compute precision (likewise)
+  void* pc;               // p - c, compute precision (written in M_CORRECT, read in M_DERIV_PREDICT)
   void* m;                // m in the compute precision (written in M_DERIV_PREDICT)
   double2* ynew;          // y_{n+1} (written in M_CORRECT; may alias y1)
   double* part_n;         // [group][site] partial sums
@@ -71,6 +73,8 @@ struct PlanesArgs {
   void* txy;              // output T_xy x
   const void* tw;         // forward twiddles, N entries
   const void* hxy;        // (alpha/2) k^2 / N^2, N entries
+  const uint32_t* ozb;    // FP64 tensor-core path: digit fragments of D2 (lise_ozaki.cuh)
+  int oz_sD;
   long n_planes;
 };
 
@@ -107,10 +111,12 @@ __host__ __device__ inline void pairing_geff(double g, double alpha_n0, double c
 }
 
 struct PointwiseArgs {
-  // predictor + modifier for the first ABM step: p = Eq. p, m = Eq. m
-  const double2 *y0, *y1, *d0, *d1, *d2, *d3, *pc;
-  double2 *q, *r;
-  void* m;                // m in the compute precision of the path
+  // predictor + modifier: p = Eq. p, m = Eq. m, and the corrector's Q, R
+  const double2 *y0, *y1;  // complex128 states
+  const void *d0, *d1, *d2, *d3, *pc;  // compute precision
+  double2* q;              // complex128
+  void* r;                 // compute precision
+  void* m;                 // m in the compute precision of the path
   int mixed;
   double h;
   // density partials of `src` (for the plain density pass) or of m
@@ -129,6 +135,12 @@ struct PointwiseArgs {
 // Eq. y becomes y_{n+1} = Q + (161/170)(17 h/48) m'_{n+1} and
 // p_{n+1} - c_{n+1} = R - (17 h/48) m'_{n+1} (algebraically identical to Eqs. c, y).
 // Q and R are formed with the predictor, so the corrector reads 2 arrays, not 6.
+//
+// Storage precision of the history.  y_n, y_{n-1} and Q are states (complex128).
+// The derivatives y', R = pt - ct and p - c are formed in the compute precision
+// (FP32 in the mixed path: the FFT/BdG apply and the derivative combinations run
+// there), so they are stored in it: exactly, without rounding.  Every sum with a
+// state value runs in FP64.
 
 // Host-side launchers (defined in lise_kernels.cu).
 int launch_planes(int N, int mixed, const PlanesArgs& a, cudaStream_t s);
@@ -145,6 +157,13 @@ int launch_finite_check(const double2* x, long count, int* err, cudaStream_t s);
 // eta[q] = a^3 * sum over the pencil blocks of eta_part[q][block] (compensated).
 int launch_eta_reduce(const double* eta_part, int n_qp, int n_blocks, double a3, double* eta, cudaStream_t s);
 int pencil_blocks_x(int N);
+// FP64 kinetic operator on the tensor cores (lise_ozaki.cuh): used for the FP64
+// path on lattices with N a multiple of 16.  The table holds the D2 digit
+// fragments (ozaki_table_words(N) uint32 words); ozaki_table returns its scale
+// exponent sD (D2 ~ I_D 2^sD).
+bool ozaki_path(int N, int mixed);
+size_t ozaki_table_words(int N);
+int ozaki_table(int N, double a, double alpha, uint32_t* out);
 // Tile width (x values per pencil block) and group width for a lattice.
 int pencil_tx(int N);
 int pencil_qb(int N, int mixed);

@@ -36,6 +36,8 @@ constexpr long double kPi = 3.141592653589793238462643383279502884L;
 // heap allocation) and copied into the scratch array on every call.
 alignas(16) double g_tab_d[4 * 64];
 alignas(16) float g_tab_f[4 * 64];
+// D2 digit fragments of the FP64 tensor-core path (largest lattice: 64)
+alignas(16) uint32_t g_tab_oz[7 * 8 * 4 * 32 * 2];
 
 template <typename R>
 void tables(int N, double a, double alpha, R* tw, R* hxy, R* hz) {
@@ -94,6 +96,9 @@ extern "C" int lise_rhs_noalloc(const lise_params* p, const double* psi_dev, dou
   const size_t o_v = off;      off += up256(p->v_static ? (size_t)nxyz * sizeof(double) : 0);
   const size_t o_tab = off;    off += up256(4 * (size_t)N * rs);
   const size_t o_err = off;    off += up256(sizeof(int));
+  const bool use_oz = ozaki_path(N, mixed);
+  const size_t oz_words = use_oz ? ozaki_table_words(N) : 0;
+  const size_t o_oz = off;     off += up256(oz_words * sizeof(uint32_t));
   const int nbx = pencil_blocks_x(N);
   const size_t o_eta = off;    off += up256(p->remove_phase ? (size_t)p->n_qp * sizeof(double) : 0);
   const size_t o_etap = off;   off += up256(p->remove_phase ? (size_t)p->n_qp * nbx * sizeof(double) : 0);
@@ -124,6 +129,14 @@ extern "C" int lise_rhs_noalloc(const lise_params* p, const double* psi_dev, dou
       cudaMemcpyAsync(base + o_v, p->v_static, (size_t)nxyz * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess)
     return LISE_ECUDA;
   if (cudaMemsetAsync(base + o_err, 0, sizeof(int), s) != cudaSuccess) return LISE_ECUDA;
+  int oz_sD = 0;
+  if (use_oz) {
+    if (oz_words > sizeof(g_tab_oz) / sizeof(uint32_t)) return LISE_EINVAL;
+    oz_sD = ozaki_table(N, p->dx, p->alpha, g_tab_oz);
+    if (cudaMemcpyAsync(base + o_oz, g_tab_oz, oz_words * sizeof(uint32_t), cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return LISE_ECUDA;
+  }
+  const uint32_t* ozb = use_oz ? reinterpret_cast<const uint32_t*>(base + o_oz) : nullptr;
 
   const double2* x = reinterpret_cast<const double2*>(psi_dev);
   double* part_n = reinterpret_cast<double*>(base + o_pn);
@@ -175,6 +188,8 @@ extern "C" int lise_rhs_noalloc(const lise_params* p, const double* psi_dev, dou
   pa.txy = base + o_txy;
   pa.tw = tw;
   pa.hxy = hxy;
+  pa.ozb = ozb;
+  pa.oz_sD = oz_sD;
   pa.n_planes = (long)p->n_qp * 2 * N;
   if (launch_planes(N, mixed, pa, s)) return LISE_ECUDA;
   PencilArgs ka;
@@ -185,6 +200,8 @@ extern "C" int lise_rhs_noalloc(const lise_params* p, const double* psi_dev, dou
   ka.D = r.D;
   ka.tw = tw;
   ka.hz = hz;
+  ka.ozb = ozb;
+  ka.oz_sD = oz_sD;
   ka.n_qp = p->n_qp;
   ka.qg = qg;
   ka.out = reinterpret_cast<double2*>(dpsi_dev);

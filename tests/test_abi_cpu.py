@@ -46,8 +46,8 @@ def test_footprint_model():
     # state arrays dominate: 11 complex128 copies of 2048 x 2 x 32^3 (10 history + scratch)
     assert abs(f32 - 11 * 16 * 2048 * 2 * 32 ** 3) / f32 < 0.02
     fm = L.footprint_bytes(48, 4096, precision="mixed")
-    # mixed: 9 complex128 history arrays, m and T_xy in complex64
-    assert abs(fm - 10 * 16 * 4096 * 2 * 48 ** 3) / fm < 0.02
+    # mixed: y_n, y_{n-1}, Q in complex128; the y' ring, m, R, p - c and T_xy in complex64
+    assert abs(fm - (3 * 16 + 8 * 8) * 4096 * 2 * 48 ** 3) / fm < 0.02
     assert L.footprint_bytes(30, 8) == 0  # unsupported lattice
 
 

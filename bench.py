@@ -62,9 +62,21 @@ def algorithmic_per_qp_site(N, mixed):
     complex128 = 16 B per component.  The states y and Q are complex128; T_xy,
     m, the y' ring, R and p - c are kept in the compute precision (complex64
     in the mixed path).
-    FFT convention: 5 n log2 n real flops per complex length-n transform."""
+    FFT convention: 5 n log2 n real flops per complex length-n transform.
+
+    FP64 path on lattices with N % 16 == 0: the kinetic operator runs on the
+    bf16 tensor cores (exact digit products, 28 digit pairs, K = N per axis),
+    so "flops" of planes are its bf16 tensor flops and "flops" of pencils its
+    FP64 flops (an FMA counts 2), as written in the kernels:
+      corrector  per real: T_z + T_xy 1, BdG 3 FMA, y_{n+1} 1 FMA, p - c 1 FMA  -> 11
+                 densities 3 x 2 FMA per (state, site)                          -> 12
+      deriv/pred per real: T_z + T_xy 1, BdG 3 FMA, Y 1 + 3 FMA, R 1 + 3 FMA,
+                 Q 2 FMA, m 1 + 1 FMA                                           -> 28
+                 densities                                                      -> 12
+    per (state, site): 2 components x 2 reals."""
     L = log2(N)
     c16, cr = 16, (8 if mixed else 16)   # complex128 / compute-precision component
+    tensor = (not mixed) and N % 16 == 0
     planes_bytes = 2 * (cr + cr) + 2 * (c16 + cr)          # operand m, then operand y_{n+1}
     correct_bytes = 2 * (cr + cr + c16 + cr) + 2 * (c16 + cr)
     fft_bdg = 2 * (2 * 5 * L + 4) + 24                     # z fwd+inv + multiply/add, BdG apply
@@ -79,11 +91,24 @@ def algorithmic_per_qp_site(N, mixed):
         deriv_bytes = 2 * (2 * c16 + 5 * cr) + 2 * (c16 + 3 * cr)
         pencils_flops = 2 * fft_bdg + (16 + 13) + predict_flops
         pointwise = {"flops": 0.0, "bytes": 0, "launches_per_step": 0}
-    return {
+    out = {
         "planes": {"flops": planes_flops, "bytes": planes_bytes, "launches_per_step": 2},
         "pencils": {"flops": pencils_flops, "bytes": correct_bytes + deriv_bytes, "launches_per_step": 2},
         "pointwise": pointwise,
     }
+    if tensor:
+        mma = 2 * 2 * N * 28 * 2          # bf16 flops per (state, site) and axis: 2 comps x re/im x K x pairs
+        out["planes"].update({"flops": 2 * 2 * mma, "kind": "bf16 tensor"})
+        out["pencils"].update({"flops": 4 * 11 + 12 + 4 * 28 + 12, "kind": "fp64", "tensor_flops": 2 * mma})
+    return out
+
+
+def read_tensor_peak():
+    try:
+        with open(PEAKS_FILE) as f:
+            return float(json.load(f)["bf16_tflops_sustained"])
+    except Exception:
+        return 1400.0
 
 
 def read_peaks():
@@ -526,12 +551,19 @@ def main():
     gbs = bytes_per_launch / (per_launch_ms / 1e3) / 1e9
     tflops = flops_per_launch / (per_launch_ms / 1e3) / 1e12
     alu_peak = FP32_PEAK_TFLOPS if mixed else FP64_PEAK_TFLOPS
+    if a.get("kind") == "bf16 tensor":
+        alu_peak = read_tensor_peak()
     hbm_frac, alu_frac = gbs / hbm_peak, tflops / alu_peak
     traffic = recorded_traffic(w.name, dom)
     if alu_frac >= hbm_frac:
-        roof = {"bound": "alu", "achieved": tflops, "peak": alu_peak, "unit": "TFLOP/s", "frac": alu_frac,
-                "peak_source": ("FP32" if mixed else "FP64") + " unit counts x 2.032 GHz (derived)",
+        tensor_kind = a.get("kind") == "bf16 tensor"
+        roof = {"bound": "tensor" if tensor_kind else "alu", "achieved": tflops, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": alu_frac,
+                "peak_source": "measured bf16 (sustained)" if tensor_kind else
+                ("FP32" if mixed else "FP64") + " unit counts x 2.032 GHz (derived)",
                 "hbm_frac_of_measured": hbm_frac}
+        if "tensor_flops" in a:
+            roof["tensor_tflops_bf16"] = a["tensor_flops"] * qp_sites / a["launches_per_step"] / (per_launch_ms / 1e3) / 1e12
     else:
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_frac,
                 "peak_source": hbm_src, "alu_frac": alu_frac}

@@ -64,6 +64,10 @@ template <> __device__ __forceinline__ float2 to_r_hw<float>(double2 v) {
 __device__ __forceinline__ double2 to_d(double2 v) { return v; }
 __device__ __forceinline__ double2 to_d(float2 v) { return make_double2(f2d_bits(v.x), f2d_bits(v.y)); }
 
+// fused multiply-add in the operands' own precision
+__device__ __forceinline__ float fmx(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmx(double a, double b, double c) { return fma(a, b, c); }
+
 __device__ __forceinline__ double2 dadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double2 dsub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ double2 dscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
@@ -71,17 +75,18 @@ __device__ __forceinline__ double2 dmul(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-// n += 2 |v|^2 ; nu += u conj(v)
+// sn += |v|^2 ; nu += u conj(v)  (the factor 2 of n = 2 sum |v|^2 is applied where the
+// partial sums are stored; scaling by 2 is exact, so the order does not matter)
 __device__ __forceinline__ void dens_acc(double2 u, double2 v, double& sn, double& sr, double& si) {
-  sn += 2.0 * (v.x * v.x + v.y * v.y);
-  sr += u.x * v.x + u.y * v.y;
-  si += u.y * v.x - u.x * v.y;
+  sn = fma(v.x, v.x, fma(v.y, v.y, sn));
+  sr = fma(u.x, v.x, fma(u.y, v.y, sr));
+  si = fma(u.y, v.x, fma(-u.x, v.y, si));
 }
 // The same from FP32 operands (the mixed path, whose densities only set the potentials
 // of its FP32 H psi): products in FP32 (relative rounding 2^-24, the level of the FP32
 // potentials themselves), sums in FP64.
 __device__ __forceinline__ void dens_acc(float2 u, float2 v, double& sn, double& sr, double& si) {
-  sn += f2d_bits(2.0f * fmaf(v.x, v.x, v.y * v.y));
+  sn += f2d_bits(fmaf(v.x, v.x, v.y * v.y));
   sr += f2d_bits(fmaf(u.x, v.x, u.y * v.y));
   si += f2d_bits(fmaf(u.y, v.x, -(u.x * v.y)));
 }
@@ -155,7 +160,7 @@ __global__ void __launch_bounds__(NT) k_planes(PlanesArgs a) {
 // Both are exact 64-bit integer sums of one scale, added in shared memory, then
 // converted to FP64 once.
 template <int N> struct OzPlanes {
-  static constexpr int PB = N <= 16 ? 4 : (N <= 32 ? 2 : 1);
+  static constexpr int PB = N <= 16 ? 4 : 1;
   static constexpr int RS = N + 8;  // padded digit row (bf16): conflict-free ldmatrix rows
   static constexpr int G = PB * 2;  // exponent groups
   static constexpr size_t dig_bytes = (size_t)oz::S * G * N * RS * 2;
@@ -516,7 +521,7 @@ __global__ void __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N
       if (MODE == M_ENERGY) {
         const double2 v = a.x[iv];
         const double2 tv = to_d(Tv);
-        sn += 2.0 * (v.x * tv.x + v.y * tv.y);
+        sn = fma(v.x, tv.x, fma(v.y, tv.y, sn));
         continue;
       }
       // H x = [[h, Delta], [Delta*, -h*]] x with h = T + W (W real, T real-symmetric);
@@ -525,8 +530,9 @@ __global__ void __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N
       const R w = a.eta ? Wr - (R)a.eta[q] : Wr;
       const R w2 = a.eta ? Wr + (R)a.eta[q] : Wr;  // -(h + eta) on the v component
       const T d = Dr;
-      const T hu = T{Tu.x + w * u.x + (d.x * v.x - d.y * v.y), Tu.y + w * u.y + (d.x * v.y + d.y * v.x)};
-      const T hv = T{(d.x * u.x + d.y * u.y) - Tv.x - w2 * v.x, (d.x * u.y - d.y * u.x) - Tv.y - w2 * v.y};
+      // one FMA chain per real part (3 FMA after the kinetic sum)
+      const T hu = T{fmx(w, u.x, fmx(d.x, v.x, fmx(-d.y, v.y, Tu.x))), fmx(w, u.y, fmx(d.x, v.y, fmx(d.y, v.x, Tu.y)))};
+      const T hv = T{fmx(-w2, v.x, fmx(d.x, u.x, fmx(d.y, u.y, -Tv.x))), fmx(-w2, v.y, fmx(d.x, u.y, fmx(-d.y, u.x, -Tv.y)))};
       if (MODE == M_ETA) {
         const double2 du = to_d(u), dv = to_d(v), Hu_ = to_d(hu), Hv_ = to_d(hv);
         eta_acc[j] += (du.x * Hu_.x + du.y * Hu_.y) + (dv.x * Hv_.x + dv.y * Hv_.y);
@@ -575,7 +581,13 @@ __global__ void __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N
           const T f = c ? fvr : fur;
           const int si_ = (2 * j + c) * NT + threadIdx.x;
           const T rr = kPrefetch ? rstage[si_] : reinterpret_cast<const T*>(a.r)[i];
-          const double2 yn = dadd(kPrefetch ? qstage[si_] : a.q[i], to_d(T{k1 * f.x, k1 * f.y}));
+          double2 yn;
+          if constexpr (sizeof(R) == 8) {
+            const double2 qv = a.q[i];
+            yn = make_double2(fma((double)k1, (double)f.x, qv.x), fma((double)k1, (double)f.y, qv.y));
+          } else {
+            yn = dadd(kPrefetch ? qstage[si_] : a.q[i], to_d(T{k1 * f.x, k1 * f.y}));
+          }
           a.ynew[i] = yn;
           reinterpret_cast<T*>(a.pc)[i] = T{rr.x - k2 * f.x, rr.y - k2 * f.y};
           yo[c] = to_r<R>(yn);
@@ -586,11 +598,14 @@ __global__ void __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N
         //   pt = h/48 (119 y'_{n+1} - 99 y'_n + 69 y'_{n-1} - 17 y'_{n-2})
         //   ct = h/48 (51 y'_{n+1} + 3 y'_n + y'_{n-1}),  hf = (y_{n+1} + y_n)/2
         //   m = hf + pt - (161/170) pc,  Q = hf + (161/170) ct + (9/170) pt,  R = pt - ct.
-        // The derivative combinations run in the compute precision (FP32 in the
-        // mixed path, whose y' are FP32-accurate); every sum with a state value is FP64.
+        // Formed as Y = (161/170) ct + (9/170) pt and R directly from the derivatives,
+        // Q = hf + Y and m = Q + (161/170)(R - pc) (as 1 - 9/170 = 161/170, m - Q = (161/170)(pt - ct - pc)).
         const R h48 = (R)(a.h / 48.0);
         const R c161 = (R)(161.0 / 170.0), c9 = (R)(9.0 / 170.0);
-        double2 mo[2];
+        const R y0c = h48 * (c161 * R(51) + c9 * R(119)), y1c = h48 * (c161 * R(3) - c9 * R(99)),
+                y2c = h48 * (c161 + c9 * R(69)), y3c = h48 * (-c9 * R(17));
+        const R r0c = h48 * R(68), r1c = h48 * R(-102), r2c = h48 * R(68), r3c = h48 * R(-17);
+        T mo[2];
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
           const long i = c ? iv : iu;
@@ -599,16 +614,14 @@ __global__ void __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N
           const T e0 = reinterpret_cast<const T*>(a.d0)[i], e1 = reinterpret_cast<const T*>(a.d1)[i],
                   e2 = reinterpret_cast<const T*>(a.d2)[i];
           const T pcv = reinterpret_cast<const T*>(a.pc)[i];
-          const T pt = T{h48 * (R(119) * f.x - R(99) * e0.x + R(69) * e1.x - R(17) * e2.x),
-                         h48 * (R(119) * f.y - R(99) * e0.y + R(69) * e1.y - R(17) * e2.y)};
-          const T ct = T{h48 * (R(51) * f.x + R(3) * e0.x + e1.x), h48 * (R(51) * f.y + R(3) * e0.y + e1.y)};
-          const T X = T{pt.x - c161 * pcv.x, pt.y - c161 * pcv.y};
-          const T Y = T{c161 * ct.x + c9 * pt.x, c161 * ct.y + c9 * pt.y};
-          const T Rv = T{pt.x - ct.x, pt.y - ct.y};
-          const double2 hf = dscale(dadd(a.x[i], a.y0[i]), 0.5);
-          const double2 mv = dadd(hf, to_d(X));
-          reinterpret_cast<T*>(a.m)[i] = to_r<R>(mv);
-          a.q[i] = dadd(hf, to_d(Y));
+          const T Y = T{y0c * f.x + y1c * e0.x + y2c * e1.x + y3c * e2.x, y0c * f.y + y1c * e0.y + y2c * e1.y + y3c * e2.y};
+          const T Rv = T{r0c * f.x + r1c * e0.x + r2c * e1.x + r3c * e2.x, r0c * f.y + r1c * e0.y + r2c * e1.y + r3c * e2.y};
+          const double2 xv = a.x[i], y0v = a.y0[i], Yd = to_d(Y);
+          const double2 qv = make_double2(fma(0.5, xv.x, fma(0.5, y0v.x, Yd.x)), fma(0.5, xv.y, fma(0.5, y0v.y, Yd.y)));
+          const T mv = to_r<R>(make_double2(fma((double)c161, (double)(Rv.x - pcv.x), qv.x),
+                                            fma((double)c161, (double)(Rv.y - pcv.y), qv.y)));
+          reinterpret_cast<T*>(a.m)[i] = mv;
+          a.q[i] = qv;
           reinterpret_cast<T*>(a.r)[i] = Rv;
           mo[c] = mv;
         }
@@ -632,7 +645,7 @@ __global__ void __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N
   }
   if (a.dens) {
     const long o = (long)g * nxyz + site;
-    a.part_n[o] = sn;
+    a.part_n[o] = 2.0 * sn;
     if (MODE != M_ENERGY) {
       a.part_nr[o] = sr;
       a.part_ni[o] = si;
@@ -737,7 +750,7 @@ __global__ void k_predict(PointwiseArgs a) {
     dens_acc(mo[0], mo[1], sn, sr, si);
   }
   const long o = (long)g * a.nxyz + s;
-  a.part_n[o] = sn;
+  a.part_n[o] = 2.0 * sn;
   a.part_nr[o] = sr;
   a.part_ni[o] = si;
 }
@@ -753,7 +766,7 @@ __global__ void k_density(PointwiseArgs a) {
     dens_acc(a.src[i], a.src[i + a.nxyz], sn, sr, si);
   }
   const long o = (long)g * a.nxyz + s;
-  a.part_n[o] = sn;
+  a.part_n[o] = 2.0 * sn;
   a.part_nr[o] = sr;
   a.part_ni[o] = si;
 }

@@ -43,6 +43,30 @@ def test_rhs_all_lattices(N, n_qp):
     assert rel(got, ref) < TOL_FP64_RHS
 
 
+@pytest.mark.parametrize("N", [16, 32])
+def test_rhs_wide_dynamic_range(N):
+    # The FP64 kinetic operator on the tensor cores scales each (state, component,
+    # re/im) group of a tile by its own binary exponent: every state and component
+    # keeps FP64 accuracy relative to its own size, here across 12 decades and with
+    # an identically zero component (its group has exponent field 0).
+    n_qp = 6
+    psi = random_state(N, n_qp, seed=11)
+    scale = np.array([1.0, 1e-3, 1e-6, 1e-9, 1e-12, 1.0])
+    psi *= scale[:, None, None, None, None]
+    psi[1, 1] *= 1e-4          # v much smaller than u
+    psi[5, 1] = 0.0            # v identically zero
+    kw = dict(alpha=1.0, beta=-0.5, mu=0.3, g=0.8)
+    with L.Context(N, n_qp, **kw) as ctx:
+        got = ctx.rhs(psi, 0.0)
+    ref = O.rhs(O.Params(N, N, N, n_qp=n_qp, **kw), psi, 0.0)
+    for q in range(n_qp):
+        for c in range(2):
+            if not np.any(ref[q, c]):
+                continue
+            assert rel(got[q, c], ref[q, c]) < 1e-12, (q, c, rel(got[q, c], ref[q, c]))
+    assert np.all(np.isfinite(got))
+
+
 def test_rhs_mixed_precision_bound():
     N, n_qp = 24, 6
     psi = random_state(N, n_qp, seed=3, kmax=6)

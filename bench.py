@@ -339,7 +339,7 @@ def run_serve(args):
             ts = time.perf_counter()
             lag.append(ts - (t0 + arrivals[i]))
             ids.append(srv.submit(w.nx, n_qp, psi[:n_qp], 0.0, w.dt, args.serve_steps, a=w.a, alpha=w.alpha,
-                                  beta=w.beta, mu=w.mu, g=w.g, precision="mixed"))
+                                  beta=w.beta, mu=w.mu, g=w.g, precision="mixed", copy=False))
         infos = [srv.wait(i, want_state=False)[1] for i in ids]
         st = srv.stats()
     lat = np.array([inf["done_s"] - inf["submit_s"] + lg for inf, lg in zip(infos, lag)])
@@ -367,10 +367,11 @@ def run_batch(args):
     state count uniform in [128, 4096], drive amplitude A uniform in [0, 0.05]
     (Omega 0.3), mixed precision, --batch-steps ABM steps each.  All are ready at
     t = 0; their summed device footprint is far above one GPU's memory, so the
-    server admits them in arrival order as budget frees up (waves).  The client
-    keeps at most --batch-host-gb of request states outstanding on the host
-    (queued or running), submitting the next evolution when one returns.
-    Reported: aggregate throughput, makespan and the admission schedule."""
+    server admits them as budget frees up (waves), first fit in arrival order
+    with at most --batch-max-skips passes over any one evolution.  All are
+    submitted at t = 0 without host copies (the server reads each initial state
+    from the caller's array at admission).  Reported: aggregate throughput,
+    makespan and the schedule."""
     import numpy as np
     from paper_2009_00745_b300 import lise as L
     from paper_2009_00745_b300 import workloads as Wl
@@ -385,27 +386,18 @@ def run_batch(args):
         w = Wl.ufg_plane_waves(n, q, noise_eps=1e-3, precision="mixed", steps=args.batch_steps)
         base[n] = (w, w.initial_state())
     budget = int(args.batch_budget_gb * 1e9)
-    host_cap = args.batch_host_gb * 1e9
     fps = [L.footprint_bytes(int(l), int(nq), precision="mixed") for l, nq in zip(lattices, nqps)]
-    host_bytes = [32.0 * int(nq) * int(l) ** 3 for l, nq in zip(lattices, nqps)]
-    infos = [None] * R
     with L.Server(budget, max_active=args.batch_max_active, steps_per_turn=args.serve_turn) as srv:
+        srv.set_admission("first_fit", max_skips=args.batch_max_skips)
         t0 = time.perf_counter()
-        pending = []  # (request index, server id)
-        nxt, held = 0, 0.0
-        while nxt < R or pending:
-            while nxt < R and (not pending or held + host_bytes[nxt] <= host_cap):
-                w, psi = base[int(lattices[nxt])]
-                nq = int(nqps[nxt])
-                rid = srv.submit(w.nx, nq, psi[:nq], 0.0, w.dt, args.batch_steps, a=w.a, alpha=w.alpha,
-                                 beta=w.beta, mu=w.mu, g=w.g, drive_A=float(amps[nxt]), drive_Omega=0.3,
-                                 precision="mixed")
-                pending.append((nxt, rid))
-                held += host_bytes[nxt]
-                nxt += 1
-            i, rid = pending.pop(0)  # arrival order: the oldest finishes no later than its successors start
-            infos[i] = srv.wait(rid, want_state=False)[1]
-            held -= host_bytes[i]
+        ids = []
+        for i in range(R):
+            w, psi = base[int(lattices[i])]
+            nq = int(nqps[i])
+            ids.append(srv.submit(w.nx, nq, psi[:nq], 0.0, w.dt, args.batch_steps, a=w.a, alpha=w.alpha,
+                                  beta=w.beta, mu=w.mu, g=w.g, drive_A=float(amps[i]), drive_Omega=0.3,
+                                  precision="mixed", copy=False))
+        infos = [srv.wait(rid, want_state=False)[1] for rid in ids]
         st = srv.stats()
         wall = time.perf_counter() - t0
     units = sum(float(nq) * int(l) ** 3 * args.batch_steps for nq, l in zip(nqps, lattices))
@@ -424,6 +416,7 @@ def run_batch(args):
                          "resident_gb": round(sum(fps[i] for i in live) / 1e9, 1)})
     line = {"mode": "batch", "evolutions": R, "steps_per_evolution": args.batch_steps, "precision": "mixed",
             "hbm_budget_gb": args.batch_budget_gb, "max_active": args.batch_max_active,
+            "admission": "first fit, max %d skips" % args.batch_max_skips,
             "steps_per_turn": args.serve_turn, "sum_footprint_gb": round(sum(fps) / 1e9, 1),
             "throughput": units / makespan, "unit": UNIT, "makespan_s": makespan, "wall_s": wall,
             "peak_used_gb": st["peak_used_bytes"] / 1e9, "peak_active": st["peak_active"],
@@ -467,8 +460,8 @@ def main():
     ap.add_argument("--batch-evolutions", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=500)
     ap.add_argument("--batch-budget-gb", type=float, default=200.0)
-    ap.add_argument("--batch-host-gb", type=float, default=80.0)
-    ap.add_argument("--batch-max-active", type=int, default=16)
+    ap.add_argument("--batch-max-active", type=int, default=8)
+    ap.add_argument("--batch-max-skips", type=int, default=8)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

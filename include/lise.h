@@ -170,10 +170,29 @@ int lise_server_create(int device, size_t hbm_budget_bytes, int max_active, int 
  * sets them).  LISE_ENOMEM if the request alone exceeds the budget. */
 int lise_server_submit(lise_server *s, const lise_params *p, const double *psi, double t0, double dt,
                        int n_steps, long *id);
+/* Same without copying: the server reads the initial state from psi_in when it
+ * admits the request and writes the final state to psi_out (may be NULL: no
+ * state is copied back) when it finishes.  The caller keeps both buffers
+ * (host, layout above) valid and unchanged until lise_server_wait returns for
+ * this id; lise_server_wait's psi_out is then not used.  Submitting many large
+ * requests this way costs no host copies and no extra host memory. */
+int lise_server_submit_borrowed(lise_server *s, const lise_params *p, const double *psi_in, double *psi_out,
+                                double t0, double dt, int n_steps, long *id);
 /* Blocks until request id is done; copies its final state to psi_out (host;
  * may be NULL) and its timings to info (may be NULL); forgets the request.
  * Returns the request's status. */
 int lise_server_wait(lise_server *s, long id, double *psi_out, lise_request_info *info);
+/* Non-blocking: *done = 1 if request id has finished (lise_server_wait then
+ * returns at once), else 0.  LISE_EINVAL for an unknown id. */
+int lise_server_poll(lise_server *s, long id, int *done);
+/* Admission order.  LISE_ADMIT_FIFO (the default): strictly in arrival order,
+ * a request that does not fit the free budget holds back all later ones.
+ * LISE_ADMIT_FIRST_FIT: the first queued request (in arrival order) that fits
+ * is admitted; a request passed over max_skips times holds back later ones
+ * until it is admitted (bounded waiting).  max_skips >= 0 (ignored for FIFO). */
+#define LISE_ADMIT_FIFO 0
+#define LISE_ADMIT_FIRST_FIT 1
+int lise_server_set_admission(lise_server *s, int policy, int max_skips);
 /* Largest sum of admitted footprints and largest number of active requests seen. */
 int lise_server_stats(lise_server *s, size_t *peak_used_bytes, int *peak_active);
 /* Finishes every submitted request, stops the worker and frees the server. */

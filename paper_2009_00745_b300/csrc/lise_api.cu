@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "../../include/lise.h"
+#include "lise_internal.h"
 #include "lise_kernels.cuh"
 
 using namespace lise;
@@ -506,8 +507,11 @@ void free_ctx(lise_ctx* c) {
   void* ptrs[] = {c->drive_dev, c->eta, c->eta_part, c->slot[0], c->slot[1], c->D[0], c->D[1], c->D[2], c->D[3], c->M, c->RPC, c->Q, c->TXY,
                   c->part_n, c->part_nr, c->part_ni, c->dn[0], c->dn[1], c->dnu[0], c->dnu[1], c->W,
                   c->Dl, c->v_static, c->tw, c->hxy, c->hz, c->ozb, c->e_site, c->err};
+  // stream-ordered frees: no device-wide synchronisation (work of other contexts,
+  // e.g. the other requests of a server, keeps running)
   for (void* q : ptrs)
-    if (q) cudaFree(q);
+    if (q) cudaFreeAsync(q, c->stream);
+  cudaStreamSynchronize(c->stream);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   std::free(c->host_e);
@@ -590,9 +594,11 @@ int lise_create(const lise_params* p, lise_ctx** out) {
     c->own_stream = true;
   }
   const size_t sb = (size_t)c->ns * sizeof(double2);
+  // stream-ordered allocations from the device's default memory pool (cheap to
+  // create and free while other contexts run; see free_ctx)
   auto alloc = [&](void** q, size_t bytes) {
     if (rc != LISE_OK) return;
-    cudaError_t e = cudaMalloc(q, bytes);
+    cudaError_t e = cudaMallocAsync(q, bytes, c->stream);
     if (e != cudaSuccess) {
       cudaGetLastError();
       rc = (e == cudaErrorMemoryAllocation) ? LISE_ENOMEM : LISE_ECUDA;
@@ -697,6 +703,23 @@ static int set_state_common(lise_ctx* c, const double* psi, double t0, double dt
 
 int lise_set_state(lise_ctx* c, const double* psi, double t0, double dt) {
   return set_state_common(c, psi, t0, dt, cudaMemcpyHostToDevice);
+}
+
+int lise_set_state_enqueue(lise_ctx* c, const double* psi, double t0, double dt) {
+  if (!c || !psi || !(dt != 0.0) || !std::isfinite(dt) || !std::isfinite(t0)) return LISE_EINVAL;
+  if (c->sticky) return c->sticky;
+  if (cudaSetDevice(c->device) != cudaSuccess) return LISE_ECUDA;
+  c->ready = 0;
+  TRY(cu(cudaMemcpyAsync(c->slot[0], psi, (size_t)c->ns * sizeof(double2), cudaMemcpyHostToDevice, c->stream)));
+  TRY(launch_finite_check(c->slot[0], c->ns, c->err, c->stream) ? LISE_ECUDA : LISE_OK);
+  if (dt != c->dt) drop_graphs(c);
+  const int rc = start_procedure(c, t0, dt);
+  if (rc != LISE_OK) {
+    c->sticky = rc;
+    return rc;
+  }
+  c->ready = 1;
+  return LISE_OK;
 }
 
 int lise_set_state_device(lise_ctx* c, const double* psi_dev, double t0, double dt) {

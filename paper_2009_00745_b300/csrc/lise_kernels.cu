@@ -829,11 +829,9 @@ template <int N>
 static int planes_oz_n(const PlanesArgs& a, cudaStream_t s) {
   using P = OzPlanes<N>;
   auto kern = k_planes_oz<N>;
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P::smem) != cudaSuccess) return 3;
-    attr = true;
-  }
+  // once per process (thread-safe initialisation of a function-local static)
+  static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P::smem);
+  if (attr != cudaSuccess) return 3;
   const long blocks = (a.n_planes + P::PB - 1) / P::PB;
   if (blocks <= 0) return 0;
   if (!a.ozb) return 1;
@@ -849,11 +847,9 @@ static int planes_n(const PlanesArgs& a, cudaStream_t s) {
   constexpr int NT = 256;
   const size_t smem = (size_t)PB * N * (N + 1) * sizeof(T) + N * sizeof(T) + N * sizeof(R);
   auto kern = k_planes<R, N, PB, NT>;
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 3;
-    attr = true;
-  }
+  // once per process (thread-safe initialisation of a function-local static)
+  static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (attr != cudaSuccess) return 3;
   const long blocks = (a.n_planes + PB - 1) / PB;
   if (blocks <= 0) return 0;
   kern<<<(unsigned)blocks, NT, smem, s>>>(a);
@@ -869,11 +865,9 @@ static int pencils_nm(const PencilArgs& a, cudaStream_t s) {
   const size_t smem = (size_t)pencil_smem_bytes<T, N, TX, QB>();
   auto kern = k_pencils<R, N, TX, QB, MODE>;
   if (pencil_oz<R, N>() && !a.ozb) return 1;
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 3;
-    attr = true;
-  }
+  // once per process (thread-safe initialisation of a function-local static)
+  static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (attr != cudaSuccess) return 3;
   const int n_groups = (a.n_qp + a.qg - 1) / a.qg;
   dim3 grid((N / TX) * N, n_groups);
   kern<<<grid, N * TX, smem, s>>>(a);

@@ -1,17 +1,21 @@
 // lise_serve.cu -- a request loop over one GPU (lise_server_* in include/lise.h).
 //
 // Each request is one independent TDSLDA evolution (parameters, initial state,
-// number of ABM steps).  A worker thread owns the device and repeats:
-//   1. for every active request whose previous chunk of steps has finished on
-//      the GPU, enqueue the next chunk (lise_step on the request's own stream);
-//   2. retire requests whose last chunk has finished: copy the final state to
-//      the request's host buffer, compute E and N, free its context (its HBM
-//      budget share returns to the pool);
-//   3. admit queued requests in arrival order while the sum of their device
-//      footprints (lise_footprint_bytes) stays within the budget and fewer than
-//      max_active are active: create the context and run lise_set_state (the
-//      H2D copy and the series-expansion start).  Step chunks already enqueued
-//      for other requests keep the GPU busy meanwhile.
+// number of ABM steps).  Two host threads share the device:
+//   stepper  for every active request whose previous chunk of steps has finished
+//            on the GPU (event query), enqueue the next chunk (lise_step on the
+//            request's own stream); a request whose last chunk finished moves to
+//            the retire list.  It never blocks on the device, so the GPU stays fed.
+//   service  (kServiceThreads of them, so that the host-side copies of several
+//            requests proceed in parallel) retires finished requests (copy the final state to the request's
+//            host buffer, E and N, free the context: stream-ordered frees, no
+//            device-wide synchronisation) and admits queued requests while the sum
+//            of their device footprints (lise_footprint_bytes) stays within the
+//            budget and fewer than max_active are in flight: create the context
+//            and enqueue the H2D copy and the series-expansion start without
+//            waiting for the device.
+//            Order: arrival (FIFO), or first fit with a bound on how often one
+//            request may be passed over.
 // Work of different requests overlaps on the device through their streams;
 // every request runs the same deterministic kernels on its own buffers, so its
 // result does not depend on what else is in flight.
@@ -30,6 +34,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/lise.h"
+#include "lise_internal.h"
 
 namespace {
 
@@ -37,7 +42,11 @@ struct Request {
   long id = 0;
   lise_params p{};
   std::vector<double> v_static;
-  double* host = nullptr;  // input state, then the final state
+  double* host = nullptr;  // input state, then the final state (owned copy)
+  bool pinned = false;     // page-locked (cudaHostAlloc) rather than malloc
+  bool borrowed = false;   // caller's buffers instead of an owned copy:
+  const double* src = nullptr;  //   initial state, read at admission
+  double* dst = nullptr;        //   final state (may be null), written at completion
   size_t bytes = 0;
   double t0 = 0, dt = 0;
   int n_steps = 0, done_steps = 0;
@@ -46,7 +55,9 @@ struct Request {
   cudaStream_t stream = nullptr;
   cudaEvent_t ev = nullptr;
   bool ev_pending = false;
+  int status = LISE_OK;
   enum State { QUEUED, ACTIVE, DONE } state = QUEUED;
+  int skipped = 0;  // times a later request was admitted ahead of this one
   lise_request_info info{};
 };
 
@@ -57,29 +68,50 @@ struct lise_server {
   size_t budget = 0;
   int max_active = 1;
   int steps_per_turn = 1;
+  int policy = LISE_ADMIT_FIFO;
+  int max_skips = 0;
   std::mutex mu;
-  std::condition_variable cv_work, cv_done;
+  std::condition_variable cv_service, cv_done;
   std::deque<Request*> queue;
-  std::vector<Request*> active;
+  std::vector<Request*> active;   // stepped by the stepper
+  std::vector<Request*> retire;   // finished stepping (or failed), for the service thread
+  int in_flight = 0;              // admitted and not yet retired
   std::map<long, Request*> all;
   size_t used = 0, peak_used = 0;
   int peak_active = 0;
   long next_id = 1;
   bool stop = false;
-  std::thread worker;
+  std::thread stepper;
+  std::vector<std::thread> service;
   std::chrono::steady_clock::time_point t0;
 
   double now() const {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
-  void run();
+  void run_stepper();
+  void run_service();
 };
 
 namespace {
 
-void finish(lise_server* s, Request* r, int status) {
+constexpr int kServiceThreads = 4;
+
+void release_host(Request* r) {
+  if (!r->host) return;
+  if (r->pinned)
+    cudaFreeHost(r->host);
+  else
+    std::free(r->host);
+  r->host = nullptr;
+}
+
+// Final state, E, N; free the context and the request's budget share.
+void finish(lise_server* s, Request* r) {
+  int status = r->status;
   if (r->ctx) {
-    if (status == LISE_OK) status = lise_get_state(r->ctx, r->host);
+    double* out = r->borrowed ? r->dst : r->host;
+    if (status == LISE_OK && out) status = lise_get_state(r->ctx, out);
+    if (status == LISE_OK && !out) status = lise_sync(r->ctx);
     double t = 0;
     lise_get_time(r->ctx, &t);
     r->info.t = t;
@@ -96,85 +128,120 @@ void finish(lise_server* s, Request* r, int status) {
   r->info.done_s = s->now();
   r->state = Request::DONE;
   s->used -= r->footprint;
-  for (size_t i = 0; i < s->active.size(); ++i)
-    if (s->active[i] == r) {
-      s->active.erase(s->active.begin() + i);
-      break;
-    }
+  --s->in_flight;
   s->cv_done.notify_all();
+}
+
+// Context, stream and series start of an admitted request (service thread).
+int admit(Request* r) {
+  int rc = cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking) == cudaSuccess ? LISE_OK : LISE_ECUDA;
+  if (rc == LISE_OK && cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming) != cudaSuccess) rc = LISE_ECUDA;
+  if (rc == LISE_OK) {
+    r->p.stream = r->stream;
+    r->p.v_static = r->v_static.empty() ? nullptr : r->v_static.data();
+    rc = lise_create(&r->p, &r->ctx);
+  }
+  if (rc == LISE_OK) rc = lise_set_state_enqueue(r->ctx, r->borrowed ? r->src : r->host, r->t0, r->dt);
+  return rc;
 }
 
 }  // namespace
 
-void lise_server::run() {
+void lise_server::run_stepper() {
   cudaSetDevice(device);
+  std::vector<Request*> act;
   for (;;) {
-    std::vector<Request*> act;
     {
-      std::unique_lock<std::mutex> lk(mu);
-      cv_work.wait(lk, [&] { return stop || !queue.empty() || !active.empty(); });
-      if (stop && queue.empty() && active.empty()) return;
+      std::lock_guard<std::mutex> lk(mu);
+      if (stop && queue.empty() && in_flight == 0) return;
       act = active;
     }
     bool progressed = false;
-    // 1-2: enqueue the next chunk of every request whose last chunk finished; retire finished ones
     for (Request* r : act) {
       if (r->ev_pending) {
-        cudaError_t q = cudaEventQuery(r->ev);
+        const cudaError_t q = cudaEventQuery(r->ev);
         if (q == cudaErrorNotReady) continue;
         r->ev_pending = false;
-        if (q != cudaSuccess) {
-          finish(this, r, LISE_ECUDA);
-          progressed = true;
-          continue;
+        if (q != cudaSuccess) r->status = LISE_ECUDA;
+      }
+      bool last = r->status != LISE_OK || r->done_steps >= r->n_steps;
+      if (!last) {
+        const int k = std::min(steps_per_turn, r->n_steps - r->done_steps);
+        int rc = lise_step(r->ctx, k, r->dt);
+        if (rc == LISE_OK && cudaEventRecord(r->ev, r->stream) != cudaSuccess) rc = LISE_ECUDA;
+        if (rc != LISE_OK) {
+          r->status = rc;
+          last = true;
+        } else {
+          r->done_steps += k;
+          r->ev_pending = true;
         }
       }
-      if (r->done_steps >= r->n_steps) {
-        finish(this, r, lise_sync(r->ctx));
-        progressed = true;
-        continue;
+      if (last) {
+        std::lock_guard<std::mutex> lk(mu);
+        active.erase(std::find(active.begin(), active.end(), r));
+        retire.push_back(r);
+        cv_service.notify_one();
       }
-      const int k = std::min(steps_per_turn, r->n_steps - r->done_steps);
-      int rc = lise_step(r->ctx, k, r->dt);
-      if (rc == LISE_OK && cudaEventRecord(r->ev, r->stream) != cudaSuccess) rc = LISE_ECUDA;
-      if (rc != LISE_OK) {
-        finish(this, r, rc);
+      progressed = true;
+    }
+    if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(100));
+  }
+}
+
+void lise_server::run_service() {
+  cudaSetDevice(device);
+  for (;;) {
+    Request* done = nullptr;
+    Request* r = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(mu);
+      auto pick_next = [&]() -> std::deque<Request*>::iterator {
+        if (queue.empty() || in_flight >= max_active) return queue.end();
+        for (auto it = queue.begin(); it != queue.end(); ++it) {
+          if (used + (*it)->footprint <= budget) return it;
+          // FIFO, or a request already passed over max_skips times: nothing later may go first
+          if (policy == LISE_ADMIT_FIFO || (*it)->skipped >= max_skips) break;
+        }
+        return queue.end();
+      };
+      cv_service.wait_for(lk, std::chrono::milliseconds(50), [&] {
+        return stop || !retire.empty() || pick_next() != queue.end();
+      });
+      if (stop && queue.empty() && in_flight == 0) {
+        cv_service.notify_all();
+        return;
+      }
+      if (!retire.empty()) {  // retirements first: they return budget
+        done = retire.back();
+        retire.pop_back();
       } else {
-        r->done_steps += k;
-        r->ev_pending = true;
+        auto it = pick_next();
+        if (it != queue.end()) {
+          for (auto jt = queue.begin(); jt != it; ++jt) ++(*jt)->skipped;
+          r = *it;
+          queue.erase(it);
+          used += r->footprint;
+          peak_used = std::max(peak_used, used);
+          ++in_flight;
+          peak_active = std::max(peak_active, in_flight);
+          r->state = Request::ACTIVE;
+          r->info.admit_s = now();
+        }
       }
-      progressed = true;
     }
-    // 3: admission in arrival order under the budget
-    for (;;) {
-      Request* r = nullptr;
-      {
-        std::lock_guard<std::mutex> lk(mu);
-        if (queue.empty() || (int)active.size() >= max_active || used + queue.front()->footprint > budget) break;
-        r = queue.front();
-        queue.pop_front();
-        used += r->footprint;
-        if (used > peak_used) peak_used = used;
-        r->state = Request::ACTIVE;
-        r->info.admit_s = now();
-      }
-      int rc = cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking) == cudaSuccess ? LISE_OK : LISE_ECUDA;
-      if (rc == LISE_OK && cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming) != cudaSuccess) rc = LISE_ECUDA;
-      if (rc == LISE_OK) {
-        r->p.stream = r->stream;
-        r->p.v_static = r->v_static.empty() ? nullptr : r->v_static.data();
-        rc = lise_create(&r->p, &r->ctx);
-      }
-      if (rc == LISE_OK) rc = lise_set_state(r->ctx, r->host, r->t0, r->dt);
-      {
-        std::lock_guard<std::mutex> lk(mu);
+    if (done) {
+      finish(this, done);
+      cv_service.notify_all();  // budget returned: another thread may admit
+    }
+    if (r) {
+      r->status = admit(r);
+      std::lock_guard<std::mutex> lk(mu);
+      if (r->status == LISE_OK)
         active.push_back(r);
-        if ((int)active.size() > peak_active) peak_active = (int)active.size();
-      }
-      if (rc != LISE_OK) finish(this, r, rc);
-      progressed = true;
+      else
+        retire.push_back(r);
     }
-    if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(200));
   }
 }
 
@@ -192,13 +259,21 @@ int lise_server_create(int device, size_t hbm_budget_bytes, int max_active, int 
   s->max_active = max_active;
   s->steps_per_turn = steps_per_turn;
   s->t0 = std::chrono::steady_clock::now();
-  s->worker = std::thread([s] { s->run(); });
+  // keep freed context memory in the device's pool for the next requests (up to the budget)
+  cudaMemPool_t pool;
+  if (cudaSetDevice(device) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+    unsigned long long keep = hbm_budget_bytes;  // the attribute is a 64-bit unsigned value
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  s->stepper = std::thread([s] { s->run_stepper(); });
+  for (int k = 0; k < kServiceThreads; ++k) s->service.emplace_back([s] { s->run_service(); });
   *out = s;
   return LISE_OK;
 }
 
-int lise_server_submit(lise_server* s, const lise_params* p, const double* psi, double t0, double dt, int n_steps,
-                       long* id_out) {
+namespace {
+int submit_common(lise_server* s, const lise_params* p, const double* psi, double* psi_out, bool borrow, double t0,
+                  double dt, int n_steps, long* id_out) {
   if (!s || !p || !psi || !id_out || n_steps < 0 || !(dt != 0.0)) return LISE_EINVAL;
   const size_t fp = lise_footprint_bytes(p);
   if (fp == 0) return LISE_EINVAL;
@@ -211,12 +286,20 @@ int lise_server_submit(lise_server* s, const lise_params* p, const double* psi, 
   const long nxyz = (long)p->nx * p->ny * p->nz;
   if (p->v_static) r->v_static.assign(p->v_static, p->v_static + nxyz);
   r->bytes = (size_t)p->n_qp * 2 * nxyz * 2 * sizeof(double);
-  r->host = static_cast<double*>(std::malloc(r->bytes));
-  if (!r->host) {
-    delete r;
-    return LISE_ENOMEM;
+  if (borrow) {
+    r->borrowed = true;
+    r->src = psi;
+    r->dst = psi_out;
+  } else {
+    // pageable host copy: page-locking multi-GB buffers (cudaHostAlloc) stalls the
+    // other threads' CUDA calls for seconds, which costs more than the slower copies
+    r->host = static_cast<double*>(std::malloc(r->bytes));
+    if (!r->host) {
+      delete r;
+      return LISE_ENOMEM;
+    }
+    std::memcpy(r->host, psi, r->bytes);
   }
-  std::memcpy(r->host, psi, r->bytes);
   r->t0 = t0;
   r->dt = dt;
   r->n_steps = n_steps;
@@ -224,7 +307,7 @@ int lise_server_submit(lise_server* s, const lise_params* p, const double* psi, 
   {
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->stop) {
-      std::free(r->host);
+      release_host(r);
       delete r;
       return LISE_ESTATE;
     }
@@ -234,8 +317,19 @@ int lise_server_submit(lise_server* s, const lise_params* p, const double* psi, 
     s->all[r->id] = r;
     *id_out = r->id;
   }
-  s->cv_work.notify_one();
+  s->cv_service.notify_one();
   return LISE_OK;
+}
+}  // namespace
+
+int lise_server_submit(lise_server* s, const lise_params* p, const double* psi, double t0, double dt, int n_steps,
+                       long* id_out) {
+  return submit_common(s, p, psi, nullptr, false, t0, dt, n_steps, id_out);
+}
+
+int lise_server_submit_borrowed(lise_server* s, const lise_params* p, const double* psi_in, double* psi_out, double t0,
+                                double dt, int n_steps, long* id_out) {
+  return submit_common(s, p, psi_in, psi_out, true, t0, dt, n_steps, id_out);
 }
 
 int lise_server_wait(lise_server* s, long id, double* psi_out, lise_request_info* info) {
@@ -249,12 +343,32 @@ int lise_server_wait(lise_server* s, long id, double* psi_out, lise_request_info
     s->cv_done.wait(lk, [&] { return r->state == Request::DONE; });
     s->all.erase(it);
   }
-  if (psi_out && r->info.status == LISE_OK) std::memcpy(psi_out, r->host, r->bytes);
+  if (psi_out && !r->borrowed && r->info.status == LISE_OK) std::memcpy(psi_out, r->host, r->bytes);
   if (info) *info = r->info;
   const int status = r->info.status;
-  std::free(r->host);
+  release_host(r);
   delete r;
   return status;
+}
+
+int lise_server_poll(lise_server* s, long id, int* done) {
+  if (!s || !done) return LISE_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->all.find(id);
+  if (it == s->all.end()) return LISE_EINVAL;
+  *done = it->second->state == Request::DONE ? 1 : 0;
+  return LISE_OK;
+}
+
+int lise_server_set_admission(lise_server* s, int policy, int max_skips) {
+  if (!s || (policy != LISE_ADMIT_FIFO && policy != LISE_ADMIT_FIRST_FIT) || max_skips < 0) return LISE_EINVAL;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->policy = policy;
+    s->max_skips = max_skips;
+  }
+  s->cv_service.notify_one();
+  return LISE_OK;
 }
 
 int lise_server_stats(lise_server* s, size_t* peak_used_bytes, int* peak_active) {
@@ -271,10 +385,12 @@ void lise_server_destroy(lise_server* s) {
     std::lock_guard<std::mutex> lk(s->mu);
     s->stop = true;
   }
-  s->cv_work.notify_all();
-  if (s->worker.joinable()) s->worker.join();
+  s->cv_service.notify_all();
+  if (s->stepper.joinable()) s->stepper.join();
+  for (auto& t : s->service)
+    if (t.joinable()) t.join();
   for (auto& kv : s->all) {
-    std::free(kv.second->host);
+    release_host(kv.second);
     delete kv.second;
   }
   delete s;

@@ -19,6 +19,7 @@ FP64 = 0
 MIXED = 1
 
 OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ESTATE = range(7)
+ADMIT_FIFO, ADMIT_FIRST_FIT = 0, 1
 KC_PLANES, KC_PENCILS, KC_REDUCE, KC_POINTWISE, KC_COUNT = range(5)
 
 
@@ -65,7 +66,11 @@ SIGNATURES = {
     "lise_server_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_int,
                                      C.POINTER(C.c_long)]),
     "lise_server_wait": (C.c_int, [C.c_void_p, C.c_long, C.c_void_p, C.c_void_p]),
+    "lise_server_submit_borrowed": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
+                                              C.c_double, C.c_int, C.POINTER(C.c_long)]),
     "lise_server_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t), C.POINTER(C.c_int)]),
+    "lise_server_poll": (C.c_int, [C.c_void_p, C.c_long, C.POINTER(C.c_int)]),
+    "lise_server_set_admission": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "lise_server_destroy": (None, [C.c_void_p]),
 }
 
@@ -266,16 +271,30 @@ class Server:
                                          int(steps_per_turn), C.byref(h)), "lise_server_create")
         self._h = h
         self._shapes = {}
+        self._borrowed = {}  # id -> (input, output) arrays the server reads/writes until wait()
 
     def submit(self, N, n_qp, psi, t0, dt, n_steps, *, a=1.0, alpha=1.0, beta=0.0, mu=0.0, g=0.0,
-               v_static=None, drive_A=0.0, drive_Omega=0.0, precision="fp64"):
+               v_static=None, drive_A=0.0, drive_Omega=0.0, precision="fp64", copy=True, out=None):
+        """Queue one evolution.  copy=True: the server copies psi now.  copy=False: the
+        server reads psi at admission and writes the final state into `out` (None: no
+        state is returned); both arrays must stay untouched until wait()."""
         p, vs = _params(N, n_qp, a, alpha, beta, mu, g, v_static, drive_A, drive_Omega, precision, 0, 0, None)
         ptr, dev, keep = _ptr(psi, count=n_qp * 2 * N ** 3)
         if dev:
             raise ValueError("the server takes host states")
         rid = C.c_long()
-        _check(load().lise_server_submit(self._h, C.byref(p), ptr, float(t0), float(dt), int(n_steps),
-                                         C.byref(rid)), "lise_server_submit")
+        if copy:
+            _check(load().lise_server_submit(self._h, C.byref(p), ptr, float(t0), float(dt), int(n_steps),
+                                             C.byref(rid)), "lise_server_submit")
+        else:
+            optr = None
+            if out is not None:
+                optr, odev, _ = _ptr(out, count=n_qp * 2 * N ** 3, writable=True)
+                if odev:
+                    raise ValueError("the server takes host states")
+            _check(load().lise_server_submit_borrowed(self._h, C.byref(p), ptr, optr, float(t0), float(dt),
+                                                      int(n_steps), C.byref(rid)), "lise_server_submit_borrowed")
+            self._borrowed[rid.value] = (keep, out)
         self._shapes[rid.value] = (n_qp, 2, N, N, N)
         return rid.value
 
@@ -286,13 +305,31 @@ class Server:
                            drive_Omega=w.drive_Omega, precision=precision or w.precision)
 
     def wait(self, rid, want_state=True):
+        """(final state or None, info dict).  For copy=False submissions the state is the
+        `out` array given at submit (None if none was given)."""
         shape = self._shapes.pop(rid)
-        out = np.empty(shape, dtype=np.complex128) if want_state else None
+        borrowed = self._borrowed.pop(rid, None)
+        out = None
+        if borrowed is None and want_state:
+            out = np.empty(shape, dtype=np.complex128)
         info = RequestInfo()
         rc = load().lise_server_wait(self._h, int(rid), None if out is None else out.ctypes.data,
                                      C.byref(info))
         _check(rc, "lise_server_wait")
+        if borrowed is not None:
+            out = borrowed[1]
         return out, info.as_dict()
+
+    def poll(self, rid):
+        """True if request rid has finished (wait() then returns at once)."""
+        d = C.c_int()
+        _check(load().lise_server_poll(self._h, int(rid), C.byref(d)), "lise_server_poll")
+        return bool(d.value)
+
+    def set_admission(self, policy="fifo", max_skips=0):
+        """'fifo' (arrival order) or 'first_fit' (a request may be passed over at most max_skips times)."""
+        code = {"fifo": ADMIT_FIFO, "first_fit": ADMIT_FIRST_FIT}[policy]
+        _check(load().lise_server_set_admission(self._h, code, int(max_skips)), "lise_server_set_admission")
 
     def stats(self):
         u, a = C.c_size_t(), C.c_int()

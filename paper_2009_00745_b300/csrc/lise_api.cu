@@ -99,8 +99,8 @@ int check_params(const lise_params* p) {
   return LISE_OK;
 }
 
-void choose_groups(int N, int n_qp, int* qg, int* n_groups) {
-  const int tiles = (N / pencil_tx(N)) * N;
+void choose_groups(int N, int n_qp, int mixed, int* qg, int* n_groups) {
+  const int tiles = (N / pencil_tx(N, mixed)) * N;
   int q = 64;
   while (q > 4 && (long)tiles * ((n_qp + q - 1) / q) < 2048) q /= 2;
   if (q > n_qp) q = n_qp;
@@ -118,7 +118,7 @@ Footprint footprint(const lise_params* p) {
   const long nxyz = N * N * N;
   const long ns = (long)p->n_qp * 2 * nxyz;
   int qg, ng;
-  choose_groups((int)N, p->n_qp, &qg, &ng);
+  choose_groups((int)N, p->n_qp, p->precision == LISE_MIXED, &qg, &ng);
   // 2 y slots and Q in complex128; 4 y', m, R and P-C in the compute precision
   const size_t rc = p->precision == LISE_MIXED ? sizeof(float2) : sizeof(double2);
   f.state = 3 * (size_t)ns * sizeof(double2) + 7 * (size_t)ns * rc;
@@ -127,7 +127,7 @@ Footprint footprint(const lise_params* p) {
   f.small = (size_t)nxyz * (2 * sizeof(double) + 2 * sizeof(double2) + sizeof(double) + sizeof(double2) +
                             sizeof(double) + 2 * sizeof(double)) +
             3 * (size_t)N * sizeof(double2) + 256;
-  if (p->remove_phase) f.small += (size_t)p->n_qp * (1 + pencil_blocks_x((int)N)) * sizeof(double);
+  if (p->remove_phase) f.small += (size_t)p->n_qp * (1 + pencil_blocks_x((int)N, p->precision == LISE_MIXED)) * sizeof(double);
   f.total = f.state + f.txy + f.partials + f.small;
   return f;
 }
@@ -585,7 +585,7 @@ int lise_create(const lise_params* p, lise_ctx** out) {
   c->ns = (long)p->n_qp * 2 * c->nxyz;
   c->mixed = p->precision == LISE_MIXED;
   c->device = p->device;
-  choose_groups(c->N, p->n_qp, &c->qg, &c->n_groups);
+  choose_groups(c->N, p->n_qp, c->mixed, &c->qg, &c->n_groups);
   int rc = LISE_OK;
   if (p->stream) {
     c->stream = (cudaStream_t)p->stream;
@@ -640,7 +640,7 @@ int lise_create(const lise_params* p, lise_ctx** out) {
     c->oz_sD = ozaki_table(c->N, p->dx, p->alpha, ozt.data());
     alloc((void**)&c->ozb, ozt.size() * sizeof(uint32_t));
   }
-  c->n_blocks_x = pencil_blocks_x(c->N);
+  c->n_blocks_x = pencil_blocks_x(c->N, c->mixed);
   if (p->remove_phase) {
     alloc((void**)&c->eta, (size_t)p->n_qp * sizeof(double));
     alloc((void**)&c->eta_part, (size_t)p->n_qp * c->n_blocks_x * sizeof(double));

@@ -363,7 +363,7 @@ __host__ __device__ constexpr int pencil_smem_bytes() {
 }
 
 template <typename R, int N, int TX, int QB, int MODE>
-__global__ void __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N * TX == 256 ? 2 : 1) k_pencils(PencilArgs a) {
+__global__ void __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N * TX == 256 ? 2 : ((sizeof(R) == 8 && N * TX == 128) ? 4 : 1)) k_pencils(PencilArgs a) {
   using T = typename Cx<R>::T;
   constexpr int NT = N * TX;
   // one component block [z][x] in shared memory; for 8-byte elements the blocks are
@@ -822,7 +822,9 @@ bool supported_n(int N) {
     default: return false;
   }
 }
-int pencil_tx(int N) { return N % 8 == 0 ? 8 : 4; }
+// FP64 tensor-core path: 4-wide tiles (128-thread blocks, 4 resident per SM), so that
+// blocks in their digit/tensor phase overlap others in their FP64 epilogue
+int pencil_tx(int N, int mixed) { return (ozaki_path(N, mixed) || N % 8 != 0) ? 4 : 8; }
 int pencil_qb(int N, int mixed) { return (N >= 40 || (mixed && N >= 32)) ? 2 : 4; }
 
 template <int N>
@@ -859,7 +861,7 @@ static int planes_n(const PlanesArgs& a, cudaStream_t s) {
 template <typename R, int N, int MODE>
 static int pencils_nm(const PencilArgs& a, cudaStream_t s) {
   using T = typename Cx<R>::T;
-  constexpr int TX = (N % 8 == 0) ? 8 : 4;
+  constexpr int TX = (pencil_oz<R, N>() || N % 8 != 0) ? 4 : 8;  // = pencil_tx
   // states per batch: fewer at large N (registers) and for the FP32 path from N = 32 (staging)
   constexpr int QB = (N >= 40 || (sizeof(R) == 4 && N >= 32)) ? 2 : 4;
   const size_t smem = (size_t)pencil_smem_bytes<T, N, TX, QB>();
@@ -1013,7 +1015,7 @@ int launch_eta_reduce(const double* eta_part, int n_qp, int n_blocks, double a3,
   return cudaGetLastError() == cudaSuccess ? 0 : 3;
 }
 
-int pencil_blocks_x(int N) { return (N / pencil_tx(N)) * N; }
+int pencil_blocks_x(int N, int mixed) { return (N / pencil_tx(N, mixed)) * N; }
 
 int launch_finite_check(const double2* x, long count, int* err, cudaStream_t s) {
   k_finite<<<148 * 4, 256, 0, s>>>(x, count, err);

@@ -156,7 +156,7 @@ double pairing_lattice_c(double a, double alpha);
 int launch_finite_check(const double2* x, long count, int* err, cudaStream_t s);
 // eta[q] = a^3 * sum over the pencil blocks of eta_part[q][block] (compensated).
 int launch_eta_reduce(const double* eta_part, int n_qp, int n_blocks, double a3, double* eta, cudaStream_t s);
-int pencil_blocks_x(int N);
+int pencil_blocks_x(int N, int mixed);
 // FP64 kinetic operator on the tensor cores (lise_ozaki.cuh): used for the FP64
 // path on lattices with N a multiple of 16.  The table holds the D2 digit
 // fragments (ozaki_table_words(N) uint32 words); ozaki_table returns its scale
@@ -165,7 +165,7 @@ bool ozaki_path(int N, int mixed);
 size_t ozaki_table_words(int N);
 int ozaki_table(int N, double a, double alpha, uint32_t* out);
 // Tile width (x values per pencil block) and group width for a lattice.
-int pencil_tx(int N);
+int pencil_tx(int N, int mixed);
 int pencil_qb(int N, int mixed);
 bool supported_n(int N);
 

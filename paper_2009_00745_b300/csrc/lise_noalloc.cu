@@ -76,7 +76,7 @@ extern "C" int lise_rhs_noalloc(const lise_params* p, const double* psi_dev, dou
   const bool mixed = p->precision == LISE_MIXED;
   // density groups: same rule as a context (at most 64 states per group,
   // enough groups to fill the GPU)
-  const int tiles = (N / pencil_tx(N)) * N;
+  const int tiles = (N / pencil_tx(N, mixed)) * N;
   int qg = 64;
   while (qg > 4 && (long)tiles * ((p->n_qp + qg - 1) / qg) < 2048) qg /= 2;
   if (qg > p->n_qp) qg = p->n_qp;
@@ -99,7 +99,7 @@ extern "C" int lise_rhs_noalloc(const lise_params* p, const double* psi_dev, dou
   const bool use_oz = ozaki_path(N, mixed);
   const size_t oz_words = use_oz ? ozaki_table_words(N) : 0;
   const size_t o_oz = off;     off += up256(oz_words * sizeof(uint32_t));
-  const int nbx = pencil_blocks_x(N);
+  const int nbx = pencil_blocks_x(N, mixed);
   const size_t o_eta = off;    off += up256(p->remove_phase ? (size_t)p->n_qp * sizeof(double) : 0);
   const size_t o_etap = off;   off += up256(p->remove_phase ? (size_t)p->n_qp * nbx * sizeof(double) : 0);
   if (off > (size_t)LISE_NOALLOC_SCRATCH_BYTES) return LISE_ENOMEM;

@@ -64,11 +64,13 @@ def test_admission_policy(policy, small_first):
     fa, fb, fs = (L.footprint_bytes(16, w.n_qp) for w in (a, big, small))
     budget = fa + fb - 1
     assert fa + fs <= budget and fb <= budget
+    states = [w.initial_state() for w in (a, big, small)]  # built before the clock starts
     with L.Server(budget, max_active=4, steps_per_turn=2) as srv:
         srv.set_admission(policy, max_skips=4)
-        ia = srv.submit_workload(a, n_steps=120)
-        ib = srv.submit_workload(big, n_steps=2)
-        i_s = srv.submit_workload(small, n_steps=2)
+        # the long request runs far longer than the two submissions that follow it
+        ia = srv.submit_workload(a, psi=states[0], n_steps=1000)
+        ib = srv.submit_workload(big, psi=states[1], n_steps=2)
+        i_s = srv.submit_workload(small, psi=states[2], n_steps=2)
         t_end = time.time() + 120
         while not srv.poll(ia) and time.time() < t_end:
             time.sleep(0.01)
@@ -86,9 +88,11 @@ def test_first_fit_skip_bound():
     big = W.ufg_plane_waves(16, 256, noise_eps=0.05)
     small = W.ufg_plane_waves(16, 16, noise_eps=0.05)
     fa, fb = L.footprint_bytes(16, 96), L.footprint_bytes(16, 256)
+    states = [w.initial_state() for w in (a, big, small)]
     with L.Server(fa + fb - 1, max_active=4, steps_per_turn=2) as srv:
         srv.set_admission("first_fit", max_skips=0)
-        ids = [srv.submit_workload(w, n_steps=k) for w, k in ((a, 60), (big, 2), (small, 2))]
+        ids = [srv.submit_workload(w, psi=x, n_steps=k) for w, x, k in ((a, states[0], 1000), (big, states[1], 2),
+                                                                         (small, states[2], 2))]
         infos = [srv.wait(i, want_state=False)[1] for i in ids]
     assert infos[2]["admit_s"] >= infos[1]["admit_s"]
     with L.Server(1 << 30) as srv:

@@ -84,11 +84,31 @@ __device__ __forceinline__ void dens_acc(double2 u, double2 v, double& sn, doubl
 }
 // The same from FP32 operands (the mixed path, whose densities only set the potentials
 // of its FP32 H psi): products in FP32 (relative rounding 2^-24, the level of the FP32
-// potentials themselves), sums in FP64.
-__device__ __forceinline__ void dens_acc(float2 u, float2 v, double& sn, double& sr, double& si) {
-  sn += f2d_bits(fmaf(v.x, v.x, v.y * v.y));
-  sr += f2d_bits(fmaf(u.x, v.x, u.y * v.y));
-  si += f2d_bits(fmaf(u.y, v.x, -(u.x * v.y)));
+// potentials themselves), compensated (Kahan) FP32 sums over the thread's states (error
+// a few units of 2^-24 of the sum, independent of the count), folded into the FP64
+// partial sums at the end; the sum over groups is FP64 (Neumaier, k_reduce).
+struct KahanF {
+  float s = 0.f, c = 0.f;  // sum and the negative of its lost low part
+  __device__ __forceinline__ void add(float x) {
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return f2d_bits(s) - f2d_bits(c); }
+};
+struct DensF {
+  KahanF n, r, i;
+};
+__device__ __forceinline__ void dens_acc(float2 u, float2 v, DensF& d) {
+  d.n.add(fmaf(v.x, v.x, v.y * v.y));
+  d.r.add(fmaf(u.x, v.x, u.y * v.y));
+  d.i.add(fmaf(u.y, v.x, -(u.x * v.y)));
+}
+__device__ __forceinline__ void dens_fold(const DensF& d, double& sn, double& sr, double& si) {
+  sn += d.n.value();
+  sr += d.r.value();
+  si += d.i.value();
 }
 
 // Asynchronous global -> shared copies (no register staging).  Each thread copies
@@ -408,6 +428,16 @@ __global__ void __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N
   const R Wr = (R)Wv;
   const T Dr = to_r<R>(Dv);
   double sn = 0.0, sr = 0.0, si = 0.0;
+  DensF dF;  // FP32 operands (mixed path)
+  // step-size coefficients of the ABM epilogues, once per thread:
+  //   corrector  y_{n+1} = Q + kc1 m',  p - c = R - kc2 m'
+  //   predictor  Y = sum y?c y'_?,  R = sum r?c y'_?  (see M_DERIV_PREDICT)
+  constexpr bool kCor = MODE == M_CORRECT, kPred = MODE == M_DERIV_PREDICT;
+  const R kc2 = kCor ? (R)(17.0 / 48.0 * a.h) : R(0), kc1 = kCor ? (R)(161.0 / 170.0 * 17.0 / 48.0 * a.h) : R(0);
+  const R h48 = kPred ? (R)(a.h / 48.0) : R(0), c161_ = (R)(161.0 / 170.0), c9_ = (R)(9.0 / 170.0);
+  const R y0c = h48 * (c161_ * R(51) + c9_ * R(119)), y1c = h48 * (c161_ * R(3) - c9_ * R(99)),
+          y2c = h48 * (c161_ + c9_ * R(69)), y3c = h48 * (-c9_ * R(17));
+  const R r0c = h48 * R(68), r1c = h48 * R(-102), r2c = h48 * R(68), r3c = h48 * R(-17);
   auto base = [](int l) { return (l / TX) * CS + (l % TX); };
   // issue the asynchronous copies of one batch's operand and T_xy (own site only)
   auto prefetch = [&](int qb) {
@@ -572,8 +602,7 @@ __global__ void __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N
         if (a.dens) dens_acc(au, av, sn, sr, si);
       } else if (MODE == M_CORRECT) {
         // Eq. c and Eq. y through Q, R:  y_{n+1} = Q + k1 m',  p - c = R - k2 m'
-        const R k2 = (R)(17.0 / 48.0 * a.h);
-        const R k1 = (R)(161.0 / 170.0 * 17.0 / 48.0 * a.h);
+        const R k2 = kc2, k1 = kc1;
         T yo[2];  // y_{n+1} in the compute precision, for its densities
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
@@ -592,7 +621,10 @@ __global__ void __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N
           reinterpret_cast<T*>(a.pc)[i] = T{rr.x - k2 * f.x, rr.y - k2 * f.y};
           yo[c] = to_r<R>(yn);
         }
-        dens_acc(yo[0], yo[1], sn, sr, si);
+        if constexpr (sizeof(R) == 4)
+          dens_acc(yo[0], yo[1], dF);
+        else
+          dens_acc(yo[0], yo[1], sn, sr, si);
       } else if (MODE == M_DERIV_PREDICT) {
         // y'_{n+1}; then Eq. p and Eq. m of step n+2 and that step's Q, R:
         //   pt = h/48 (119 y'_{n+1} - 99 y'_n + 69 y'_{n-1} - 17 y'_{n-2})
@@ -600,11 +632,7 @@ __global__ void __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N
         //   m = hf + pt - (161/170) pc,  Q = hf + (161/170) ct + (9/170) pt,  R = pt - ct.
         // Formed as Y = (161/170) ct + (9/170) pt and R directly from the derivatives,
         // Q = hf + Y and m = Q + (161/170)(R - pc) (as 1 - 9/170 = 161/170, m - Q = (161/170)(pt - ct - pc)).
-        const R h48 = (R)(a.h / 48.0);
-        const R c161 = (R)(161.0 / 170.0), c9 = (R)(9.0 / 170.0);
-        const R y0c = h48 * (c161 * R(51) + c9 * R(119)), y1c = h48 * (c161 * R(3) - c9 * R(99)),
-                y2c = h48 * (c161 + c9 * R(69)), y3c = h48 * (-c9 * R(17));
-        const R r0c = h48 * R(68), r1c = h48 * R(-102), r2c = h48 * R(68), r3c = h48 * R(-17);
+        const R c161 = (R)(161.0 / 170.0);
         T mo[2];
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
@@ -625,7 +653,10 @@ __global__ void __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N
           reinterpret_cast<T*>(a.r)[i] = Rv;
           mo[c] = mv;
         }
-        dens_acc(mo[0], mo[1], sn, sr, si);
+        if constexpr (sizeof(R) == 4)
+          dens_acc(mo[0], mo[1], dF);
+        else
+          dens_acc(mo[0], mo[1], sn, sr, si);
       }
     }
     if constexpr (MODE == M_ETA) {
@@ -644,6 +675,7 @@ __global__ void __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N
     __syncthreads();  // the batch buffer is reused
   }
   if (a.dens) {
+    if constexpr (sizeof(R) == 4) dens_fold(dF, sn, sr, si);
     const long o = (long)g * nxyz + site;
     a.part_n[o] = 2.0 * sn;
     if (MODE != M_ENERGY) {
@@ -714,6 +746,7 @@ __global__ void k_predict(PointwiseArgs a) {
   const R h48 = (R)(a.h / 48.0);
   const R c161 = (R)(161.0 / 170.0), c9 = (R)(9.0 / 170.0);
   double sn = 0, sr = 0, si = 0;
+  DensF dF;  // FP32 operands (mixed path)
   for (int q = q_begin; q < q_end; ++q) {
     T mo[2];  // m in the compute precision, for its densities
 #pragma unroll
@@ -747,8 +780,12 @@ __global__ void k_predict(PointwiseArgs a) {
       }
       reinterpret_cast<T*>(a.r)[i] = T{pt.x - ct.x, pt.y - ct.y};
     }
-    dens_acc(mo[0], mo[1], sn, sr, si);
+    if constexpr (sizeof(R) == 4)
+      dens_acc(mo[0], mo[1], dF);
+    else
+      dens_acc(mo[0], mo[1], sn, sr, si);
   }
+  if constexpr (sizeof(R) == 4) dens_fold(dF, sn, sr, si);
   const long o = (long)g * a.nxyz + s;
   a.part_n[o] = 2.0 * sn;
   a.part_nr[o] = sr;

@@ -862,7 +862,7 @@ bool supported_n(int N) {
 // FP64 tensor-core path: 4-wide tiles (128-thread blocks, 4 resident per SM), so that
 // blocks in their digit/tensor phase overlap others in their FP64 epilogue
 int pencil_tx(int N, int mixed) { return (ozaki_path(N, mixed) || N % 8 != 0) ? 4 : 8; }
-int pencil_qb(int N, int mixed) { return (N >= 40 || (mixed && N >= 32)) ? 2 : 4; }
+int pencil_qb(int N, int mixed) { return (N >= 40 || (N >= 32 && (mixed || ozaki_path(N, mixed)))) ? 2 : 4; }
 
 template <int N>
 static int planes_oz_n(const PlanesArgs& a, cudaStream_t s) {
@@ -900,7 +900,8 @@ static int pencils_nm(const PencilArgs& a, cudaStream_t s) {
   using T = typename Cx<R>::T;
   constexpr int TX = (pencil_oz<R, N>() || N % 8 != 0) ? 4 : 8;  // = pencil_tx
   // states per batch: fewer at large N (registers) and for the FP32 path from N = 32 (staging)
-  constexpr int QB = (N >= 40 || (sizeof(R) == 4 && N >= 32)) ? 2 : 4;
+  // (the FP64 tensor-core path from N = 32 too: registers for four resident blocks)
+  constexpr int QB = (N >= 40 || (sizeof(R) == 4 && N >= 32) || (pencil_oz<R, N>() && N >= 32)) ? 2 : 4;
   const size_t smem = (size_t)pencil_smem_bytes<T, N, TX, QB>();
   auto kern = k_pencils<R, N, TX, QB, MODE>;
   if (pencil_oz<R, N>() && !a.ozb) return 1;

@@ -123,7 +123,7 @@ def read_peaks():
 def kernel_source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2009_00745_b300", "csrc")
-    for name in ("lise_fft.cuh", "lise_kernels.cuh", "lise_kernels.cu"):  # the kernels' sources
+    for name in ("lise_fft.cuh", "lise_ozaki.cuh", "lise_kernels.cuh", "lise_kernels.cu"):  # the kernels' sources
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]

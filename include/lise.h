@@ -103,6 +103,15 @@ int lise_set_state(lise_ctx *c, const double *psi, double t0, double dt);
 /* Same with psi a device pointer (same layout) on the context's device. */
 int lise_set_state_device(lise_ctx *c, const double *psi_dev, double t0, double dt);
 
+/* Boost (Eq. kick, Sec. "External boosts and external potentials"): every state
+ * of the current state y(t) becomes u -> e^{i chi(r)} u, v -> e^{-i chi(r)} v, and
+ * the ABM history restarts through the series start at t with the same dt (as
+ * after lise_set_state; t advances by 3 dt).  chi: host, N^3 doubles [z][y][x]
+ * (e.g. p.r for a velocity p/m; periodic on the lattice when p is a lattice
+ * momentum).  Copies chi; synchronises.  Errors: LISE_ESTATE before set_state,
+ * LISE_EINVAL (null or non-finite chi), LISE_ECUDA. */
+int lise_kick(lise_ctx *c, const double *chi);
+
 /* Enqueues n_steps >= 0 ABM steps (Eqs. p, m, c, y).  dt must equal the
  * set_state dt (the stored history is only valid for that step), else
  * LISE_EINVAL.  Errors: LISE_ESTATE before set_state, LISE_ECUDA. */

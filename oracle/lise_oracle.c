@@ -429,6 +429,27 @@ int or_set_state(or_solver *s, const double complex *psi, double t0, double dt) 
   return 0;
 }
 
+void or_kick(const or_params *p, double complex *psi, const double *chi) {
+  long nt = (long)p->nx * p->ny * p->nz;
+  for (int q = 0; q < p->n_qp; ++q) {
+    double complex *u = psi + (long)q * 2 * nt, *v = u + nt;
+    for (long i = 0; i < nt; ++i) {
+      u[i] *= cexp(I * chi[i]);
+      v[i] *= cexp(-I * chi[i]);
+    }
+  }
+}
+
+int or_solver_kick(or_solver *s, const double *chi) {
+  if (!s->ready) return 1;
+  double complex *psi = (double complex *)malloc(sizeof(double complex) * s->ns);
+  memcpy(psi, s->y0, sizeof(double complex) * s->ns);
+  or_kick(&s->p, psi, chi);
+  int rc = or_set_state(s, psi, s->t, s->dt);
+  free(psi);
+  return rc;
+}
+
 /* Eq. p: p_{n+1} = (y_n + y_{n-1})/2
  *               + h/48 (119 y'_n - 99 y'_{n-1} + 69 y'_{n-2} - 17 y'_{n-3}) */
 void or_abm_predictor(long ns, double h, const double complex *yn, const double complex *ynm1,

@@ -109,6 +109,12 @@ void or_destroy(or_solver *s);
 int or_set_state(or_solver *s, const double complex *psi, double t0, double dt);
 /* n_steps ABM steps of size dt (must equal the set_state dt). */
 int or_step(or_solver *s, int n_steps);
+/* Eq. kick (Sec. "External boosts and external potentials"): u -> e^{i chi(r)} u,
+ * v -> e^{-i chi(r)} v for every state, chi real [z][y][x]. */
+void or_kick(const or_params *p, double complex *psi, const double *chi);
+/* Kick the solver's current state and restart the history through the series
+ * start at the current time with the current step (as after a set_state). */
+int or_solver_kick(or_solver *s, const double *chi);
 void or_get_state(const or_solver *s, double complex *psi_out);
 double or_time(const or_solver *s);
 void or_get_densities(const or_solver *s, double *n, double complex *nu);

@@ -35,6 +35,9 @@ def lib():
         L.or_potentials.argtypes = [vp, vp, vp, d, vp, vp]
         L.or_apply_h.argtypes = [vp, vp, vp, vp, vp]
         L.or_rhs.argtypes = [vp, vp, d, vp]
+        L.or_kick.argtypes = [vp, vp, vp]
+        L.or_solver_kick.argtypes = [vp, vp]
+        L.or_solver_kick.restype = i
         L.or_create.argtypes = [vp]
         L.or_create.restype = vp
         L.or_destroy.argtypes = [vp]
@@ -193,6 +196,15 @@ def eta(p: Params, psi, hpsi):
     return out
 
 
+def kick(p: Params, psi, chi):
+    """Eq. kick: u -> exp(i chi) u, v -> exp(-i chi) v (returns a new array)."""
+    out = _c128(psi, p.shape).copy()
+    chi = np.ascontiguousarray(chi, dtype=np.float64).reshape(p.grid)
+    ps = p._c()
+    lib().or_kick(C.byref(ps), out.ctypes.data, chi.ctypes.data)
+    return out
+
+
 def geff(p: Params, n):
     """(g_eff, d g_eff / dn) at density n."""
     g, dg = C.c_double(), C.c_double()
@@ -264,6 +276,12 @@ class Solver:
         rc = lib().or_set_state(self._h, psi.ctypes.data, float(t0), float(dt))
         if rc:
             raise ValueError("oracle set_state failed")
+
+    def kick(self, chi):
+        """Eq. kick on the current state, then a new series start at the current time."""
+        chi = np.ascontiguousarray(chi, dtype=np.float64).reshape(self.p.grid)
+        if lib().or_solver_kick(self._h, chi.ctypes.data):
+            raise RuntimeError("oracle kick before set_state")
 
     def step(self, n):
         rc = lib().or_step(self._h, int(n))

@@ -726,6 +726,29 @@ int lise_set_state_device(lise_ctx* c, const double* psi_dev, double t0, double 
   return set_state_common(c, psi_dev, t0, dt, cudaMemcpyDeviceToDevice);
 }
 
+int lise_kick(lise_ctx* c, const double* chi) {
+  if (!c || !chi) return LISE_EINVAL;
+  if (c->sticky) return c->sticky;
+  if (!c->ready) return LISE_ESTATE;
+  for (long i = 0; i < c->nxyz; ++i)
+    if (!std::isfinite(chi[i])) return LISE_EINVAL;
+  if (cudaSetDevice(c->device) != cudaSuccess) return LISE_ECUDA;
+  c->ready = 0;
+  // chi into the energy scratch (2 nxyz doubles); the kicked y(t) into slot 0, where the
+  // series start expects its initial state
+  TRY(cu(cudaMemcpyAsync(c->e_site, chi, c->nxyz * sizeof(double), cudaMemcpyHostToDevice, c->stream)));
+  TRY(launch_kick(c->slot[c->y0_slot], c->slot[0], c->e_site, c->p.n_qp, c->nxyz, c->stream) ? LISE_ECUDA
+                                                                                                : LISE_OK);
+  const int rc = start_procedure(c, c->t, c->dt);
+  if (rc != LISE_OK) {
+    c->sticky = rc;
+    return rc;
+  }
+  TRY(fetch_err(c));
+  c->ready = 1;
+  return LISE_OK;
+}
+
 int lise_step(lise_ctx* c, int n_steps, double dt) {
   if (!c || n_steps < 0) return LISE_EINVAL;
   if (c->sticky) return c->sticky;

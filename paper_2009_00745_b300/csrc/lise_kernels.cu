@@ -843,6 +843,19 @@ __global__ void k_eta_reduce(const double* part, int n_qp, int n_blocks, double 
   eta[q] = a3 * (s + c);
 }
 
+// Eq. kick: u -> e^{i chi} u, v -> e^{-i chi} v.
+__global__ void k_kick(const double2* src, double2* dst, const double* chi, long count, long nxyz) {
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long)gridDim.x * blockDim.x) {
+    const long site = i % nxyz;
+    const bool v = (i / nxyz) & 1;  // component index within the state
+    double sn, cs;
+    sincos(chi[site], &sn, &cs);
+    if (v) sn = -sn;
+    const double2 x = src[i];
+    dst[i] = make_double2(x.x * cs - x.y * sn, x.x * sn + x.y * cs);
+  }
+}
+
 __global__ void k_finite(const double2* x, long count, int* err) {
   int bad = 0;
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long)gridDim.x * blockDim.x) {
@@ -964,6 +977,15 @@ int launch_predict(const PointwiseArgs& a, cudaStream_t s) {
     k_predict<float><<<grid, nt, 0, s>>>(a);
   else
     k_predict<double><<<grid, nt, 0, s>>>(a);
+  return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}
+
+int launch_kick(const double2* src, double2* dst, const double* chi, int n_qp, long nxyz, cudaStream_t s) {
+  const long count = (long)n_qp * 2 * nxyz;
+  const int nt = 256;
+  const long blocks = std::min<long>((count + nt - 1) / nt, 148L * 16);
+  if (blocks <= 0) return 0;
+  k_kick<<<(unsigned)blocks, nt, 0, s>>>(src, dst, chi, count, nxyz);
   return cudaGetLastError() == cudaSuccess ? 0 : 3;
 }
 

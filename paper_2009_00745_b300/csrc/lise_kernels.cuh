@@ -154,6 +154,8 @@ int launch_energy_sites(const double* part_ekin, int n_groups, const double* n, 
 // pair_c of Eq. geff_3D for lattice constant a and kinetic coefficient alpha (meff = 1/alpha).
 double pairing_lattice_c(double a, double alpha);
 int launch_finite_check(const double2* x, long count, int* err, cudaStream_t s);
+// dst = Eq. kick of src: u e^{i chi}, v e^{-i chi} for n_qp states of nxyz sites (dst may alias src).
+int launch_kick(const double2* src, double2* dst, const double* chi, int n_qp, long nxyz, cudaStream_t s);
 // eta[q] = a^3 * sum over the pencil blocks of eta_part[q][block] (compensated).
 int launch_eta_reduce(const double* eta_part, int n_qp, int n_blocks, double a3, double* eta, cudaStream_t s);
 int pencil_blocks_x(int N, int mixed);

@@ -45,6 +45,7 @@ SIGNATURES = {
     "lise_create": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lise_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_double]),
     "lise_set_state_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_double]),
+    "lise_kick": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lise_step": (C.c_int, [C.c_void_p, C.c_int, C.c_double]),
     "lise_get_state": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lise_get_state_device": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -188,6 +189,13 @@ class Context:
         fn = load().lise_set_state_device if dev else load().lise_set_state
         _check(fn(self._h, ptr, float(t0), float(dt)), "lise_set_state")
         self.dt = float(dt)
+
+    def kick(self, chi):
+        """Eq. kick on the current state (u e^{i chi}, v e^{-i chi}), then a new series start."""
+        chi = np.ascontiguousarray(chi, dtype=np.float64)
+        if chi.size != self.N ** 3:
+            raise ValueError(f"chi has {chi.size} values, expected {self.N ** 3}")
+        _check(load().lise_kick(self._h, chi.ctypes.data), "lise_kick")
 
     def step(self, n_steps, dt=None):
         _check(load().lise_step(self._h, int(n_steps), float(self.dt if dt is None else dt)), "lise_step")

@@ -378,3 +378,31 @@ def test_graph_replay_matches_plain_launches(workload):
             out.append((ctx.state(), ctx.t))
     assert out[0][1] == out[1][1]
     assert np.array_equal(out[0][0], out[1][0])
+
+
+# ------------------------------------------------------------ boost (Eq. kick) ----
+
+def test_kick_parity():
+    # evolve, boost with a smooth periodic profile plus a lattice momentum, evolve again
+    w = W.ufg_plane_waves(16, 12, noise_eps=0.05)
+    N = w.nx
+    x = np.arange(N) * w.a
+    L_ = N * w.a
+    chi = (0.3 * np.sin(2 * np.pi * x / L_)[None, None, :] + 0.2 * np.cos(4 * np.pi * x / L_)[:, None, None]
+           + (2 * np.pi / L_) * x[None, :, None])
+    with L.Context.from_workload(w) as ctx:
+        with pytest.raises(L.LiseError) as e:
+            ctx.kick(chi)
+        assert e.value.status == L.ESTATE
+        ctx.set_state(w.initial_state(), 0.0, w.dt)
+        ctx.step(4)
+        ctx.kick(chi)
+        ctx.step(5)
+        got, t = ctx.state(), ctx.t
+    s = O.Solver(oracle_params(w))
+    s.set_state(w.initial_state(), 0.0, w.dt)
+    s.step(4)
+    s.kick(chi)
+    s.step(5)
+    assert t == pytest.approx(s.t, abs=1e-14)
+    assert rel(got, s.state()) < TOL_FP64_RUN

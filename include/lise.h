@@ -103,6 +103,14 @@ int lise_set_state(lise_ctx *c, const double *psi, double t0, double dt);
 /* Same with psi a device pointer (same layout) on the context's device. */
 int lise_set_state_device(lise_ctx *c, const double *psi_dev, double t0, double dt);
 
+/* Current density of Eq. j of the current state (spin factor 2):
+ * j(r) = 2 sum_k Im(v_k grad v_k^*), with the spectral first derivative
+ * F^-1[(ik) F] whose Nyquist coefficient is dropped (Sec. "Discretization").
+ * j_out: host, 3 N^3 doubles [component x, y, z][z][y][x].  FP64 on the device
+ * for both precisions; deterministic.  Synchronises.  Errors: LISE_ESTATE before
+ * set_state, LISE_EINVAL (null), LISE_ENOMEM, LISE_ECUDA. */
+int lise_currents(lise_ctx *c, double *j_out);
+
 /* Boost (Eq. kick, Sec. "External boosts and external potentials"): every state
  * of the current state y(t) becomes u -> e^{i chi(r)} u, v -> e^{-i chi(r)} v, and
  * the ABM history restarts through the series start at t with the same dt (as

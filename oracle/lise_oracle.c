@@ -429,6 +429,38 @@ int or_set_state(or_solver *s, const double complex *psi, double t0, double dt) 
   return 0;
 }
 
+void or_gradient(const or_params *p, const double complex *in, int axis, double complex *out) {
+  int nx = p->nx, ny = p->ny, nz = p->nz;
+  long nt = (long)nx * ny * nz;
+  int n_ax = axis == 0 ? nx : (axis == 1 ? ny : nz);
+  memcpy(out, in, sizeof(double complex) * nt);
+  or_fft3d(out, nx, ny, nz, -1);
+  for (int z = 0; z < nz; ++z)
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        int idx = axis == 0 ? x : (axis == 1 ? y : z);
+        /* odd derivative: the Nyquist coefficient is dropped */
+        double k = (n_ax % 2 == 0 && idx == n_ax / 2) ? 0.0 : or_kgrid(idx, n_ax, p->a);
+        out[((long)z * ny + y) * nx + x] *= I * k;
+      }
+  or_fft3d(out, nx, ny, nz, +1);
+}
+
+void or_currents(const or_params *p, const double complex *psi, double *j) {
+  long nt = (long)p->nx * p->ny * p->nz;
+  double complex *g = (double complex *)malloc(sizeof(double complex) * nt);
+  for (int a = 0; a < 3; ++a) {
+    double *ja = j + (long)a * nt;
+    for (long i = 0; i < nt; ++i) ja[i] = 0.0;
+    for (int q = 0; q < p->n_qp; ++q) {
+      const double complex *v = psi + ((long)q * 2 + 1) * nt;
+      or_gradient(p, v, a, g);
+      for (long i = 0; i < nt; ++i) ja[i] -= 2.0 * cimag(conj(v[i]) * g[i]);
+    }
+  }
+  free(g);
+}
+
 void or_kick(const or_params *p, double complex *psi, const double *chi) {
   long nt = (long)p->nx * p->ny * p->nz;
   for (int q = 0; q < p->n_qp; ++q) {

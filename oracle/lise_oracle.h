@@ -109,6 +109,12 @@ void or_destroy(or_solver *s);
 int or_set_state(or_solver *s, const double complex *psi, double t0, double dt);
 /* n_steps ABM steps of size dt (must equal the set_state dt). */
 int or_step(or_solver *s, int n_steps);
+/* First derivative along axis (0 = x, 1 = y, 2 = z): F^-1[(ik) F f] with the
+ * Nyquist coefficient set to zero (Sec. "Discretization", odd derivatives). */
+void or_gradient(const or_params *p, const double complex *in, int axis, double complex *out);
+/* Current density of Eq. j for the two-component states (spin factor 2):
+ * j(r) = 2 sum_k Im(v_k grad v_k^*) = -2 sum_k Im(v_k^* grad v_k); j[3][z][y][x] (x, y, z). */
+void or_currents(const or_params *p, const double complex *psi, double *j);
 /* Eq. kick (Sec. "External boosts and external potentials"): u -> e^{i chi(r)} u,
  * v -> e^{-i chi(r)} v for every state, chi real [z][y][x]. */
 void or_kick(const or_params *p, double complex *psi, const double *chi);

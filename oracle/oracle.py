@@ -36,6 +36,8 @@ def lib():
         L.or_apply_h.argtypes = [vp, vp, vp, vp, vp]
         L.or_rhs.argtypes = [vp, vp, d, vp]
         L.or_kick.argtypes = [vp, vp, vp]
+        L.or_gradient.argtypes = [vp, vp, i, vp]
+        L.or_currents.argtypes = [vp, vp, vp]
         L.or_solver_kick.argtypes = [vp, vp]
         L.or_solver_kick.restype = i
         L.or_create.argtypes = [vp]
@@ -193,6 +195,24 @@ def eta(p: Params, psi, hpsi):
     out = np.empty(p.n_qp)
     ps = p._c()
     lib().or_eta(C.byref(ps), psi.ctypes.data, hpsi.ctypes.data, out.ctypes.data)
+    return out
+
+
+def gradient(p: Params, f, axis):
+    """F^-1[(ik) F f] along axis 0 = x, 1 = y, 2 = z, Nyquist coefficient dropped."""
+    f = _c128(f, p.grid)
+    out = np.empty(p.grid, dtype=np.complex128)
+    ps = p._c()
+    lib().or_gradient(C.byref(ps), f.ctypes.data, int(axis), out.ctypes.data)
+    return out
+
+
+def currents(p: Params, psi):
+    """Current density of Eq. j (spin factor 2): j[3][z][y][x], components x, y, z."""
+    psi = _c128(psi, p.shape)
+    out = np.empty((3,) + p.grid)
+    ps = p._c()
+    lib().or_currents(C.byref(ps), psi.ctypes.data, out.ctypes.data)
     return out
 
 

@@ -726,6 +726,37 @@ int lise_set_state_device(lise_ctx* c, const double* psi_dev, double t0, double 
   return set_state_common(c, psi_dev, t0, dt, cudaMemcpyDeviceToDevice);
 }
 
+int lise_currents(lise_ctx* c, double* j_out) {
+  if (!c || !j_out) return LISE_EINVAL;
+  if (c->sticky) return c->sticky;
+  if (!c->ready) return LISE_ESTATE;
+  if (cudaSetDevice(c->device) != cudaSuccess) return LISE_ECUDA;
+  double d1h[64];
+  first_derivative_table(c->N, c->p.dx, d1h);
+  double* d1 = nullptr;
+  double* out = nullptr;
+  if (cudaMallocAsync((void**)&d1, c->N * sizeof(double), c->stream) != cudaSuccess ||
+      cudaMallocAsync((void**)&out, 3 * c->nxyz * sizeof(double), c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    if (d1) cudaFreeAsync(d1, c->stream);
+    return LISE_ENOMEM;
+  }
+  int rc = cu(cudaMemcpyAsync(d1, d1h, c->N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  // the density partial arrays [group][site] serve as the three current partials
+  if (rc == LISE_OK && launch_currents(c->slot[c->y0_slot], d1, c->N, c->p.n_qp, c->qg, c->part_n, c->part_nr,
+                                       c->part_ni, c->stream))
+    rc = LISE_ECUDA;
+  if (rc == LISE_OK &&
+      launch_sum_groups3(c->part_n, c->part_nr, c->part_ni, c->n_groups, c->nxyz, out, c->stream))
+    rc = LISE_ECUDA;
+  if (rc == LISE_OK)
+    rc = cu(cudaMemcpyAsync(j_out, out, 3 * c->nxyz * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  cudaFreeAsync(d1, c->stream);
+  cudaFreeAsync(out, c->stream);
+  if (rc == LISE_OK) rc = cu(cudaStreamSynchronize(c->stream));
+  return rc;
+}
+
 int lise_kick(lise_ctx* c, const double* chi) {
   if (!c || !chi) return LISE_EINVAL;
   if (c->sticky) return c->sticky;

@@ -843,6 +843,64 @@ __global__ void k_eta_reduce(const double* part, int n_qp, int n_blocks, double 
   eta[q] = a3 * (s + c);
 }
 
+// Current density partials (Eq. j): one block per x-line (y, z), one thread per x, one grid
+// row per state group; d/dx from the line in shared memory, d/dy and d/dz from global
+// (coalesced across the block).  Dense circulant sums in FP64: an observable, not the step.
+__global__ void k_currents(const double2* psi, const double* d1g, int N, int n_qp, int qg, double* jx, double* jy,
+                           double* jz) {
+  extern __shared__ double2 cur_smem[];
+  double2* line = cur_smem;                               // [N]
+  double* d1 = reinterpret_cast<double*>(line + N);       // [N]
+  const int x = threadIdx.x;
+  const int y = blockIdx.x % N, z = blockIdx.x / N;
+  const long nxyz = (long)N * N * N;
+  const long site = ((long)z * N + y) * N + x;
+  for (int i = x; i < N; i += blockDim.x) d1[i] = d1g[i];
+  const int g = blockIdx.y;
+  const int q0 = g * qg, q1 = min(n_qp, q0 + qg);
+  double sx = 0, sy = 0, sz = 0;
+  for (int q = q0; q < q1; ++q) {
+    const double2* v = psi + ((long)q * 2 + 1) * nxyz;  // v component of state q
+    __syncthreads();
+    line[x] = v[site];
+    __syncthreads();
+    const double2 vv = line[x];
+    double2 dx = make_double2(0, 0), dy = make_double2(0, 0), dz = make_double2(0, 0);
+    for (int k = 0; k < N; ++k) {
+      const double wx = d1[(x - k + N) % N], wy = d1[(y - k + N) % N], wz = d1[(z - k + N) % N];
+      const double2 ax = line[k];
+      const double2 ay = v[((long)z * N + k) * N + x];
+      const double2 az = v[((long)k * N + y) * N + x];
+      dx.x = fma(wx, ax.x, dx.x); dx.y = fma(wx, ax.y, dx.y);
+      dy.x = fma(wy, ay.x, dy.x); dy.y = fma(wy, ay.y, dy.y);
+      dz.x = fma(wz, az.x, dz.x); dz.y = fma(wz, az.y, dz.y);
+    }
+    // -2 Im(conj(v) d) = -2 (v.x d.y - v.y d.x)
+    sx -= 2.0 * (vv.x * dx.y - vv.y * dx.x);
+    sy -= 2.0 * (vv.x * dy.y - vv.y * dy.x);
+    sz -= 2.0 * (vv.x * dz.y - vv.y * dz.x);
+  }
+  const long o = (long)g * nxyz + site;
+  jx[o] = sx;
+  jy[o] = sy;
+  jz[o] = sz;
+}
+
+__global__ void k_sum_groups3(const double* jx, const double* jy, const double* jz, int n_groups, long nxyz,
+                              double* out) {
+  const long s = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nxyz) return;
+  double a = 0, b = 0, c = 0;
+  for (int g = 0; g < n_groups; ++g) {
+    a += jx[(long)g * nxyz + s];
+    b += jy[(long)g * nxyz + s];
+    c += jz[(long)g * nxyz + s];
+  }
+  out[s] = a;
+  out[nxyz + s] = b;
+  out[2 * nxyz + s] = c;
+}
+
 // Eq. kick: u -> e^{i chi} u, v -> e^{-i chi} v.
 __global__ void k_kick(const double2* src, double2* dst, const double* chi, long count, long nxyz) {
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long)gridDim.x * blockDim.x) {
@@ -978,6 +1036,35 @@ int launch_predict(const PointwiseArgs& a, cudaStream_t s) {
   else
     k_predict<double><<<grid, nt, 0, s>>>(a);
   return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}
+
+int launch_currents(const double2* psi, const double* d1, int N, int n_qp, int qg, double* jx, double* jy,
+                    double* jz, cudaStream_t s) {
+  const int n_groups = (n_qp + qg - 1) / qg;
+  dim3 grid((unsigned)(N * N), (unsigned)n_groups);
+  const size_t smem = (size_t)N * (sizeof(double2) + sizeof(double));
+  k_currents<<<grid, N, smem, s>>>(psi, d1, N, n_qp, qg, jx, jy, jz);
+  return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}
+
+int launch_sum_groups3(const double* jx, const double* jy, const double* jz, int n_groups, long nxyz, double* out,
+                       cudaStream_t s) {
+  const int nt = 256;
+  k_sum_groups3<<<(unsigned)((nxyz + nt - 1) / nt), nt, 0, s>>>(jx, jy, jz, n_groups, nxyz, out);
+  return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}
+
+void first_derivative_table(int N, double a, double* d1) {
+  const long double PI = 3.141592653589793238462643383279502884L;
+  for (int m = 0; m < N; ++m) {
+    long double acc = 0;
+    for (int j = 0; j < N; ++j) {
+      if (N % 2 == 0 && j == N / 2) continue;  // the Nyquist coefficient of an odd derivative
+      const long double kj = 2.0L * PI * (long double)(j < N / 2 ? j : j - N) / ((long double)N * a);
+      acc += -kj * sinl(kj * (long double)m * a);  // Re(i k e^{i k m a})
+    }
+    d1[m] = (double)(acc / N);
+  }
 }
 
 int launch_kick(const double2* src, double2* dst, const double* chi, int n_qp, long nxyz, cudaStream_t s) {

@@ -154,6 +154,15 @@ int launch_energy_sites(const double* part_ekin, int n_groups, const double* n, 
 // pair_c of Eq. geff_3D for lattice constant a and kinetic coefficient alpha (meff = 1/alpha).
 double pairing_lattice_c(double a, double alpha);
 int launch_finite_check(const double2* x, long count, int* err, cudaStream_t s);
+// Current density of Eq. j: per state group g, jx/jy/jz partial sums [g][site] of
+// -2 Im(conj(v) D1 v) along each axis; d1 = first-derivative circulant (N entries,
+// Nyquist coefficient dropped).  Then out[3][site] = sums over groups in group order.
+int launch_currents(const double2* psi, const double* d1, int N, int n_qp, int qg, double* jx, double* jy,
+                    double* jz, cudaStream_t s);
+int launch_sum_groups3(const double* jx, const double* jy, const double* jz, int n_groups, long nxyz, double* out,
+                       cudaStream_t s);
+// d1[m] = (1/N) sum_j (i k_j) e^{i k_j m a} over j != N/2 (real), m = 0..N-1.
+void first_derivative_table(int N, double a, double* d1);
 // dst = Eq. kick of src: u e^{i chi}, v e^{-i chi} for n_qp states of nxyz sites (dst may alias src).
 int launch_kick(const double2* src, double2* dst, const double* chi, int n_qp, long nxyz, cudaStream_t s);
 // eta[q] = a^3 * sum over the pencil blocks of eta_part[q][block] (compensated).

@@ -46,6 +46,7 @@ SIGNATURES = {
     "lise_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_double]),
     "lise_set_state_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_double]),
     "lise_kick": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "lise_currents": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lise_step": (C.c_int, [C.c_void_p, C.c_int, C.c_double]),
     "lise_get_state": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lise_get_state_device": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -189,6 +190,12 @@ class Context:
         fn = load().lise_set_state_device if dev else load().lise_set_state
         _check(fn(self._h, ptr, float(t0), float(dt)), "lise_set_state")
         self.dt = float(dt)
+
+    def currents(self):
+        """Current density of Eq. j of the current state: array [3][z][y][x] (x, y, z components)."""
+        out = np.empty((3, self.N, self.N, self.N))
+        _check(load().lise_currents(self._h, out.ctypes.data), "lise_currents")
+        return out
 
     def kick(self, chi):
         """Eq. kick on the current state (u e^{i chi}, v e^{-i chi}), then a new series start."""

@@ -406,3 +406,20 @@ def test_kick_parity():
     s.step(5)
     assert t == pytest.approx(s.t, abs=1e-14)
     assert rel(got, s.state()) < TOL_FP64_RUN
+
+
+# ------------------------------------------------------------ current density (Eq. j) ----
+
+@pytest.mark.parametrize("N,n_qp,precision", [(16, 9, "fp64"), (12, 5, "fp64"), (32, 5, "mixed")])
+def test_currents_parity(N, n_qp, precision):
+    psi = random_state(N, n_qp, seed=21 + N)
+    kw = dict(a=0.9, alpha=1.0, beta=-0.5, mu=0.3, g=0.7)
+    with L.Context(N, n_qp, precision=precision, **kw) as ctx:
+        with pytest.raises(L.LiseError) as e:
+            ctx.currents()
+        assert e.value.status == L.ESTATE
+        ctx.set_state(psi, 0.0, 0.005)
+        y = ctx.state()          # the state after the 3-step series start
+        j = ctx.currents()
+    ref = O.currents(O.Params(N, N, N, n_qp=n_qp, **kw), y)
+    assert rel(j, ref) < 1e-12

@@ -85,6 +85,9 @@ typedef struct {
                                K = 2.442749607806335; 0: g_eff = g0(r).  Delta = -g_eff nu; with a
                                density-dependent g_eff, U gains (d g_eff/dn) |nu|^2 and
                                E_pair = g_eff(n) |nu|^2 (Eq. pairing) */
+  int renormalize;          /* 1: at the end of every ABM step each state is scaled to unit norm,
+                               a^3 sum_r (|u|^2 + |v|^2) = 1, before its y' is formed (the optional
+                               renormalisation the paper describes after Eq. sp_en); 0: off */
 } lise_params;
 
 /* Device bytes lise_create would allocate for these parameters (0 if invalid). */

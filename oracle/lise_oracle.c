@@ -518,6 +518,19 @@ void or_abm_final(long ns, const double complex *p, const double complex *c, dou
 }
 
 /* One step of Eqs. p, m, c, y with f(t, y) = -i H[y](t) y. */
+/* psi_k <- psi_k / sqrt(a^3 sum_r (|u_k|^2 + |v_k|^2)) for every state */
+static void normalize_states(const or_params *p, double complex *psi) {
+  long nt = (long)p->nx * p->ny * p->nz;
+  double a3 = p->a * p->a * p->a;
+  for (int q = 0; q < p->n_qp; ++q) {
+    double complex *x = psi + (long)q * 2 * nt;
+    double s = 0, c = 0;
+    for (long i = 0; i < 2 * nt; ++i) neumaier_add(&s, &c, creal(x[i]) * creal(x[i]) + cimag(x[i]) * cimag(x[i]));
+    double f = 1.0 / sqrt(a3 * (s + c));
+    for (long i = 0; i < 2 * nt; ++i) x[i] *= f;
+  }
+}
+
 static void abm_step(or_solver *s) {
   long ns = s->ns;
   double h = s->dt;
@@ -530,6 +543,7 @@ static void abm_step(or_solver *s) {
   or_abm_corrector(ns, h, yn, ynm1, s->mp, dn, dn1, dn2, s->c);
   /* y_{n+1} is stored in the y_{n-1} slot, which the corrector no longer needs */
   or_abm_final(ns, s->pr, s->c, ynm1, s->pc);
+  if (s->p.renormalize) normalize_states(&s->p, ynm1);
   /* y'_{n+1} = f(t_{n+1}, y_{n+1}) into the y'_{n-3} slot, then rotate */
   or_rhs(&s->p, ynm1, tn1, dn3);
   s->y0 = ynm1;

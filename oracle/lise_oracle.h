@@ -49,6 +49,8 @@ typedef struct {
   double pair_alpha;       /* Eq. g0: g0(r) = g (1 - pair_alpha n(r) / pair_n0); 0 = constant g */
   double pair_n0;
   int pair_lattice;        /* 1: Eq. geff_3D, 1/g_eff = 1/g0(r) - meff (pi/a) K / (4 pi^2 hbar^2), meff = 1/alpha */
+  int renormalize;         /* 1: at the end of every ABM step each state is scaled to a^3 sum(|u|^2+|v|^2) = 1
+                              (the renormalisation remark that follows Eq. sp_en), before its y' is formed */
 } or_params;
 
 /* K of Eq. geff_3D (the value printed with it). */

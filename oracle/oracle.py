@@ -70,7 +70,8 @@ class _Params(C.Structure):
                 ("n_qp", C.c_int), ("alpha", C.c_double), ("beta", C.c_double),
                 ("mu", C.c_double), ("g", C.c_double), ("v_static", C.c_void_p),
                 ("drive_A", C.c_double), ("drive_Omega", C.c_double), ("remove_phase", C.c_int),
-                ("pair_alpha", C.c_double), ("pair_n0", C.c_double), ("pair_lattice", C.c_int)]
+                ("pair_alpha", C.c_double), ("pair_n0", C.c_double), ("pair_lattice", C.c_int),
+                ("renormalize", C.c_int)]
 
 
 class Params:
@@ -78,19 +79,21 @@ class Params:
 
     def __init__(self, nx, ny, nz, a=1.0, n_qp=1, alpha=1.0, beta=0.0, mu=0.0, g=0.0,
                  v_static=None, drive_A=0.0, drive_Omega=0.0, remove_phase=False, pair_alpha=0.0,
-                 pair_n0=1.0, pair_lattice=False):
+                 pair_n0=1.0, pair_lattice=False, renormalize=False):
         self.nx, self.ny, self.nz, self.a, self.n_qp = int(nx), int(ny), int(nz), float(a), int(n_qp)
         self.alpha, self.beta, self.mu, self.g = float(alpha), float(beta), float(mu), float(g)
         self.v_static = None if v_static is None else np.ascontiguousarray(v_static, dtype=np.float64).reshape(nz, ny, nx)
         self.drive_A, self.drive_Omega = float(drive_A), float(drive_Omega)
         self.remove_phase = bool(remove_phase)
         self.pair_alpha, self.pair_n0, self.pair_lattice = float(pair_alpha), float(pair_n0), bool(pair_lattice)
+        self.renormalize = bool(renormalize)
 
     def with_(self, **kw):
         d = dict(nx=self.nx, ny=self.ny, nz=self.nz, a=self.a, n_qp=self.n_qp, alpha=self.alpha,
                  beta=self.beta, mu=self.mu, g=self.g, v_static=self.v_static,
                  drive_A=self.drive_A, drive_Omega=self.drive_Omega, remove_phase=self.remove_phase,
-                 pair_alpha=self.pair_alpha, pair_n0=self.pair_n0, pair_lattice=self.pair_lattice)
+                 pair_alpha=self.pair_alpha, pair_n0=self.pair_n0, pair_lattice=self.pair_lattice,
+                 renormalize=self.renormalize)
         d.update(kw)
         return Params(**d)
 
@@ -98,7 +101,7 @@ class Params:
         s = _Params(self.nx, self.ny, self.nz, self.a, self.n_qp, self.alpha, self.beta, self.mu,
                     self.g, None if self.v_static is None else self.v_static.ctypes.data,
                     self.drive_A, self.drive_Omega, int(self.remove_phase), self.pair_alpha,
-                    self.pair_n0, int(self.pair_lattice))
+                    self.pair_n0, int(self.pair_lattice), int(self.renormalize))
         return s
 
     @property

@@ -68,6 +68,9 @@ struct lise_ctx {
   double* eta = nullptr;
   double* eta_part = nullptr;
   int n_blocks_x = 0;
+  // per-step renormalisation: norm partials [state][kNormBlocks] and the scale per state
+  double* norm_part = nullptr;
+  double* norm_scale = nullptr;
   // CUDA graphs of kGraphSteps ABM steps, one per history configuration (y-slot
   // parity x position of the derivative ring), replayed by lise_step
   cudaGraphExec_t graph[2][4] = {};
@@ -108,6 +111,8 @@ void choose_groups(int N, int n_qp, int mixed, int* qg, int* n_groups) {
   *n_groups = (n_qp + q - 1) / q;
 }
 
+constexpr int kNormBlocks = 32;  // blocks per state of the norm reduction (renormalisation)
+
 struct Footprint {
   size_t state, txy, partials, small, total;
 };
@@ -128,6 +133,7 @@ Footprint footprint(const lise_params* p) {
                             sizeof(double) + 2 * sizeof(double)) +
             3 * (size_t)N * sizeof(double2) + 256;
   if (p->remove_phase) f.small += (size_t)p->n_qp * (1 + pencil_blocks_x((int)N, p->precision == LISE_MIXED)) * sizeof(double);
+  if (p->renormalize) f.small += (size_t)p->n_qp * (1 + kNormBlocks) * sizeof(double);
   f.total = f.state + f.txy + f.partials + f.small;
   return f;
 }
@@ -404,6 +410,24 @@ int abm_step(lise_ctx* c) {
   a.ynew = ynm1;
   a.dens = 1;
   TRY(run_pencils(c, M_CORRECT, a));
+  if (c->p.renormalize) {
+    // end of the step: each state of y_{n+1} to unit norm, and the densities of the scaled state
+    const double a3 = c->p.dx * c->p.dx * c->p.dx;
+    PointwiseArgs w;
+    std::memset(&w, 0, sizeof(w));
+    w.part_n = c->part_n;
+    w.part_nr = c->part_nr;
+    w.part_ni = c->part_ni;
+    w.n_qp = c->p.n_qp;
+    w.qg = c->qg;
+    w.nxyz = c->nxyz;
+    TRY(timed(c, LISE_KC_POINTWISE, [&] {
+      return launch_norms(ynm1, c->p.n_qp, c->nxyz, a3, kNormBlocks, c->norm_part, c->norm_scale, c->stream) ||
+                     launch_scale_density(ynm1, c->norm_scale, w, c->stream)
+                 ? LISE_ECUDA
+                 : LISE_OK;
+    }));
+  }
   TRY(run_reduce(c, 1, nullptr, nullptr, true, t1));
   // RHS #2 on y_{n+1}: y'_{n+1} into the y'_{n-3} slot, then Eq. p and Eq. m of step n+2
   TRY(run_planes(c, ynm1));
@@ -504,7 +528,7 @@ int graph_steps(lise_ctx* c) {
 
 void free_ctx(lise_ctx* c) {
   drop_graphs(c);
-  void* ptrs[] = {c->drive_dev, c->eta, c->eta_part, c->slot[0], c->slot[1], c->D[0], c->D[1], c->D[2], c->D[3], c->M, c->RPC, c->Q, c->TXY,
+  void* ptrs[] = {c->norm_part, c->norm_scale, c->drive_dev, c->eta, c->eta_part, c->slot[0], c->slot[1], c->D[0], c->D[1], c->D[2], c->D[3], c->M, c->RPC, c->Q, c->TXY,
                   c->part_n, c->part_nr, c->part_ni, c->dn[0], c->dn[1], c->dnu[0], c->dnu[1], c->W,
                   c->Dl, c->v_static, c->tw, c->hxy, c->hz, c->ozb, c->e_site, c->err};
   // stream-ordered frees: no device-wide synchronisation (work of other contexts,
@@ -641,6 +665,10 @@ int lise_create(const lise_params* p, lise_ctx** out) {
     alloc((void**)&c->ozb, ozt.size() * sizeof(uint32_t));
   }
   c->n_blocks_x = pencil_blocks_x(c->N, c->mixed);
+  if (p->renormalize) {
+    alloc((void**)&c->norm_part, (size_t)p->n_qp * kNormBlocks * sizeof(double));
+    alloc((void**)&c->norm_scale, (size_t)p->n_qp * sizeof(double));
+  }
   if (p->remove_phase) {
     alloc((void**)&c->eta, (size_t)p->n_qp * sizeof(double));
     alloc((void**)&c->eta_part, (size_t)p->n_qp * c->n_blocks_x * sizeof(double));

@@ -901,6 +901,54 @@ __global__ void k_sum_groups3(const double* jx, const double* jy, const double* 
   out[2 * nxyz + s] = c;
 }
 
+// Norm partials: block b of state q sums |x|^2 over its slice of the state's 2 nxyz
+// elements (strided per thread, then a fixed-order tree in shared memory).
+__global__ void k_norm_part(const double2* y, long nxyz, int nb, double* part) {
+  __shared__ double red[256];
+  const int q = blockIdx.y, b = blockIdx.x;
+  const long n = 2 * nxyz, chunk = (n + nb - 1) / nb;
+  const long i0 = (long)b * chunk, i1 = min(n, i0 + chunk);
+  const double2* x = y + (long)q * n;
+  double s = 0.0;
+  for (long i = i0 + threadIdx.x; i < i1; i += blockDim.x) s = fma(x[i].x, x[i].x, fma(x[i].y, x[i].y, s));
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[(long)q * nb + b] = red[0];
+}
+
+__global__ void k_norm_scale(const double* part, int n_qp, int nb, double a3, double* scale) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n_qp) return;
+  double s = 0, c = 0;
+  for (int b = 0; b < nb; ++b) neumaier(s, c, part[(long)q * nb + b]);
+  scale[q] = 1.0 / sqrt(a3 * (s + c));
+}
+
+// y *= scale per state (in place) and the density partials of the scaled state.
+__global__ void k_scale_density(double2* y, const double* scale, PointwiseArgs a) {
+  const long s = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= a.nxyz) return;
+  const int g = blockIdx.y;
+  const int q_begin = g * a.qg, q_end = min(a.n_qp, q_begin + a.qg);
+  double sn = 0, sr = 0, si = 0;
+  for (int q = q_begin; q < q_end; ++q) {
+    const long i = (long)(2 * q) * a.nxyz + s;
+    const double f = scale[q];
+    const double2 u = dscale(y[i], f), v = dscale(y[i + a.nxyz], f);
+    y[i] = u;
+    y[i + a.nxyz] = v;
+    dens_acc(u, v, sn, sr, si);
+  }
+  const long o = (long)g * a.nxyz + s;
+  a.part_n[o] = 2.0 * sn;
+  a.part_nr[o] = sr;
+  a.part_ni[o] = si;
+}
+
 // Eq. kick: u -> e^{i chi} u, v -> e^{-i chi} v.
 __global__ void k_kick(const double2* src, double2* dst, const double* chi, long count, long nxyz) {
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long)gridDim.x * blockDim.x) {
@@ -1035,6 +1083,21 @@ int launch_predict(const PointwiseArgs& a, cudaStream_t s) {
     k_predict<float><<<grid, nt, 0, s>>>(a);
   else
     k_predict<double><<<grid, nt, 0, s>>>(a);
+  return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}
+
+int launch_norms(const double2* y, int n_qp, long nxyz, double a3, int nb, double* part, double* scale,
+                 cudaStream_t s) {
+  k_norm_part<<<dim3((unsigned)nb, (unsigned)n_qp), 256, 0, s>>>(y, nxyz, nb, part);
+  if (cudaGetLastError() != cudaSuccess) return 3;
+  k_norm_scale<<<(unsigned)((n_qp + 127) / 128), 128, 0, s>>>(part, n_qp, nb, a3, scale);
+  return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}
+
+int launch_scale_density(double2* y, const double* scale, const PointwiseArgs& a, cudaStream_t s) {
+  const int nt = 256;
+  dim3 grid((unsigned)((a.nxyz + nt - 1) / nt), (a.n_qp + a.qg - 1) / a.qg);
+  k_scale_density<<<grid, nt, 0, s>>>(y, scale, a);
   return cudaGetLastError() == cudaSuccess ? 0 : 3;
 }
 

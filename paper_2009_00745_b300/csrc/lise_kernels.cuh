@@ -154,6 +154,12 @@ int launch_energy_sites(const double* part_ekin, int n_groups, const double* n, 
 // pair_c of Eq. geff_3D for lattice constant a and kinetic coefficient alpha (meff = 1/alpha).
 double pairing_lattice_c(double a, double alpha);
 int launch_finite_check(const double2* x, long count, int* err, cudaStream_t s);
+// Per-step renormalisation: norm partials [q][block] of a^3 sum(|u|^2 + |v|^2) over nb
+// blocks per state, then scale[q] = 1 / sqrt(sum over blocks in order); then y *= scale
+// in place with the density partials of the scaled state (groups of qg states).
+int launch_norms(const double2* y, int n_qp, long nxyz, double a3, int nb, double* part, double* scale,
+                 cudaStream_t s);
+int launch_scale_density(double2* y, const double* scale, const PointwiseArgs& a, cudaStream_t s);
 // Current density of Eq. j: per state group g, jx/jy/jz partial sums [g][site] of
 // -2 Im(conj(v) D1 v) along each axis; d1 = first-derivative circulant (N entries,
 // Nyquist coefficient dropped).  Then out[3][site] = sums over groups in group order.

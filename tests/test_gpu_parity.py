@@ -423,3 +423,21 @@ def test_currents_parity(N, n_qp, precision):
         j = ctx.currents()
     ref = O.currents(O.Params(N, N, N, n_qp=n_qp, **kw), y)
     assert rel(j, ref) < 1e-12
+
+
+# ------------------------------------------------------------ per-step renormalisation ----
+
+@pytest.mark.parametrize("N", [16, 12])
+def test_renormalize_parity(N):
+    w = W.ufg_plane_waves(N, 20, noise_eps=0.3)
+    w.dt = 0.02  # the plain ABM norm drift is visible at this step
+    with L.Context.from_workload(w, renormalize=True) as ctx:
+        ctx.set_state(w.initial_state(), 0.0, w.dt)
+        ctx.step(10)
+        got = ctx.state()
+    norms = np.sum(np.abs(got) ** 2, axis=(1, 2, 3, 4)) * w.a ** 3
+    assert np.max(np.abs(norms - 1)) < 1e-14
+    s = O.Solver(oracle_params(w, renormalize=True))
+    s.set_state(w.initial_state(), 0.0, w.dt)
+    s.step(10)
+    assert rel(got, s.state()) < TOL_FP64_RUN

@@ -599,6 +599,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if not mixed else "f64+c64",
             "data": "synthetic", "config": config_of(w, args), "roofline": roof, "cpu_baseline": cpu,
+            "tuned": {"pencils_states_per_batch": L.pencil_batch(w.nx, w.precision)},
             "e2e": e2e, "clocks": clocks, "gpu_launches": gpu_launches,
             "energy_after_timed_steps": E_dev, "particle_number": N_dev,
         }

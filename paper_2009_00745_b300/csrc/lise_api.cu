@@ -20,6 +20,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -702,6 +703,88 @@ int lise_create(const lise_params* p, lise_ctx** out) {
   return LISE_OK;
 }
 
+// Pencil batch autotuning (once per process for each lattice size and precision): time the
+// two pencils launches of an ABM step for every compiled batch size on this context's
+// buffers, before the series start overwrites them, and keep the fastest.  Needs the
+// input state in slot 0; uses the other arrays as scratch.  Results do not depend on it.
+static std::mutex g_tune_mu;
+
+static int tune_pencils(lise_ctx* c, double t0) {
+  if (pencil_qb_get(c->N, c->mixed)) return LISE_OK;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  if (pencil_qb_get(c->N, c->mixed)) return LISE_OK;
+  const int cands[2] = {2, 4};
+  int n_valid = 0;
+  for (int qb : cands) n_valid += pencil_qb_valid(c->N, c->mixed, qb) ? 1 : 0;
+  if (n_valid < 2) {  // nothing to choose
+    for (int qb : cands)
+      if (pencil_qb_valid(c->N, c->mixed, qb)) pencil_qb_set(c->N, c->mixed, qb);
+    return LISE_OK;
+  }
+  // valid potentials and T_xy of the input for representative launches
+  TRY(run_density(c, c->slot[0]));
+  TRY(run_reduce(c, 0, nullptr, nullptr, true, t0));
+  TRY(run_planes(c, c->slot[0]));
+  TRY(cu(cudaMemsetAsync(c->M, 0, (size_t)c->ns * (c->mixed ? sizeof(float2) : sizeof(double2)), c->stream)));
+  PencilArgs a = pencil_base(c);  // corrector on m = 0: y_{n+1}, p - c into free arrays
+  a.xr = c->M;
+  a.h = c->dt != 0.0 ? c->dt : 0.005;
+  a.q = c->Q;
+  a.r = c->R;
+  a.pc = c->PC;
+  a.ynew = c->slot[1];
+  a.dens = 1;
+  PencilArgs b = pencil_base(c);  // derivative (and, FP64, predictor) on the input
+  b.x = c->slot[0];
+  b.h = a.h;
+  b.y0 = c->slot[1];
+  b.d0 = c->D[0];
+  b.d1 = c->D[1];
+  b.d2 = c->D[2];
+  b.dslot = c->D[3];
+  b.pc = c->PC;
+  b.q = c->Q;
+  b.r = c->R;
+  b.m = c->M;
+  b.dens = 1;
+  const int mode_b = c->mixed ? M_RHS : M_DERIV_PREDICT;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return LISE_ECUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return LISE_ECUDA;
+  }
+  int best = 0, rc = LISE_OK;
+  float best_ms = 0.f;
+  for (int qb : cands) {
+    auto run = [&] {
+      return launch_pencils(c->N, c->mixed, M_CORRECT, a, c->stream, qb) ||
+             launch_pencils(c->N, c->mixed, mode_b, b, c->stream, qb);
+    };
+    if (run()) {  // warm-up (and the one-time launch set-up)
+      rc = LISE_ECUDA;
+      break;
+    }
+    cudaEventRecord(e0, c->stream);
+    for (int k = 0; k < 3; ++k)
+      if (run()) rc = LISE_ECUDA;
+    cudaEventRecord(e1, c->stream);
+    float ms = 0.f;
+    if (rc != LISE_OK || cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      rc = LISE_ECUDA;
+      break;
+    }
+    if (!best || ms < best_ms) {
+      best = qb;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc == LISE_OK && best) pencil_qb_set(c->N, c->mixed, best);
+  return rc;
+}
+
 static int set_state_common(lise_ctx* c, const double* psi, double t0, double dt, cudaMemcpyKind kind) {
   if (!c || !psi || !(dt != 0.0) || !std::isfinite(dt) || !std::isfinite(t0)) return LISE_EINVAL;
   if (c->sticky) return c->sticky;
@@ -719,6 +802,7 @@ static int set_state_common(lise_ctx* c, const double* psi, double t0, double dt
     return LISE_ENONFINITE;
   }
   if (dt != c->dt) drop_graphs(c);  // the step is baked into the captured kernels
+  TRY(tune_pencils(c, t0));
   int rc = start_procedure(c, t0, dt);
   if (rc != LISE_OK) {
     c->sticky = rc;
@@ -752,6 +836,20 @@ int lise_set_state_enqueue(lise_ctx* c, const double* psi, double t0, double dt)
 
 int lise_set_state_device(lise_ctx* c, const double* psi_dev, double t0, double dt) {
   return set_state_common(c, psi_dev, t0, dt, cudaMemcpyDeviceToDevice);
+}
+
+int lise_pencil_batch(int N, int precision) {
+  if (!supported_n(N) || (precision != LISE_FP64 && precision != LISE_MIXED)) return 0;
+  return pencil_qb(N, precision == LISE_MIXED);
+}
+
+int lise_set_pencil_batch(int N, int precision, int qb) {
+  if (!supported_n(N) || (precision != LISE_FP64 && precision != LISE_MIXED)) return LISE_EINVAL;
+  const int mixed = precision == LISE_MIXED;
+  if (qb != 0 && !pencil_qb_valid(N, mixed, qb)) return LISE_EINVAL;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  pencil_qb_set(N, mixed, qb);
+  return LISE_OK;
 }
 
 int lise_currents(lise_ctx* c, double* j_out) {

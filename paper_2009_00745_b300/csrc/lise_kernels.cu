@@ -1,6 +1,7 @@
 // lise_kernels.cu -- device kernels of the two-component TDSLDA step and their
 // launchers.  See lise_kernels.cuh for the operator split and the modes.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -981,7 +982,10 @@ bool supported_n(int N) {
 // FP64 tensor-core path: 4-wide tiles (128-thread blocks, 4 resident per SM), so that
 // blocks in their digit/tensor phase overlap others in their FP64 epilogue
 int pencil_tx(int N, int mixed) { return (ozaki_path(N, mixed) || N % 8 != 0) ? 4 : 8; }
-int pencil_qb(int N, int mixed) { return (N >= 40 || (N >= 32 && (mixed || ozaki_path(N, mixed)))) ? 2 : 4; }
+int pencil_qb(int N, int mixed) {
+  const int t = pencil_qb_get(N, mixed);
+  return t ? t : ((N >= 40 || (N >= 32 && (mixed || ozaki_path(N, mixed)))) ? 2 : 4);
+}
 
 template <int N>
 static int planes_oz_n(const PlanesArgs& a, cudaStream_t s) {
@@ -1014,13 +1018,38 @@ static int planes_n(const PlanesArgs& a, cudaStream_t s) {
   return cudaGetLastError() == cudaSuccess ? 0 : 3;
 }
 
-template <typename R, int N, int MODE>
-static int pencils_nm(const PencilArgs& a, cudaStream_t s) {
+// ----------------------------------------------------- pencil batch autotune --
+// States per batch (QB) of the pencils kernel: a default per lattice and precision, or
+// the value an autotuning pass measured fastest (lise_api.cu: tune_pencils).  QB only
+// changes how a block walks its states (the per-thread density sums and every per-state
+// operation keep their order), so results are bitwise identical for every QB.
+template <typename R, int N>
+constexpr int qb_default() {
+  // fewer states per batch at large N (registers), for the FP32 path from N = 32 (staging)
+  // and for the FP64 tensor-core path from N = 32 (registers for four resident blocks)
+  return (N >= 40 || (sizeof(R) == 4 && N >= 32) || (pencil_oz<R, N>() && N >= 32)) ? 2 : 4;
+}
+template <typename R, int N, int QB>
+constexpr bool qb_fits() {
+  using T = typename Cx<R>::T;
+  constexpr int TX = (pencil_oz<R, N>() || N % 8 != 0) ? 4 : 8;
+  return pencil_smem_bytes<T, N, TX, QB>() <= 227 * 1024;
+}
+
+static std::atomic<int> g_qb_tuned[2][65];  // 0: not tuned
+
+int pencil_qb_get(int N, int mixed) {
+  if (N < 0 || N > 64) return 0;
+  return g_qb_tuned[mixed ? 1 : 0][N].load(std::memory_order_relaxed);
+}
+void pencil_qb_set(int N, int mixed, int qb) {
+  if (N >= 0 && N <= 64) g_qb_tuned[mixed ? 1 : 0][N].store(qb, std::memory_order_relaxed);
+}
+
+template <typename R, int N, int MODE, int QB>
+static int pencils_nmq(const PencilArgs& a, cudaStream_t s) {
   using T = typename Cx<R>::T;
   constexpr int TX = (pencil_oz<R, N>() || N % 8 != 0) ? 4 : 8;  // = pencil_tx
-  // states per batch: fewer at large N (registers) and for the FP32 path from N = 32 (staging)
-  // (the FP64 tensor-core path from N = 32 too: registers for four resident blocks)
-  constexpr int QB = (N >= 40 || (sizeof(R) == 4 && N >= 32) || (pencil_oz<R, N>() && N >= 32)) ? 2 : 4;
   const size_t smem = (size_t)pencil_smem_bytes<T, N, TX, QB>();
   auto kern = k_pencils<R, N, TX, QB, MODE>;
   if (pencil_oz<R, N>() && !a.ozb) return 1;
@@ -1033,18 +1062,39 @@ static int pencils_nm(const PencilArgs& a, cudaStream_t s) {
   return cudaGetLastError() == cudaSuccess ? 0 : 3;
 }
 
+// the step's modes have QB = 2 and QB = 4 variants (where they fit); the others use the default
+template <typename R, int N, int MODE>
+static int pencils_nm(const PencilArgs& a, cudaStream_t s, int qb) {
+  constexpr bool kTunable = MODE == M_RHS || MODE == M_CORRECT || MODE == M_DERIV_PREDICT;
+  if constexpr (kTunable) {
+    if (qb == 0) qb = pencil_qb_get(N, sizeof(R) == 4);
+    if constexpr (qb_fits<R, N, 2>())
+      if (qb == 2) return pencils_nmq<R, N, MODE, 2>(a, s);
+    if constexpr (qb_fits<R, N, 4>())
+      if (qb == 4) return pencils_nmq<R, N, MODE, 4>(a, s);
+  }
+  return pencils_nmq<R, N, MODE, qb_default<R, N>()>(a, s);
+}
+
 template <typename R, int N>
-static int pencils_n(int mode, const PencilArgs& a, cudaStream_t s) {
+static int pencils_n(int mode, const PencilArgs& a, cudaStream_t s, int qb) {
   switch (mode) {
-    case M_RHS: return pencils_nm<R, N, M_RHS>(a, s);
-    case M_TAYLOR_FIRST: return pencils_nm<R, N, M_TAYLOR_FIRST>(a, s);
-    case M_TAYLOR: return pencils_nm<R, N, M_TAYLOR>(a, s);
-    case M_CORRECT: return pencils_nm<R, N, M_CORRECT>(a, s);
-    case M_DERIV_PREDICT: return pencils_nm<R, N, M_DERIV_PREDICT>(a, s);
-    case M_ENERGY: return pencils_nm<R, N, M_ENERGY>(a, s);
-    case M_ETA: return pencils_nm<R, N, M_ETA>(a, s);
+    case M_RHS: return pencils_nm<R, N, M_RHS>(a, s, qb);
+    case M_TAYLOR_FIRST: return pencils_nm<R, N, M_TAYLOR_FIRST>(a, s, qb);
+    case M_TAYLOR: return pencils_nm<R, N, M_TAYLOR>(a, s, qb);
+    case M_CORRECT: return pencils_nm<R, N, M_CORRECT>(a, s, qb);
+    case M_DERIV_PREDICT: return pencils_nm<R, N, M_DERIV_PREDICT>(a, s, qb);
+    case M_ENERGY: return pencils_nm<R, N, M_ENERGY>(a, s, qb);
+    case M_ETA: return pencils_nm<R, N, M_ETA>(a, s, qb);
     default: return 1;
   }
+}
+
+template <typename R, int N>
+static bool qb_valid_n(int qb) {
+  if (qb == 2) return qb_fits<R, N, 2>();
+  if (qb == 4) return qb_fits<R, N, 4>();
+  return false;
 }
 
 #define LISE_FOR_N(X) X(8) X(12) X(16) X(20) X(24) X(32) X(40) X(48) X(64)
@@ -1059,13 +1109,23 @@ int launch_planes(int N, int mixed, const PlanesArgs& a, cudaStream_t s) {
   }
 }
 
-int launch_pencils(int N, int mixed, int mode, const PencilArgs& a, cudaStream_t s) {
+int launch_pencils(int N, int mixed, int mode, const PencilArgs& a, cudaStream_t s, int qb) {
   switch (N) {
 #define CASE(n) \
-  case n: return mixed ? pencils_n<float, n>(mode, a, s) : pencils_n<double, n>(mode, a, s);
+  case n: return mixed ? pencils_n<float, n>(mode, a, s, qb) : pencils_n<double, n>(mode, a, s, qb);
     LISE_FOR_N(CASE)
 #undef CASE
     default: return 1;
+  }
+}
+
+bool pencil_qb_valid(int N, int mixed, int qb) {
+  switch (N) {
+#define CASE(n) \
+  case n: return mixed ? qb_valid_n<float, n>(qb) : qb_valid_n<double, n>(qb);
+    LISE_FOR_N(CASE)
+#undef CASE
+    default: return false;
   }
 }
 

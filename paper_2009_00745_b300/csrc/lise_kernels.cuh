@@ -144,7 +144,13 @@ struct PointwiseArgs {
 
 // Host-side launchers (defined in lise_kernels.cu).
 int launch_planes(int N, int mixed, const PlanesArgs& a, cudaStream_t s);
-int launch_pencils(int N, int mixed, int mode, const PencilArgs& a, cudaStream_t s);
+// qb: states per batch of the step modes (2 or 4 where compiled); 0 = the tuned value,
+// else the default for the lattice and precision
+int launch_pencils(int N, int mixed, int mode, const PencilArgs& a, cudaStream_t s, int qb = 0);
+// Pencil batch autotuning state (per process): tuned QB per (precision, N), 0 = none.
+int pencil_qb_get(int N, int mixed);
+void pencil_qb_set(int N, int mixed, int qb);
+bool pencil_qb_valid(int N, int mixed, int qb);
 int launch_reduce(const ReduceArgs& a, cudaStream_t s);
 int launch_predict(const PointwiseArgs& a, cudaStream_t s);
 int launch_density(const PointwiseArgs& a, cudaStream_t s);

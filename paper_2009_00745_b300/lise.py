@@ -47,6 +47,8 @@ SIGNATURES = {
     "lise_set_state_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_double]),
     "lise_kick": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lise_currents": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "lise_pencil_batch": (C.c_int, [C.c_int, C.c_int]),
+    "lise_set_pencil_batch": (C.c_int, [C.c_int, C.c_int, C.c_int]),
     "lise_step": (C.c_int, [C.c_void_p, C.c_int, C.c_double]),
     "lise_get_state": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lise_get_state_device": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -117,6 +119,17 @@ def _params(N, n_qp, a, alpha, beta, mu, g, v_static, drive_A, drive_Omega, prec
                 int(prec), int(device), int(hbm_budget_bytes), stream, int(bool(remove_phase)),
                 float(pair_alpha), float(pair_n0), int(bool(pair_lattice)), int(bool(renormalize)))
     return p, vs
+
+
+def pencil_batch(N, precision="fp64") -> int:
+    """States per batch the pencils kernel uses for this lattice and precision (tuned or default)."""
+    return int(load().lise_pencil_batch(int(N), {"fp64": FP64, "mixed": MIXED}[precision]))
+
+
+def set_pencil_batch(N, precision="fp64", qb=0):
+    """Force the pencils batch size (2 or 4), or qb = 0 to re-tune at the next set_state."""
+    _check(load().lise_set_pencil_batch(int(N), {"fp64": FP64, "mixed": MIXED}[precision], int(qb)),
+           "lise_set_pencil_batch")
 
 
 def footprint_bytes(N, n_qp, precision="fp64", **kw) -> int:

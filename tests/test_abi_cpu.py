@@ -86,3 +86,16 @@ def test_null_arguments(lib):
     assert lib.lise_step(None, 1, 0.1) == L.EINVAL
     assert lib.lise_sync(None) == L.EINVAL
     lib.lise_destroy(None)
+
+
+def test_pencil_batch_controls_host_only():
+    # host-side table of the pencil autotuner: no device call
+    assert L.pencil_batch(30) == 0                       # unsupported lattice
+    assert L.pencil_batch(32, "fp64") in (2, 4)
+    with pytest.raises(L.LiseError) as e:
+        L.set_pencil_batch(32, "fp64", 3)                # no such variant
+    assert e.value.status == L.EINVAL
+    L.set_pencil_batch(16, "mixed", 4)
+    assert L.pencil_batch(16, "mixed") == 4
+    L.set_pencil_batch(16, "mixed", 0)                   # back to the default / next tuning
+    assert L.pencil_batch(16, "mixed") in (2, 4)

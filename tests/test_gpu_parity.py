@@ -441,3 +441,29 @@ def test_renormalize_parity(N):
     s.set_state(w.initial_state(), 0.0, w.dt)
     s.step(10)
     assert rel(got, s.state()) < TOL_FP64_RUN
+
+
+# ------------------------------------------------------------ pencil batch autotuning ----
+
+@pytest.mark.parametrize("N,precision", [(16, "fp64"), (32, "fp64"), (24, "mixed"), (48, "mixed")])
+def test_pencil_batch_choice_is_bitwise_neutral(N, precision):
+    w = W.ufg_plane_waves(N, 13, noise_eps=0.05)
+
+    def run():
+        with L.Context.from_workload(w, precision=precision) as ctx:
+            ctx.set_state(w.initial_state(), 0.0, w.dt)
+            ctx.step(5)
+            return ctx.state()
+
+    outs = {}
+    for qb in (2, 4):
+        try:
+            L.set_pencil_batch(N, precision, qb)
+        except L.LiseError:
+            continue  # variant not compiled for this lattice (shared memory)
+        outs[qb] = run()
+    L.set_pencil_batch(N, precision, 0)   # the next set_state tunes
+    tuned = run()
+    assert L.pencil_batch(N, precision) in outs
+    for x in outs.values():
+        assert np.array_equal(x, tuned)

@@ -467,3 +467,21 @@ def test_pencil_batch_choice_is_bitwise_neutral(N, precision):
     assert L.pencil_batch(N, precision) in outs
     for x in outs.values():
         assert np.array_equal(x, tuned)
+
+
+# ------------------------------------------------------------ large lattices ----
+
+def test_fp64_run_64_cubed():
+    # the largest lattice: tensor-core kinetic operator with K = 64 (levels converted per
+    # 16-deep step) in both kernels
+    w = W.ufg_plane_waves(64, 3, noise_eps=0.05, steps=3)
+    check_run(w, w.steps)
+
+
+@pytest.mark.parametrize("N", [40, 64])
+def test_mixed_run_large_lattices(N):
+    w = W.ufg_plane_waves(N, 4, noise_eps=1e-3, steps=4)
+    g = run_gpu(w, w.steps, precision="mixed")
+    o = run_oracle(w, w.steps)
+    assert rel(g[0], o[0]) < 5e-6
+    assert abs(g[3] - o[3]) / abs(o[3]) < 1e-6

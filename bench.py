@@ -70,8 +70,9 @@ def algorithmic_per_qp_site(N, mixed):
     FP64 flops (an FMA counts 2), as written in the kernels:
       corrector  per real: T_z + T_xy 1, BdG 3 FMA, y_{n+1} 1 FMA, p - c 1 FMA  -> 11
                  densities 3 x 2 FMA per (state, site)                          -> 12
-      deriv/pred per real: T_z + T_xy 1, BdG 3 FMA, Y 1 + 3 FMA, R 1 + 3 FMA,
-                 Q 2 FMA, m 1 + 1 FMA                                           -> 28
+      deriv/pred per real: T_z + T_xy 1, BdG 3 FMA, Y 1 + 1 FMA, R 1, Q 2 FMA,
+                 m 1 + 1 FMA (the derivative sums of Y and R are exact integer
+                 sums, no FP64 instruction)                                     -> 18
                  densities                                                      -> 12
     per (state, site): 2 components x 2 reals."""
     L = log2(N)
@@ -99,7 +100,7 @@ def algorithmic_per_qp_site(N, mixed):
     if tensor:
         mma = 2 * 2 * N * 28 * 2          # bf16 flops per (state, site) and axis: 2 comps x re/im x K x pairs
         out["planes"].update({"flops": 2 * 2 * mma, "kind": "bf16 tensor"})
-        out["pencils"].update({"flops": 4 * 11 + 12 + 4 * 28 + 12, "kind": "fp64", "tensor_flops": 2 * mma})
+        out["pencils"].update({"flops": 4 * 11 + 12 + 4 * 18 + 12, "kind": "fp64", "tensor_flops": 2 * mma})
     return out
 
 

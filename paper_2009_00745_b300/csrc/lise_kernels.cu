@@ -76,6 +76,41 @@ __device__ __forceinline__ double2 dmul(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
+// The predictor's derivative sums of the FP64 path, evaluated exactly in integers:
+//   sp = 119 f - 99 e0 + 69 e1 - 17 e2   (pt = h/48 sp, Eq. p)
+//   sr =  68 f - 102 e0 + 68 e1 - 17 e2  (pt - ct = h/48 sr, with ct of Eq. c)
+// The four significands are aligned to the largest exponent (bits below 2^-52 of the
+// largest value are dropped), the sums are exact in 64-bit integers (|sum| < 2^62) and
+// each is rounded once to FP64 -- no FP64 instruction.  Non-finite or extreme inputs take
+// the FP64 formula (which keeps NaN and inf).
+__device__ __forceinline__ void pred_sums(double f, double e0, double e1, double e2, double& sp, double& sr) {
+  const double v[4] = {f, e0, e1, e2};
+  unsigned long long b[4];
+  int ex[4], emax = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    b[k] = (unsigned long long)__double_as_longlong(v[k]);
+    ex[k] = (int)((b[k] >> 52) & 0x7FF);
+    emax = max(emax, ex[k]);
+  }
+  if (emax == 0 || emax > 2000) {
+    sp = 119.0 * f - 99.0 * e0 + 69.0 * e1 - 17.0 * e2;
+    sr = 68.0 * f - 102.0 * e0 + 68.0 * e1 - 17.0 * e2;
+    return;
+  }
+  long long A[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    unsigned long long m = ex[k] ? ((b[k] & 0xFFFFFFFFFFFFFull) | (1ull << 52)) : 0ull;
+    const int sh = emax - ex[k];
+    m = sh < 64 ? (m >> sh) : 0ull;
+    A[k] = (b[k] >> 63) ? -(long long)m : (long long)m;
+  }
+  const int sc = emax - 1075;  // a significand aligned to emax is worth 2^(emax - 1075)
+  sp = oz::to_double(119 * A[0] - 99 * A[1] + 69 * A[2] - 17 * A[3], sc);
+  sr = oz::to_double(68 * A[0] - 102 * A[1] + 68 * A[2] - 17 * A[3], sc);
+}
+
 // sn += |v|^2 ; nu += u conj(v)  (the factor 2 of n = 2 sum |v|^2 is applied where the
 // partial sums are stored; scaling by 2 is exact, so the order does not matter)
 __device__ __forceinline__ void dens_acc(double2 u, double2 v, double& sn, double& sr, double& si) {
@@ -439,6 +474,7 @@ __global__ void __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N
   const R y0c = h48 * (c161_ * R(51) + c9_ * R(119)), y1c = h48 * (c161_ * R(3) - c9_ * R(99)),
           y2c = h48 * (c161_ + c9_ * R(69)), y3c = h48 * (-c9_ * R(17));
   const R r0c = h48 * R(68), r1c = h48 * R(-102), r2c = h48 * R(68), r3c = h48 * R(-17);
+  const R c161h = c161_ * h48;
   auto base = [](int l) { return (l / TX) * CS + (l % TX); };
   // issue the asynchronous copies of one batch's operand and T_xy (own site only)
   auto prefetch = [&](int qb) {
@@ -643,8 +679,18 @@ __global__ void __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N
           const T e0 = reinterpret_cast<const T*>(a.d0)[i], e1 = reinterpret_cast<const T*>(a.d1)[i],
                   e2 = reinterpret_cast<const T*>(a.d2)[i];
           const T pcv = reinterpret_cast<const T*>(a.pc)[i];
-          const T Y = T{y0c * f.x + y1c * e0.x + y2c * e1.x + y3c * e2.x, y0c * f.y + y1c * e0.y + y2c * e1.y + y3c * e2.y};
-          const T Rv = T{r0c * f.x + r1c * e0.x + r2c * e1.x + r3c * e2.x, r0c * f.y + r1c * e0.y + r2c * e1.y + r3c * e2.y};
+          T Y, Rv;
+          if constexpr (sizeof(R) == 8) {
+            // exact integer sums (pred_sums), then Y = (161/170) ct + (9/170) pt = pt - (161/170)(pt - ct)
+            double spx, srx, spy, sry;
+            pred_sums(f.x, e0.x, e1.x, e2.x, spx, srx);
+            pred_sums(f.y, e0.y, e1.y, e2.y, spy, sry);
+            Rv = T{h48 * srx, h48 * sry};
+            Y = T{fma(-c161h, srx, h48 * spx), fma(-c161h, sry, h48 * spy)};
+          } else {
+            Y = T{y0c * f.x + y1c * e0.x + y2c * e1.x + y3c * e2.x, y0c * f.y + y1c * e0.y + y2c * e1.y + y3c * e2.y};
+            Rv = T{r0c * f.x + r1c * e0.x + r2c * e1.x + r3c * e2.x, r0c * f.y + r1c * e0.y + r2c * e1.y + r3c * e2.y};
+          }
           const double2 xv = a.x[i], y0v = a.y0[i], Yd = to_d(Y);
           const double2 qv = make_double2(fma(0.5, xv.x, fma(0.5, y0v.x, Yd.x)), fma(0.5, xv.y, fma(0.5, y0v.y, Yd.y)));
           const T mv = to_r<R>(make_double2(fma((double)c161, (double)(Rv.x - pcv.x), qv.x),

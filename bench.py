@@ -3,22 +3,32 @@
 python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl reference]
 
 A "step" is one Adams-Bashforth-Milne step (Eqs. p, m, c, y of arXiv:2009.00745:
-two right-hand sides, each an FFT kinetic operator, a BdG apply and a density
+two right-hand sides, each a kinetic operator, a BdG apply and a density
 reduction) over all quasiparticle states of the workload.  Default workload:
 32^3 lattice, 2048 states in a harmonic trap with a vortex phase, FP64
 (trap32_vortex_fp64).  Inputs are synthetic and seeded (workloads.py).
 
-value   device time of K steps with the state resident in HBM (CUDA events on
-        the context's stream, W warm-up steps first).  The state and history
-        (10 complex128 copies, ~21 GB) are far larger than L2, so no flush.
-e2e     the same metric through the C ABI with host buffers: lise_set_state
-        from pinned host memory (including the start procedure), K steps,
-        lise_get_state back to pinned host memory and lise_energy.
-roofline, cpu_baseline, clocks, gpu_launches: see the README of each key in
-the design doc.  --impl reference times the FP64 CPU oracle instead (the reference
-arm of this build: a deliberately plain program on the host cores).
-Multi-GPU (torchrun): every rank runs an independent replica ("replicas only";
-the single-GPU path has no exchange step), value = total units / max time.
+value        device time of K steps with the state resident in HBM (CUDA events
+             on the context's stream, W warm-up steps first).  The state and ABM
+             history (~21 GB in FP64) are far larger than L2, so no flush.
+e2e          the same metric through the C ABI with host buffers: lise_set_state
+             from pinned host memory (including the start procedure), K steps,
+             lise_get_state back to pinned host memory and lise_energy.
+roofline     the kernel class with the largest share of device time (per-launch
+             CUDA events): algorithmic flops or bytes per launch (see
+             algorithmic_per_qp_site) over the mean launch time, against the
+             FP64/FP32 unit peak or the measured HBM copy bandwidth; traffic is
+             the DRAM bytes per launch from the committed ncu summary
+             (profiles/traffic.json) when it was taken on the current sources.
+cpu_baseline the FP64 CPU oracle on a bounded sample of the same workload, on the
+             host cores (thread count reported).
+clocks       SM clocks and throttle reasons sampled during the timed region.
+gpu_launches the library's kernel launches inside the timed region.
+--impl reference times the FP64 CPU oracle instead (a deliberately plain program
+on the host cores).  Multi-GPU (torchrun): every rank runs an independent replica
+("replicas only"; the single-GPU path has no exchange step), value = total units /
+max time.  --drift, --serve and --batch run the other measurements (see their
+functions).
 """
 import argparse
 import hashlib

@@ -7,7 +7,7 @@
  * used only over independent quasiparticle states or lattice sites, never
  * inside a sum, so results do not depend on the thread count.
  *
- * Readings of points the paper leaves open (all listed again in the design doc):
+ * Readings of points the paper leaves open:
  *   - Eq. p prints the y'_n coefficient without a number; 119 is used (the
  *     unique value that makes the predictor exact for polynomials of degree 4
  *     and gives the printed error constant 161/480).

@@ -9,7 +9,7 @@
 // Ozaki, Ogita, Oishi and Rump, in its integer-digit form):
 //   * every FP64 value of a group of lines sharing one binary exponent E (the
 //     largest biased exponent in the group) becomes the integer
-//       I = round(x 2^(1077 - E)),  |I| <= 2^55,
+//       I = trunc(x 2^(1077 - E)),  |I| < 2^55,
 //     written as 7 balanced base-256 digits I = sum_k d_k 256^(6-k), |d_k| <= 128;
 //     the D2 entries likewise, with a common exponent (host tables);
 //   * digit products are exact in bf16 x bf16 -> FP32, and the sum over K and
@@ -62,33 +62,34 @@ __device__ __forceinline__ unsigned short bf16_of_int(int d) {
   return (unsigned short)(__float_as_uint(f) >> 16);
 }
 
+// bf16 bit pattern of (byte - 128) for the byte held in the low byte of w = 0x4B4000bb:
+// as FP32 that word is 1.5 * 2^23 + byte, so one subtraction gives byte - 128 exactly.
+__device__ __forceinline__ unsigned short bf16_of_biased_byte(unsigned w) {
+  return (unsigned short)(__float_as_uint(__int_as_float(w) - 12583040.0f) >> 16);
+}
+
 // The 7 balanced base-256 digits (as bf16 bit patterns, most significant first)
-// of I = round(x 2^(1077 - E)), for E >= the exponent field of x (E >= 1).
+// of I = trunc(x 2^(1077 - E)) (magnitude truncated), for E >= the exponent field
+// of x (E >= 1).  Balanced digits without a carry chain: with the bias
+// B = sum_{k=1..6} 128 * 256^(6-k), the low six bytes of I + B are d_k + 128 and
+// (I + B) >> 48 is the top digit d_0.
 __device__ __forceinline__ void split(double x, unsigned E, unsigned short d[S]) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const int ex = (int)((b >> 52) & 0x7FF);
   const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
   const int s = (int)E - ex - 2;  // right shift of the 53-bit significand, >= -2
-  unsigned long long u;
-  if (ex == 0 || s >= 56)
-    u = 0;
-  else if (s <= 0)
-    u = m << (-s);
-  else
-    u = (m + (1ull << (s - 1))) >> s;  // round half away from zero (on the magnitude)
-  const long long I = (b >> 63) ? -(long long)u : (long long)u;
-  const unsigned lo = (unsigned)I;
-  const int hi = (int)(I >> 32);
-  // bytes from the least significant up, with a balancing carry
-  int carry = 0;
-#pragma unroll
-  for (int k = S - 1; k >= 1; --k) {
-    const int sh = 8 * (S - 1 - k);  // 0, 8, ..., 40
-    const int byte = (int)(((sh < 32) ? (lo >> sh) : ((unsigned)hi >> (sh - 32))) & 0xFFu) + carry;
-    carry = (byte + 128) >> 8;  // 1 if byte >= 128
-    d[k] = bf16_of_int(byte - (carry << 8));
-  }
-  d[0] = bf16_of_int((hi >> 16) + carry);  // I >> 48 (arithmetic) plus the carry
+  unsigned long long u = s <= 0 ? (m << (-s)) : (s < 64 ? (m >> s) : 0ull);
+  if (ex == 0) u = 0;
+  const unsigned long long sm = (unsigned long long)((long long)b >> 63);  // 0, or all ones if x < 0
+  const unsigned long long ib = ((u ^ sm) - sm) + 0x0000808080808080ull;   // I + B
+  const unsigned lo = (unsigned)ib, hi = (unsigned)(ib >> 32);
+  d[6] = bf16_of_biased_byte(__byte_perm(lo, 0x4B400000u, 0x7640));
+  d[5] = bf16_of_biased_byte(__byte_perm(lo, 0x4B400000u, 0x7641));
+  d[4] = bf16_of_biased_byte(__byte_perm(lo, 0x4B400000u, 0x7642));
+  d[3] = bf16_of_biased_byte(__byte_perm(lo, 0x4B400000u, 0x7643));
+  d[2] = bf16_of_biased_byte(__byte_perm(hi, 0x4B400000u, 0x7640));
+  d[1] = bf16_of_biased_byte(__byte_perm(hi, 0x4B400000u, 0x7641));
+  d[0] = bf16_of_int(((int)hi) >> 16);
 }
 
 // Exact FP32 integer (|v| < 2^22) to int.

@@ -334,8 +334,9 @@ __global__ void __launch_bounds__(256) k_planes_oz(PlanesArgs a) {
   double2* dst = reinterpret_cast<double2*>(a.txy) + plane0 * N * N;
   for (int i = tid; i < np * N * N; i += NT) {
     const int pl = i / (N * N), rem = i % (N * N);
-    const double re = oz::to_double(acc64[(2 * pl) * N * N + rem], oz::out_scale(a.oz_sD, Eg[2 * pl]));
-    const double im = oz::to_double(acc64[(2 * pl + 1) * N * N + rem], oz::out_scale(a.oz_sD, Eg[2 * pl + 1]));
+    // (the FP64 pipe is idle in this kernel: convert there)
+    const double re = oz::to_double_hw(acc64[(2 * pl) * N * N + rem], oz::out_scale(a.oz_sD, Eg[2 * pl]));
+    const double im = oz::to_double_hw(acc64[(2 * pl + 1) * N * N + rem], oz::out_scale(a.oz_sD, Eg[2 * pl + 1]));
     dst[i] = make_double2(re, im);
   }
 }

@@ -122,6 +122,14 @@ __device__ __forceinline__ double to_double(long long T, int sc) {
   return __longlong_as_double((long long)(sign | ((unsigned long long)ex << 52) | (mant & 0xFFFFFFFFFFFFFull)));
 }
 
+// The same conversion through the FP64 unit (one I2F.F64 and an exponent add), for
+// kernels whose FP64 pipe is otherwise idle; T * 2^sc must be a normal number.
+__device__ __forceinline__ double to_double_hw(long long T, int sc) {
+  if (T == 0) return 0.0;
+  const double v = __ll2double_rn(T);
+  return __longlong_as_double(__double_as_longlong(v) + ((long long)sc << 52));
+}
+
 // Output scale: value = T * 2^(sD + E - 1021) for a data group of exponent field E
 // and D2 digits of I_D = round(D2 * 2^-sD).
 __device__ __forceinline__ int out_scale(int sD, unsigned E) { return sD + (int)E - 1021; }

@@ -1030,7 +1030,7 @@ int lise_rhs(lise_ctx* c, const double* psi, double t, double* dpsi_out) {
 // ---------------------------------------------------------------- checkpoint --
 namespace {
 struct CkptHeader {
-  char magic[8];        // "LISECKP2"
+  char magic[8];        // "LISECKP3"
   int N, n_qp, precision, y0_slot_unused;
   double t, dt;
   long long ns, nxyz;
@@ -1068,7 +1068,7 @@ int lise_checkpoint_save(lise_ctx* c, void* buf, size_t bytes) {
   TRY(fetch_err(c));
   CkptHeader hd;
   std::memset(&hd, 0, sizeof(hd));
-  std::memcpy(hd.magic, "LISECKP2", 8);
+  std::memcpy(hd.magic, "LISECKP3", 8);
   hd.N = c->N;
   hd.n_qp = c->p.n_qp;
   hd.precision = c->p.precision;
@@ -1096,7 +1096,7 @@ int lise_checkpoint_load(lise_ctx* c, const void* buf, size_t bytes) {
   if (bytes < lise_checkpoint_bytes(c)) return LISE_EINVAL;
   CkptHeader hd;
   std::memcpy(&hd, buf, sizeof(hd));
-  if (std::memcmp(hd.magic, "LISECKP2", 8) != 0 || hd.N != c->N || hd.n_qp != c->p.n_qp ||
+  if (std::memcmp(hd.magic, "LISECKP3", 8) != 0 || hd.N != c->N || hd.n_qp != c->p.n_qp ||
       hd.precision != c->p.precision || hd.ns != c->ns || hd.nxyz != c->nxyz || !(hd.dt != 0.0))
     return LISE_EINVAL;
   if (cudaSetDevice(c->device) != cudaSuccess) return LISE_ECUDA;

@@ -420,7 +420,7 @@ __host__ __device__ constexpr int pencil_smem_bytes() {
 }
 
 template <typename R, int N, int TX, int QB, int MODE>
-__global__ void __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N * TX == 256 ? 2 : ((sizeof(R) == 8 && N * TX == 128) ? 4 : 1)) k_pencils(PencilArgs a) {
+__global__ void __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N * TX == 256 ? 2 : ((sizeof(R) == 8 && N * TX == 128) ? 7 : 1)) k_pencils(PencilArgs a) {
   using T = typename Cx<R>::T;
   constexpr int NT = N * TX;
   // one component block [z][x] in shared memory; for 8-byte elements the blocks are
@@ -469,8 +469,12 @@ __global__ void __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N
   // step-size coefficients of the ABM epilogues, once per thread:
   //   corrector  y_{n+1} = Q + kc1 m',  p - c = R - kc2 m'
   //   predictor  Y = sum y?c y'_?,  R = sum r?c y'_?  (see M_DERIV_PREDICT)
+  // In FP64, R and p - c are kept in units of h/48 (R = 68 y'_{n+1} - 102 y'_n + ..., the
+  // exact integer-coefficient sum, p - c = R - 17 m'): the scale h/48 then enters once, where
+  // m is formed, instead of once per stored value.
   constexpr bool kCor = MODE == M_CORRECT, kPred = MODE == M_DERIV_PREDICT;
-  const R kc2 = kCor ? (R)(17.0 / 48.0 * a.h) : R(0), kc1 = kCor ? (R)(161.0 / 170.0 * 17.0 / 48.0 * a.h) : R(0);
+  const R kc2 = kCor ? (sizeof(R) == 8 ? R(17) : (R)(17.0 / 48.0 * a.h)) : R(0),
+          kc1 = kCor ? (R)(161.0 / 170.0 * 17.0 / 48.0 * a.h) : R(0);
   const R h48 = kPred ? (R)(a.h / 48.0) : R(0), c161_ = (R)(161.0 / 170.0), c9_ = (R)(9.0 / 170.0);
   const R y0c = h48 * (c161_ * R(51) + c9_ * R(119)), y1c = h48 * (c161_ * R(3) - c9_ * R(99)),
           y2c = h48 * (c161_ + c9_ * R(69)), y3c = h48 * (-c9_ * R(17));
@@ -593,8 +597,13 @@ __global__ void __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N
         continue;
       }
       // H x = [[h, Delta], [Delta*, -h*]] x with h = T + W (W real, T real-symmetric);
-      // with trivial-phase removal (Eq. sp_en) the generator is H - eta_q
-      const T u = xr[j][0], v = xr[j][1];
+      // with trivial-phase removal (Eq. sp_en) the generator is H - eta_q.
+      // The FP64 tensor-core path reloads the operand (an L1/L2 hit) rather than keeping
+      // it in registers across the digit products.
+      auto opnd = [&](long i) -> T {
+        return a.xr ? reinterpret_cast<const T*>(a.xr)[i] : to_r<R>(a.x[i]);
+      };
+      const T u = kOz ? opnd(iu) : xr[j][0], v = kOz ? opnd(iv) : xr[j][1];
       const R w = a.eta ? Wr - (R)a.eta[q] : Wr;
       const R w2 = a.eta ? Wr + (R)a.eta[q] : Wr;  // -(h + eta) on the v component
       const T d = Dr;
@@ -668,8 +677,11 @@ __global__ void __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N
         //   pt = h/48 (119 y'_{n+1} - 99 y'_n + 69 y'_{n-1} - 17 y'_{n-2})
         //   ct = h/48 (51 y'_{n+1} + 3 y'_n + y'_{n-1}),  hf = (y_{n+1} + y_n)/2
         //   m = hf + pt - (161/170) pc,  Q = hf + (161/170) ct + (9/170) pt,  R = pt - ct.
-        // Formed as Y = (161/170) ct + (9/170) pt and R directly from the derivatives,
-        // Q = hf + Y and m = Q + (161/170)(R - pc) (as 1 - 9/170 = 161/170, m - Q = (161/170)(pt - ct - pc)).
+        // FP64: from the exact integer sums sp = 48 pt / h and sr = 48 R / h (pred_sums),
+        //   P = hf + pt (Eq. p),  Q = P - (161/170) R,  m = P - (161/170) pc  (Eq. m),
+        // with R and pc kept in units of h/48.  FP32 compute precision: Y = (161/170) ct +
+        // (9/170) pt and R directly from the derivatives, Q = hf + Y and m = Q + (161/170)(R - pc)
+        // (as 1 - 9/170 = 161/170, m - Q = (161/170)(pt - ct - pc)).
         const R c161 = (R)(161.0 / 170.0);
         T mo[2];
 #pragma unroll
@@ -680,22 +692,26 @@ __global__ void __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N
           const T e0 = reinterpret_cast<const T*>(a.d0)[i], e1 = reinterpret_cast<const T*>(a.d1)[i],
                   e2 = reinterpret_cast<const T*>(a.d2)[i];
           const T pcv = reinterpret_cast<const T*>(a.pc)[i];
-          T Y, Rv;
+          const double2 xv = a.x[i], y0v = a.y0[i];
+          T Rv, mv;
+          double2 qv;
           if constexpr (sizeof(R) == 8) {
-            // exact integer sums (pred_sums), then Y = (161/170) ct + (9/170) pt = pt - (161/170)(pt - ct)
             double spx, srx, spy, sry;
             pred_sums(f.x, e0.x, e1.x, e2.x, spx, srx);
             pred_sums(f.y, e0.y, e1.y, e2.y, spy, sry);
-            Rv = T{h48 * srx, h48 * sry};
-            Y = T{fma(-c161h, srx, h48 * spx), fma(-c161h, sry, h48 * spy)};
+            Rv = T{srx, sry};
+            const double Px = fma(0.5, xv.x, fma(0.5, y0v.x, h48 * spx)),
+                         Py = fma(0.5, xv.y, fma(0.5, y0v.y, h48 * spy));
+            qv = make_double2(fma(-c161h, srx, Px), fma(-c161h, sry, Py));
+            mv = T{fma(-c161h, pcv.x, Px), fma(-c161h, pcv.y, Py)};
           } else {
-            Y = T{y0c * f.x + y1c * e0.x + y2c * e1.x + y3c * e2.x, y0c * f.y + y1c * e0.y + y2c * e1.y + y3c * e2.y};
+            const T Y = T{y0c * f.x + y1c * e0.x + y2c * e1.x + y3c * e2.x, y0c * f.y + y1c * e0.y + y2c * e1.y + y3c * e2.y};
             Rv = T{r0c * f.x + r1c * e0.x + r2c * e1.x + r3c * e2.x, r0c * f.y + r1c * e0.y + r2c * e1.y + r3c * e2.y};
+            const double2 Yd = to_d(Y);
+            qv = make_double2(fma(0.5, xv.x, fma(0.5, y0v.x, Yd.x)), fma(0.5, xv.y, fma(0.5, y0v.y, Yd.y)));
+            mv = to_r<R>(make_double2(fma((double)c161, (double)(Rv.x - pcv.x), qv.x),
+                                      fma((double)c161, (double)(Rv.y - pcv.y), qv.y)));
           }
-          const double2 xv = a.x[i], y0v = a.y0[i], Yd = to_d(Y);
-          const double2 qv = make_double2(fma(0.5, xv.x, fma(0.5, y0v.x, Yd.x)), fma(0.5, xv.y, fma(0.5, y0v.y, Yd.y)));
-          const T mv = to_r<R>(make_double2(fma((double)c161, (double)(Rv.x - pcv.x), qv.x),
-                                            fma((double)c161, (double)(Rv.y - pcv.y), qv.y)));
           reinterpret_cast<T*>(a.m)[i] = mv;
           a.q[i] = qv;
           reinterpret_cast<T*>(a.r)[i] = Rv;
@@ -806,7 +822,9 @@ __global__ void k_predict(PointwiseArgs a) {
       const T pt = T{h48 * (R(119) * e0.x - R(99) * e1.x + R(69) * e2.x - R(17) * e3.x),
                      h48 * (R(119) * e0.y - R(99) * e1.y + R(69) * e2.y - R(17) * e3.y)};
       const T ct = T{h48 * (R(51) * e0.x + R(3) * e1.x + e2.x), h48 * (R(51) * e0.y + R(3) * e1.y + e2.y)};
-      const T X = T{pt.x - c161 * pcv.x, pt.y - c161 * pcv.y};
+      // FP64 keeps p - c and R in units of h/48 (as the FP64 pencils epilogues do)
+      const R cpc = sizeof(R) == 8 ? c161 * h48 : c161;
+      const T X = T{pt.x - cpc * pcv.x, pt.y - cpc * pcv.y};
       const T Y = T{c161 * ct.x + c9 * pt.x, c161 * ct.y + c9 * pt.y};
       const double2 y0 = a.y0[i], y1 = a.y1[i];
       if constexpr (sizeof(R) == 4) {
@@ -826,7 +844,11 @@ __global__ void k_predict(PointwiseArgs a) {
         a.q[i] = dadd(hf, to_d(Y));
         mo[c] = to_r<R>(mv);
       }
-      reinterpret_cast<T*>(a.r)[i] = T{pt.x - ct.x, pt.y - ct.y};
+      if constexpr (sizeof(R) == 8)
+        reinterpret_cast<T*>(a.r)[i] = T{R(68) * e0.x - R(102) * e1.x + R(68) * e2.x - R(17) * e3.x,
+                                         R(68) * e0.y - R(102) * e1.y + R(68) * e2.y - R(17) * e3.y};
+      else
+        reinterpret_cast<T*>(a.r)[i] = T{pt.x - ct.x, pt.y - ct.y};
     }
     if constexpr (sizeof(R) == 4)
       dens_acc(mo[0], mo[1], dF);

@@ -231,6 +231,9 @@ __global__ void __launch_bounds__(256) k_planes_oz(PlanesArgs a) {
   constexpr int KS = N / 16, NTILE = N / 8, MT = G * N / 16;
   constexpr int EPT = PB * N * N / NT;  // elements per thread
   static_assert(PB * N * N % NT == 0, "plane block size");
+  // x-adjacent element pairs per thread (two digits per 32-bit shared store) where the 2 NT
+  // elements of one pass lie in one plane
+  constexpr bool kPair = N * N % (2 * NT) == 0;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned short* dig = reinterpret_cast<unsigned short*>(smem_raw);  // [S][G][N][RS]
   long long* acc64 = reinterpret_cast<long long*>(smem_raw + P::dig_bytes);  // [G][N][N]
@@ -243,15 +246,16 @@ __global__ void __launch_bounds__(256) k_planes_oz(PlanesArgs a) {
   // the operand: x, or xr when the operand is stored in the compute precision (here FP64)
   const double2* src = (a.xr ? reinterpret_cast<const double2*>(a.xr) : a.x) + plane0 * N * N;
 
-  // 1. the operand and the largest exponent of each (plane, re/im) group
+  // 1. the operand and the largest exponent of each (plane, re/im) group; each thread
+  // holds pairs of x-adjacent elements (element i = 2 (tid + r' NT) + e, r = 2 r' + e)
   double2 v[EPT];
   unsigned em[G];
 #pragma unroll
   for (int g = 0; g < G; ++g) em[g] = 0;
 #pragma unroll
   for (int r = 0; r < EPT; ++r) {
-    const int i = tid + r * NT;
-    const int pl = (r * NT) / (N * N);  // the same for the whole block at this r
+    const int i = kPair ? 2 * (tid + (r >> 1) * NT) + (r & 1) : tid + r * NT;
+    const int pl = (kPair ? 2 * (r >> 1) * NT : r * NT) / (N * N);  // the same for the whole block at this r
     v[r] = pl < np ? src[i] : make_double2(0.0, 0.0);
     em[2 * pl] = max(em[2 * pl], oz::exp_field(v[r].x));
     em[2 * pl + 1] = max(em[2 * pl + 1], oz::exp_field(v[r].y));
@@ -270,31 +274,54 @@ __global__ void __launch_bounds__(256) k_planes_oz(PlanesArgs a) {
   }
   __syncthreads();
 
-  // 2. digits: dig[d][g][y][x]
+  // 2. digits: dig[d][g][y][x] (with pairs: the two x-adjacent digits in one 32-bit store)
+  if constexpr (kPair) {
 #pragma unroll
-  for (int r = 0; r < EPT; ++r) {
-    const int i = tid + r * NT;
-    const int pl = i / (N * N), rem = i % (N * N);
-    const int y = rem / N, x = rem % N;
+    for (int r = 0; r < EPT; r += 2) {
+      const int i = 2 * (tid + (r >> 1) * NT);
+      const int pl = i / (N * N), rem = i % (N * N);
+      const int y = rem / N, x = rem % N;
 #pragma unroll
-    for (int ri = 0; ri < 2; ++ri) {
-      const int g = 2 * pl + ri;
-      unsigned short d[oz::S];
-      oz::split(ri ? v[r].y : v[r].x, Eg[g], d);
+      for (int ri = 0; ri < 2; ++ri) {
+        const int g = 2 * pl + ri;
+        unsigned short d0[oz::S], d1[oz::S];
+        oz::split(ri ? v[r].y : v[r].x, Eg[g], d0);
+        oz::split(ri ? v[r + 1].y : v[r + 1].x, Eg[g], d1);
 #pragma unroll
-      for (int k = 0; k < oz::S; ++k) dig[((k * G + g) * N + y) * RS + x] = d[k];
+        for (int k = 0; k < oz::S; ++k)
+          *reinterpret_cast<unsigned*>(dig + ((k * G + g) * N + y) * RS + x) = (unsigned)d0[k] | ((unsigned)d1[k] << 16);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < EPT; ++r) {
+      const int i = tid + r * NT;
+      const int pl = i / (N * N), rem = i % (N * N);
+      const int y = rem / N, x = rem % N;
+#pragma unroll
+      for (int ri = 0; ri < 2; ++ri) {
+        const int g = 2 * pl + ri;
+        unsigned short d[oz::S];
+        oz::split(ri ? v[r].y : v[r].x, Eg[g], d);
+#pragma unroll
+        for (int k = 0; k < oz::S; ++k) dig[((k * G + g) * N + y) * RS + x] = d[k];
+      }
     }
   }
   __syncthreads();
 
   const int gq = lane >> 2, t4 = lane & 3;
   const int mi = lane >> 3, r8 = lane & 7;
+  // every job of a warp has the output tile nt = w mod NTILE when NTILE divides the warp
+  // count: its D2 fragments are then loaded once
+  constexpr bool kBOnce = NW % NTILE == 0;
+  uint32_t b[oz::S][KS][2];
+  if (kBOnce) oz::load_b<KS>(b, a.ozb, w % NTILE, NTILE);
   // 3a. T_x: data rows (g, y), K = x'
   for (int job = w; job < MT * NTILE; job += NW) {
     const int mt = job / NTILE, nt = job % NTILE;
     const int g = mt / (N / 16), y0 = (mt % (N / 16)) * 16;
-    uint32_t b[oz::S][KS][2];
-    oz::load_b<KS>(b, a.ozb, nt, NTILE);
+    if (!kBOnce) oz::load_b<KS>(b, a.ozb, nt, NTILE);
     int iacc[oz::S][4];
     oz::tile_levels<KS, false>(iacc, b, [&](int k, int ks) {
       return dig + ((k * G + g) * N + y0 + r8 + 8 * (mi & 1)) * RS + ks * 16 + 8 * (mi >> 1);
@@ -313,8 +340,7 @@ __global__ void __launch_bounds__(256) k_planes_oz(PlanesArgs a) {
   for (int job = w; job < MT * NTILE; job += NW) {
     const int mt = job / NTILE, nt = job % NTILE;
     const int g = mt / (N / 16), x0 = (mt % (N / 16)) * 16;
-    uint32_t b[oz::S][KS][2];
-    oz::load_b<KS>(b, a.ozb, nt, NTILE);
+    if (!kBOnce) oz::load_b<KS>(b, a.ozb, nt, NTILE);
     int iacc[oz::S][4];
     oz::tile_levels<KS, true>(iacc, b, [&](int k, int ks) {
       return dig + ((k * G + g) * N + ks * 16 + 8 * (mi >> 1) + r8) * RS + x0 + 8 * (mi & 1);
@@ -378,10 +404,12 @@ __device__ __forceinline__ void oz_pencils_tz(const double2 (&xr)[QB][2], double
   __syncthreads();
   const int gq = lane >> 2, t4 = lane & 3, mi = lane >> 3, r8 = lane & 7;
   double* out = reinterpret_cast<double*>(buf);
+  constexpr bool kBOnce = NW % NTILE == 0;  // as in k_planes_oz
+  uint32_t b[oz::S][KS][2];
+  if (kBOnce) oz::load_b<KS>(b, ozb, w % NTILE, NTILE);
   for (int job = w; job < MT * NTILE; job += NW) {
     const int mt = job / NTILE, nt = job % NTILE;
-    uint32_t b[oz::S][KS][2];
-    oz::load_b<KS>(b, ozb, nt, NTILE);
+    if (!kBOnce) oz::load_b<KS>(b, ozb, nt, NTILE);
     int iacc[oz::S][4];
     oz::tile_levels<KS, false>(iacc, b, [&](int k, int ks) {
       return dig + (k * NCOL + mt * 16 + r8 + 8 * (mi & 1)) * RS + ks * 16 + 8 * (mi >> 1);
@@ -393,7 +421,9 @@ __device__ __forceinline__ void oz_pencils_tz(const double2 (&xr)[QB][2], double
       for (int L = 0; L < oz::S; ++L) lv[L] = iacc[L][e];
       const int col = mt * 16 + gq + 8 * (e >> 1), zz = nt * 8 + 2 * t4 + (e & 1);
       const int g = col / TX, x2 = col % TX;
-      out[2 * ((g >> 1) * CS + zz * TX + x2) + (g & 1)] = oz::to_double(oz::combine(lv), oz::out_scale(sD, Eg[g]));
+      // T_xy (already in the buffer) added in the integer domain
+      double& o = out[2 * ((g >> 1) * CS + zz * TX + x2) + (g & 1)];
+      o = oz::add_to_double(oz::combine(lv), o, oz::out_scale(sD, Eg[g]));
     }
   }
   __syncthreads();
@@ -562,6 +592,7 @@ __global__ void __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N
           const T v = q < q_end ? (a.xr ? reinterpret_cast<const T*>(a.xr)[gi] : to_r<R>(a.x[gi])) : T{R(0), R(0)};
           xr[j][c] = v;
           if (!kOz) buf[(2 * j + c) * CS + z * TX + xl] = v;
+          else buf[(2 * j + c) * CS + z * TX + xl] = q < q_end ? txy[gi] : T{R(0), R(0)};
         }
       }
       if (!kOz) __syncthreads();
@@ -588,8 +619,9 @@ __global__ void __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N
       const int q = qb0 + j;
       if (q >= q_end) break;
       const long iu = (long)(2 * q) * nxyz + site, iv = iu + nxyz;
-      const T Tu = cadd(buf[(2 * j) * CS + z * TX + xl], kPrefetch ? tr[j][0] : txy[iu]);
-      const T Tv = cadd(buf[(2 * j + 1) * CS + z * TX + xl], kPrefetch ? tr[j][1] : txy[iv]);
+      // FP64 tensor-core path: T_z + T_xy already summed (integer domain) in the buffer
+      const T Tu = kOz ? buf[(2 * j) * CS + z * TX + xl] : cadd(buf[(2 * j) * CS + z * TX + xl], kPrefetch ? tr[j][0] : txy[iu]);
+      const T Tv = kOz ? buf[(2 * j + 1) * CS + z * TX + xl] : cadd(buf[(2 * j + 1) * CS + z * TX + xl], kPrefetch ? tr[j][1] : txy[iv]);
       if (MODE == M_ENERGY) {
         const double2 v = a.x[iv];
         const double2 tv = to_d(Tv);

@@ -122,6 +122,21 @@ __device__ __forceinline__ double to_double(long long T, int sc) {
   return __longlong_as_double((long long)(sign | ((unsigned long long)ex << 52) | (mant & 0xFFFFFFFFFFFFFull)));
 }
 
+// (T + Y) * 2^sc rounded to FP64, where y = Y * 2^sc is an FP64 value whose significand,
+// aligned to the scale 2^sc, is truncated to an integer (bits below 2^sc dropped, as in
+// the digit split); integer operations only.  Values of y above 2^(sc + 62) (not met by
+// a kinetic term added to the same operator's other axes) fall back to an FP64 add.
+__device__ __forceinline__ double add_to_double(long long T, double y, int sc) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(y);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  const int sh = ex - 1075 - sc;  // y = m 2^(ex - 1075) = (m 2^sh) 2^sc
+  if (ex == 0x7FF || sh > 8) return to_double(T, sc) + y;
+  const unsigned long long m = ex ? ((b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) : 0ull;
+  const unsigned long long u = sh >= 0 ? (m << sh) : (-sh < 64 ? (m >> -sh) : 0ull);
+  const long long Y = (b >> 63) ? -(long long)u : (long long)u;
+  return to_double(T + Y, sc);
+}
+
 // The same conversion through the FP64 unit (one I2F.F64 and an exponent add), for
 // kernels whose FP64 pipe is otherwise idle; T * 2^sc must be a normal number.
 __device__ __forceinline__ double to_double_hw(long long T, int sc) {

@@ -50,7 +50,8 @@ extern "C" {
 #define LISE_ENOMEM 2     /* footprint above hbm_budget_bytes, or device allocation failed */
 #define LISE_ECUDA 3      /* a CUDA runtime call or kernel launch failed */
 #define LISE_ENONFINITE 4 /* a density or the input state is NaN or infinite */
-#define LISE_ETIMEOUT 5   /* reserved: a bounded device wait ran out (no such wait in this path) */
+#define LISE_ETIMEOUT 5   /* a bounded device wait ran out (the tensor-memory planes kernel's
+                             wait for its MMAs); sticky like LISE_ENONFINITE */
 #define LISE_ESTATE 6     /* call out of order (e.g. lise_step before lise_set_state) */
 
 #define LISE_FP64 0       /* FFTs, H psi, ABM history, densities: all in FP64 */

@@ -199,6 +199,7 @@ int run_planes(lise_ctx* c, const double2* x, const void* xr = nullptr) {
   a.ozb = c->ozb;
   a.oz_sD = c->oz_sD;
   a.n_planes = (long)c->p.n_qp * 2 * c->N;
+  a.err = c->err;
   return timed(c, LISE_KC_PLANES, [&] { return launch_planes(c->N, c->mixed, a, c->stream) ? LISE_ECUDA : LISE_OK; });
 }
 
@@ -310,7 +311,7 @@ int fetch_err(lise_ctx* c) {
     return c->sticky;
   }
   if (h) {
-    c->sticky = LISE_ENONFINITE;
+    c->sticky = (h & 4) ? LISE_ETIMEOUT : LISE_ENONFINITE;
     return c->sticky;
   }
   return LISE_OK;

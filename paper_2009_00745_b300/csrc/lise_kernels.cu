@@ -9,6 +9,7 @@
 
 #include "lise_kernels.cuh"
 #include "lise_ozaki.cuh"
+#include "lise_umma.cuh"
 
 namespace lise {
 
@@ -365,6 +366,187 @@ __global__ void __launch_bounds__(256) k_planes_oz(PlanesArgs a) {
     const double im = oz::to_double_hw(acc64[(2 * pl + 1) * N * N + rem], oz::out_scale(a.oz_sD, Eg[2 * pl + 1]));
     dst[i] = make_double2(re, im);
   }
+}
+
+// T_x + T_y of the FP64 path on the fifth-generation tensor cores (tcgen05), 32^3 lattices.
+// One plane (a state component, N x N complex values) per pass of a persistent block; its
+// exponent groups are the plane's real and imaginary parts.  The digit operand stacks the
+// two axes into M = 128 rows, K = N:
+//   rows g N + y       (g = re/im): the data lines along x  -> T_x x  [g][y][x = column]
+//   rows 2N + g N + x:              the data lines along y  -> T_y x  [g][y = column][x]
+// so one chain of MMAs against the D2 digits (B, N x K) forms both products.  Level L of
+// the digit products (pairs k + l = L) accumulates in tensor-memory columns [L N, L N + N)
+// (exact FP32 integers, as in tile_levels); the levels are read back, combined in 64-bit
+// integers per axis, summed and converted to FP64 once.
+constexpr int kPlanesTcBlocksPerSM = 2;
+template <int N>
+struct TcPlanes {
+  static_assert(N == 32, "two axes x two parts x N lines fill the 128 rows of one MMA only at N = 32");
+  static constexpr int M = 4 * N, K = N;
+  static constexpr int LBO = 128, SBO = (K / 8) * 128;  // core-matrix strides (bytes), K-major
+  static constexpr int A_BYTES = M * K * 2, B_BYTES = N * K * 2;  // one digit of each operand
+  static constexpr int AP = N + 1;                                 // padded row of the 64-bit sums
+  static constexpr size_t acc_bytes = (size_t)2 * 2 * N * AP * 8;
+  static constexpr size_t smem = (size_t)oz::S * (A_BYTES + B_BYTES) + acc_bytes;
+  static constexpr uint32_t TMEM_COLS = 256;  // >= S N, a power of 2
+  // word offset of the core-matrix D2 table behind the mma.sync fragment table
+  static constexpr size_t table_offset = (size_t)oz::S * (N / 8) * (N / 16) * 32 * 2;
+};
+// byte offset of element (row, k) of a K-major core-matrix operand with K = 32
+__device__ __forceinline__ int tc_off(int row, int k) {
+  return (row >> 3) * TcPlanes<32>::SBO + (k >> 3) * TcPlanes<32>::LBO + (row & 7) * 16 + (k & 7) * 2;
+}
+
+template <int N>
+__global__ void __launch_bounds__(256, kPlanesTcBlocksPerSM) k_planes_tc(PlanesArgs a) {
+  using P = TcPlanes<N>;
+  constexpr int NT = 256, NW = NT / 32, S = oz::S, AP = P::AP;
+  extern __shared__ __align__(16) unsigned char smem_raw[];  // no-swizzle operands: 16-byte alignment
+  unsigned char* sA = smem_raw;                    // [S][M rows][K], core-matrix layout
+  unsigned char* sB = smem_raw + S * P::A_BYTES;   // [S][N][K], core-matrix layout
+  long long* accx = reinterpret_cast<long long*>(sB + S * P::B_BYTES);  // [g][x][y (AP)]
+  long long* accy = accx + 2 * N * AP;                                   // [g][y][x (AP)]
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tslot;
+  __shared__ unsigned ered[NW][2];
+  __shared__ unsigned Eg[2];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+
+  // the D2 digits, once per block (the table is stored in the core-matrix layout)
+  const uint4* tb = reinterpret_cast<const uint4*>(a.ozb + P::table_offset);
+  for (int i = tid; i < S * P::B_BYTES / 16; i += NT) reinterpret_cast<uint4*>(sB)[i] = tb[i];
+  if (tid == 0) um::mbar_init(&mbar, 1);
+  if (w == 0) um::alloc(&tslot, P::TMEM_COLS);
+  um::fence_proxy_async();
+  um::fence_before();
+  __syncthreads();
+  um::fence_after();
+  const uint32_t tmem = tslot;
+  uint32_t parity = 0;
+  bool failed = false;
+
+  // this thread's 2 x 2 block of the plane: an 8 x 8 tile per 16 lanes, two tiles per warp
+  // (lane bits: a = x pair, b = y pair, c = tile); digit stores then hit 32 distinct banks
+  const int la = lane & 3, lb = (lane >> 2) & 3, lc = lane >> 4;
+  const int x0 = 8 * (2 * (w & 1) + lc) + 2 * la, y0 = 8 * (w >> 1) + 2 * lb;
+  constexpr uint32_t idesc = um::idesc_bf16_f32(P::M, N);
+
+  for (long pl = blockIdx.x; pl < a.n_planes; pl += gridDim.x) {
+    const double2* src = (a.xr ? reinterpret_cast<const double2*>(a.xr) : a.x) + pl * N * N;
+    double2 v[2][2];  // [dy][dx]
+    unsigned e0 = 0, e1 = 0;
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+      for (int dx = 0; dx < 2; ++dx) {
+        v[dy][dx] = src[(y0 + dy) * N + x0 + dx];
+        e0 = max(e0, oz::exp_field(v[dy][dx].x));
+        e1 = max(e1, oz::exp_field(v[dy][dx].y));
+      }
+    e0 = oz::warp_max(e0);
+    e1 = oz::warp_max(e1);
+    if (lane == 0) {
+      ered[w][0] = e0;
+      ered[w][1] = e1;
+    }
+    __syncthreads();
+    if (tid < 2) {
+      unsigned m = 0;
+#pragma unroll
+      for (int k = 0; k < NW; ++k) m = max(m, ered[k][tid]);
+      Eg[tid] = m;
+    }
+    __syncthreads();
+    // digits into both row blocks (the lanes of one store cover one core matrix's 32 words:
+    // rows alternate with the tile bit so that the two tiles of a warp use different rows)
+#pragma unroll
+    for (int g = 0; g < 2; ++g) {
+      unsigned short d[2][2][S];
+#pragma unroll
+      for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 2; ++dx) oz::split(g ? v[dy][dx].y : v[dy][dx].x, Eg[g], d[dy][dx]);
+#pragma unroll
+      for (int st = 0; st < 2; ++st) {
+        const int o = st ^ lc;  // which row (dy for T_x, dx for T_y) this store covers
+        const int ox = tc_off(g * N + y0 + o, x0);          // T_x row (g, y), k = x pair
+        const int oy = tc_off(2 * N + g * N + x0 + o, y0);  // T_y row (g, x), k = y pair
+#pragma unroll
+        for (int k = 0; k < S; ++k) {
+          const unsigned px0 = (unsigned)d[0][0][k] | ((unsigned)d[0][1][k] << 16);
+          const unsigned px1 = (unsigned)d[1][0][k] | ((unsigned)d[1][1][k] << 16);
+          const unsigned py0 = (unsigned)d[0][0][k] | ((unsigned)d[1][0][k] << 16);
+          const unsigned py1 = (unsigned)d[0][1][k] | ((unsigned)d[1][1][k] << 16);
+          *reinterpret_cast<unsigned*>(sA + k * P::A_BYTES + ox) = o ? px1 : px0;
+          *reinterpret_cast<unsigned*>(sA + k * P::A_BYTES + oy) = o ? py1 : py0;
+        }
+      }
+    }
+    um::fence_proxy_async();
+    um::fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      um::fence_after();
+      const uint32_t a0 = um::su32(sA), b0 = um::su32(sB);
+#pragma unroll
+      for (int L = 0; L < S; ++L)
+#pragma unroll
+        for (int k = 0; k <= L; ++k)
+#pragma unroll
+          for (int ks = 0; ks < P::K / 16; ++ks)
+            um::mma_bf16(tmem + L * N, um::sdesc(a0 + k * P::A_BYTES + ks * 2 * P::LBO, P::LBO, P::SBO),
+                         um::sdesc(b0 + (L - k) * P::B_BYTES + ks * 2 * P::LBO, P::LBO, P::SBO), idesc,
+                         (k > 0 || ks > 0) ? 1u : 0u);
+      um::commit(&mbar);
+    }
+    const bool ok = um::mbar_wait(&mbar, parity, 1L << 22);
+    parity ^= 1u;
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    um::fence_after();
+    // read back: warp w reads tensor-memory lanes (rows) 32 (w % 4) + lane, columns
+    // 16 (w / 4) .. + 15; rows < 2N are T_x (g, y = row % N), the others T_y (g, x)
+    {
+      const int q = w & 3, c0 = 16 * (w >> 2);
+      const int g = (q & 1), ax = q >> 1;  // N = 32: quarter q = 2 ax + g
+      long long* dst = ax ? accy : accx;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        uint32_t r[S][8];
+#pragma unroll
+        for (int L = 0; L < S; ++L) um::ld8(r[L], tmem + ((uint32_t)(32 * q) << 16) + L * N + c0 + 8 * h);
+        um::wait_ld_deps<S>(r);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          int lv[S];
+#pragma unroll
+          for (int L = 0; L < S; ++L) lv[L] = oz::f2i_exact(__uint_as_float(r[L][j]));
+          dst[(g * N + c0 + 8 * h + j) * AP + lane] = oz::combine(lv);
+        }
+      }
+    }
+    um::fence_before();
+    __syncthreads();
+    // T_xy = T_x + T_y, one rounding; coalesced complex128 stores
+    double2* out = reinterpret_cast<double2*>(a.txy) + pl * N * N;
+    const int s0 = oz::out_scale(a.oz_sD, Eg[0]), s1 = oz::out_scale(a.oz_sD, Eg[1]);
+    for (int i = tid; i < N * N; i += NT) {
+      const int y = i / N, x = i % N;
+      const long long re = accx[(0 * N + x) * AP + y] + accy[(0 * N + y) * AP + x];
+      const long long im = accx[(1 * N + x) * AP + y] + accy[(1 * N + y) * AP + x];
+      out[i] = make_double2(oz::to_double_hw(re, s0), oz::to_double_hw(im, s1));
+    }
+  }
+  if (failed) {
+    if (tid == 0 && a.err) atomicOr(a.err, 4);
+    um::mbar_wait(&mbar, parity ^ 1u, 1L << 22);  // let the MMAs in flight finish, bounded
+  }
+  um::fence_before();
+  __syncthreads();
+  um::fence_after();
+  if (w == 0) um::dealloc(tmem, P::TMEM_COLS);
 }
 
 // T_z x on the tensor cores for one pencils batch (FP64 path, N % 16 == 0):
@@ -1102,10 +1284,32 @@ static int planes_oz_n(const PlanesArgs& a, cudaStream_t s) {
   return cudaGetLastError() == cudaSuccess ? 0 : 3;
 }
 
+// persistent: kPlanesTcBlocksPerSM blocks per SM, each walking the planes
+template <int N>
+static int planes_tc_n(const PlanesArgs& a, cudaStream_t s) {
+  using P = TcPlanes<N>;
+  auto kern = k_planes_tc<N>;
+  static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P::smem);
+  if (attr != cudaSuccess) return 3;
+  if (a.n_planes <= 0) return 0;
+  if (!a.ozb) return 1;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 3;
+  const long blocks = std::min<long>(a.n_planes, (long)kPlanesTcBlocksPerSM * sms);
+  kern<<<(unsigned)blocks, 256, P::smem, s>>>(a);
+  return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}
+
 template <typename R, int N>
 static int planes_n(const PlanesArgs& a, cudaStream_t s) {
   using T = typename Cx<R>::T;
-  if constexpr (pencil_oz<R, N>()) return planes_oz_n<N>(a, s);
+  if constexpr (pencil_oz<R, N>()) {
+    if constexpr (N == 32)
+      return planes_tc_n<N>(a, s);
+    else
+      return planes_oz_n<N>(a, s);
+  }
   constexpr int PB = PlanesPB<N>::v;
   constexpr int NT = 256;
   const size_t smem = (size_t)PB * N * (N + 1) * sizeof(T) + N * sizeof(T) + N * sizeof(R);
@@ -1309,7 +1513,10 @@ int launch_density(const PointwiseArgs& a, cudaStream_t s) {
 
 bool ozaki_path(int N, int mixed) { return !mixed && N % 16 == 0 && supported_n(N); }
 
-size_t ozaki_table_words(int N) { return (size_t)oz::S * (N / 8) * (N / 16) * 32 * 2; }
+size_t ozaki_table_words(int N) {
+  // mma.sync fragments, then (N = 32: the tcgen05 planes kernel) the core-matrix table
+  return (size_t)oz::S * (N / 8) * (N / 16) * 32 * 2 + (N == 32 ? (size_t)oz::S * N * N / 2 : 0);
+}
 
 // D2[n][k] = (1/N) sum_j (alpha/2) k_j^2 cos(k_j (n - k) a), k_j = 2 pi (j or j - N) / (N a),
 // as balanced base-256 digits of I_D = round(D2 2^-sD) (|I_D| <= 2^55), laid out as the
@@ -1362,6 +1569,16 @@ int ozaki_table(int N, double a, double alpha, uint32_t* out) {
           o[0] = bf16(D(l, n, k0)) | (bf16(D(l, n, k0 + 1)) << 16);
           o[1] = bf16(D(l, n, k0 + 8)) | (bf16(D(l, n, k0 + 9)) << 16);
         }
+  if (N == 32) {
+    // [digit][n][k] in the K-major core-matrix layout of the tcgen05 operands (bf16 pairs)
+    uint32_t* t = out + (size_t)oz::S * NTL * KS * 32 * 2;
+    for (int l = 0; l < oz::S; ++l)
+      for (int n = 0; n < N; ++n)
+        for (int k = 0; k < N; k += 2) {
+          const size_t byte = (size_t)l * N * N * 2 + (size_t)(n / 8) * (N / 8) * 128 + (k / 8) * 128 + (n % 8) * 16 + (k % 8) * 2;
+          t[byte / 4] = bf16(D(l, n, k)) | (bf16(D(l, n, k + 1)) << 16);
+        }
+  }
   return sD;
 }
 

@@ -76,6 +76,7 @@ struct PlanesArgs {
   const uint32_t* ozb;    // FP64 tensor-core path: digit fragments of D2 (lise_ozaki.cuh)
   int oz_sD;
   long n_planes;
+  int* err;               // device error word: bit 4 set when a bounded wait ran out
 };
 
 struct ReduceArgs {

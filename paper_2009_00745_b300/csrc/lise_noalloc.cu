@@ -191,6 +191,7 @@ extern "C" int lise_rhs_noalloc(const lise_params* p, const double* psi_dev, dou
   pa.ozb = ozb;
   pa.oz_sD = oz_sD;
   pa.n_planes = (long)p->n_qp * 2 * N;
+  pa.err = err;
   if (launch_planes(N, mixed, pa, s)) return LISE_ECUDA;
   PencilArgs ka;
   std::memset(&ka, 0, sizeof(ka));
@@ -219,5 +220,5 @@ extern "C" int lise_rhs_noalloc(const lise_params* p, const double* psi_dev, dou
   int h_err = 0;
   if (cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return LISE_ECUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return LISE_ECUDA;
-  return h_err ? LISE_ENONFINITE : LISE_OK;
+  return h_err ? ((h_err & 4) ? LISE_ETIMEOUT : LISE_ENONFINITE) : LISE_OK;
 }

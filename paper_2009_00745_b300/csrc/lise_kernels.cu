@@ -431,18 +431,29 @@ __global__ void __launch_bounds__(256, kPlanesTcBlocksPerSM) k_planes_tc(PlanesA
   const int x0 = 8 * (2 * (w & 1) + lc) + 2 * la, y0 = 8 * (w >> 1) + 2 * lb;
   constexpr uint32_t idesc = um::idesc_bf16_f32(P::M, N);
 
+  const double2* src0 = a.xr ? reinterpret_cast<const double2*>(a.xr) : a.x;
+  // this thread's values of the block's next plane, loaded one pass ahead
+  double2 vn[2][2];
+  auto load_plane = [&](long pl) {
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+      for (int dx = 0; dx < 2; ++dx)
+        vn[dy][dx] = pl < a.n_planes ? src0[pl * N * N + (y0 + dy) * N + x0 + dx] : make_double2(0.0, 0.0);
+  };
+  load_plane(blockIdx.x);
   for (long pl = blockIdx.x; pl < a.n_planes; pl += gridDim.x) {
-    const double2* src = (a.xr ? reinterpret_cast<const double2*>(a.xr) : a.x) + pl * N * N;
     double2 v[2][2];  // [dy][dx]
     unsigned e0 = 0, e1 = 0;
 #pragma unroll
     for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
       for (int dx = 0; dx < 2; ++dx) {
-        v[dy][dx] = src[(y0 + dy) * N + x0 + dx];
+        v[dy][dx] = vn[dy][dx];
         e0 = max(e0, oz::exp_field(v[dy][dx].x));
         e1 = max(e1, oz::exp_field(v[dy][dx].y));
       }
+    load_plane(pl + gridDim.x);  // in flight through this pass's digit products
     e0 = oz::warp_max(e0);
     e1 = oz::warp_max(e1);
     if (lane == 0) {

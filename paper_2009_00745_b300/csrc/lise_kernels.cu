@@ -442,6 +442,18 @@ __global__ void __launch_bounds__(256, kPlanesTcBlocksPerSM) k_planes_tc(PlanesA
         vn[dy][dx] = pl < a.n_planes ? src0[pl * N * N + (y0 + dy) * N + x0 + dx] : make_double2(0.0, 0.0);
   };
   load_plane(blockIdx.x);
+  // T_xy = T_x + T_y of a finished plane, one rounding; coalesced complex128 stores
+  auto final_pass = [&](long pp, int s0, int s1) {
+    double2* out = reinterpret_cast<double2*>(a.txy) + pp * N * N;
+    for (int i = tid; i < N * N; i += NT) {
+      const int y = i / N, x = i % N;
+      const long long re = accx[(0 * N + x) * AP + y] + accy[(0 * N + y) * AP + x];
+      const long long im = accx[(1 * N + x) * AP + y] + accy[(1 * N + y) * AP + x];
+      out[i] = make_double2(oz::to_double_hw(re, s0), oz::to_double_hw(im, s1));
+    }
+  };
+  long prev = -1;  // the plane whose sums wait in accx/accy, and their output scales
+  int ps0 = 0, ps1 = 0;
   for (long pl = blockIdx.x; pl < a.n_planes; pl += gridDim.x) {
     double2 v[2][2];  // [dy][dx]
     unsigned e0 = 0, e1 = 0;
@@ -510,9 +522,11 @@ __global__ void __launch_bounds__(256, kPlanesTcBlocksPerSM) k_planes_tc(PlanesA
                          (k > 0 || ks > 0) ? 1u : 0u);
       um::commit(&mbar);
     }
+    // the previous plane's T_xy while this plane's MMAs run
+    if (prev >= 0) final_pass(prev, ps0, ps1);
     const bool ok = um::mbar_wait(&mbar, parity, 1L << 22);
     parity ^= 1u;
-    if (__syncthreads_or(!ok)) {
+    if (__syncthreads_or(!ok)) {  // (also: every thread is done with the sums of the previous plane)
       failed = true;
       break;
     }
@@ -531,24 +545,21 @@ __global__ void __launch_bounds__(256, kPlanesTcBlocksPerSM) k_planes_tc(PlanesA
         um::wait_ld_deps<S>(r);
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-          int lv[S];
+          unsigned lb[S];
 #pragma unroll
-          for (int L = 0; L < S; ++L) lv[L] = oz::f2i_exact(__uint_as_float(r[L][j]));
-          dst[(g * N + c0 + 8 * h + j) * AP + lane] = oz::combine(lv);
+          for (int L = 0; L < S; ++L) lb[L] = __float_as_uint(__uint_as_float(r[L][j]) + 12582912.0f);
+          dst[(g * N + c0 + 8 * h + j) * AP + lane] = oz::combine_biased(lb);
         }
       }
     }
-    um::fence_before();
+    um::fence_before();  // (the next pass's first barrier orders these reads before its MMAs)
+    prev = pl;
+    ps0 = oz::out_scale(a.oz_sD, Eg[0]);
+    ps1 = oz::out_scale(a.oz_sD, Eg[1]);
+  }
+  if (!failed && prev >= 0) {
     __syncthreads();
-    // T_xy = T_x + T_y, one rounding; coalesced complex128 stores
-    double2* out = reinterpret_cast<double2*>(a.txy) + pl * N * N;
-    const int s0 = oz::out_scale(a.oz_sD, Eg[0]), s1 = oz::out_scale(a.oz_sD, Eg[1]);
-    for (int i = tid; i < N * N; i += NT) {
-      const int y = i / N, x = i % N;
-      const long long re = accx[(0 * N + x) * AP + y] + accy[(0 * N + y) * AP + x];
-      const long long im = accx[(1 * N + x) * AP + y] + accy[(1 * N + y) * AP + x];
-      out[i] = make_double2(oz::to_double_hw(re, s0), oz::to_double_hw(im, s1));
-    }
+    final_pass(prev, ps0, ps1);
   }
   if (failed) {
     if (tid == 0 && a.err) atomicOr(a.err, 4);

@@ -103,6 +103,18 @@ __device__ __forceinline__ long long combine(const int i[S]) {
   return ((long long)h1 << 32) + ((long long)h2 << 16) + (long long)h3 + (long long)(i[6] >> 8);
 }
 
+// combine() from the FP32 bit patterns of (level + 1.5 * 2^23), i.e. before f2i_exact's
+// subtraction: the bias cancels in 32-bit wrap-around arithmetic (each pair's true value
+// 256 i_k + i_{k+1} fits in 31 bits), leaving one subtraction for the last level.
+__device__ __forceinline__ long long combine_biased(const unsigned b[S]) {
+  constexpr unsigned kM = 0x4B400000u, kM257 = 257u * kM;
+  const int h1 = (int)(b[0] * 256u + b[1] - kM257);
+  const int h2 = (int)(b[2] * 256u + b[3] - kM257);
+  const int h3 = (int)(b[4] * 256u + b[5] - kM257);
+  const int i6 = (int)(b[6] - kM);
+  return ((long long)h1 << 32) + ((long long)h2 << 16) + (long long)h3 + (long long)(i6 >> 8);
+}
+
 // T * 2^sc rounded to FP64 (nearest even), integer operations only.
 __device__ __forceinline__ double to_double(long long T, int sc) {
   if (T == 0) return 0.0;

@@ -654,7 +654,7 @@ __host__ __device__ constexpr int pencil_smem_bytes() {
 }
 
 template <typename R, int N, int TX, int QB, int MODE>
-__global__ void __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N * TX == 256 ? 2 : ((sizeof(R) == 8 && N * TX == 128) ? 7 : 1)) k_pencils(PencilArgs a) {
+__global__ void __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N * TX == 256 ? 2 : ((sizeof(R) == 8 && N * TX == 128) ? 7 : ((sizeof(R) == 8 && N * TX == 192) ? 3 : 1))) k_pencils(PencilArgs a) {
   using T = typename Cx<R>::T;
   constexpr int NT = N * TX;
   // one component block [z][x] in shared memory; for 8-byte elements the blocks are

@@ -76,13 +76,13 @@ def algorithmic_per_qp_site(N, mixed):
 
     FP64 path on lattices with N % 16 == 0: the kinetic operator runs on the
     bf16 tensor cores (exact digit products, 28 digit pairs, K = N per axis),
-    so "flops" of planes are its bf16 tensor flops and "flops" of pencils its
-    FP64 flops (an FMA counts 2), as written in the kernels:
-      corrector  per real: T_z + T_xy 1, BdG 3 FMA, y_{n+1} 1 FMA, p - c 1 FMA  -> 11
+    so "flops" of planes are its bf16 tensor flops and "flops" of pencils the
+    FP64 flops its kernels execute (an FMA counts 2; work done exactly in
+    integers -- T_z + T_xy, the derivative sums of Eqs. p, c -- is not counted):
+      corrector  per real: BdG 3 FMA, y_{n+1} 1 FMA, p - c 1 FMA               -> 10
                  densities 3 x 2 FMA per (state, site)                          -> 12
-      deriv/pred per real: T_z + T_xy 1, BdG 3 FMA, Y 1 + 1 FMA, R 1, Q 2 FMA,
-                 m 1 + 1 FMA (the derivative sums of Y and R are exact integer
-                 sums, no FP64 instruction)                                     -> 18
+      deriv/pred per real: BdG 3 FMA, P = hf + h/48 sp 1 + 2 FMA, Q 1 FMA,
+                 m 1 FMA                                                        -> 15
                  densities                                                      -> 12
     per (state, site): 2 components x 2 reals."""
     L = log2(N)
@@ -110,7 +110,7 @@ def algorithmic_per_qp_site(N, mixed):
     if tensor:
         mma = 2 * 2 * N * 28 * 2          # bf16 flops per (state, site) and axis: 2 comps x re/im x K x pairs
         out["planes"].update({"flops": 2 * 2 * mma, "kind": "bf16 tensor"})
-        out["pencils"].update({"flops": 4 * 11 + 12 + 4 * 18 + 12, "kind": "fp64", "tensor_flops": 2 * mma})
+        out["pencils"].update({"flops": 4 * 10 + 12 + 4 * 15 + 12, "kind": "fp64", "tensor_flops": 2 * mma})
     return out
 
 

@@ -81,8 +81,8 @@ def algorithmic_per_qp_site(N, mixed):
     integers -- T_z + T_xy, the derivative sums of Eqs. p, c -- is not counted):
       corrector  per real: BdG 3 FMA, y_{n+1} 1 FMA, p - c 1 FMA               -> 10
                  densities 3 x 2 FMA per (state, site)                          -> 12
-      deriv/pred per real: BdG 3 FMA, P = hf + h/48 sp 1 + 2 FMA, Q 1 FMA,
-                 m 1 FMA                                                        -> 15
+      deriv/pred per real: BdG 3 FMA, P = hf + h/48 sp 1 + 1 FMA (the halving of
+                 hf is an exponent decrement), Q 1 FMA, m 1 FMA                 -> 13
                  densities                                                      -> 12
     per (state, site): 2 components x 2 reals."""
     L = log2(N)
@@ -110,7 +110,7 @@ def algorithmic_per_qp_site(N, mixed):
     if tensor:
         mma = 2 * 2 * N * 28 * 2          # bf16 flops per (state, site) and axis: 2 comps x re/im x K x pairs
         out["planes"].update({"flops": 2 * 2 * mma, "kind": "bf16 tensor"})
-        out["pencils"].update({"flops": 4 * 10 + 12 + 4 * 15 + 12, "kind": "fp64", "tensor_flops": 2 * mma})
+        out["pencils"].update({"flops": 4 * 10 + 12 + 4 * 13 + 12, "kind": "fp64", "tensor_flops": 2 * mma})
     return out
 
 

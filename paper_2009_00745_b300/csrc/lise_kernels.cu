@@ -112,6 +112,15 @@ __device__ __forceinline__ void pred_sums(double f, double e0, double e1, double
   sr = oz::to_double(68 * A[0] - 102 * A[1] + 68 * A[2] - 17 * A[3], sc);
 }
 
+// v / 2 through an exponent decrement on the integer pipe: exact for normal v above the
+// smallest normal exponent; zero, subnormals and the smallest normal binade are returned
+// unchanged (an absolute difference below 2^-1022), infinities and NaN as they are.
+__device__ __forceinline__ double half_exp(double v) {
+  const long long b = __double_as_longlong(v);
+  const int e = (int)((b >> 52) & 0x7FF);
+  return (e > 1 && e < 0x7FF) ? __longlong_as_double(b - (1ll << 52)) : v;
+}
+
 // sn += |v|^2 ; nu += u conj(v)  (the factor 2 of n = 2 sum |v|^2 is applied where the
 // partial sums are stored; scaling by 2 is exact, so the order does not matter)
 __device__ __forceinline__ void dens_acc(double2 u, double2 v, double& sn, double& sr, double& si) {
@@ -936,8 +945,8 @@ __global__ void __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N
             pred_sums(f.x, e0.x, e1.x, e2.x, spx, srx);
             pred_sums(f.y, e0.y, e1.y, e2.y, spy, sry);
             Rv = T{srx, sry};
-            const double Px = fma(0.5, xv.x, fma(0.5, y0v.x, h48 * spx)),
-                         Py = fma(0.5, xv.y, fma(0.5, y0v.y, h48 * spy));
+            // hf = (y_{n+1} + y_n) / 2 with the halving on the integer pipe
+            const double Px = fma(h48, spx, half_exp(xv.x + y0v.x)), Py = fma(h48, spy, half_exp(xv.y + y0v.y));
             qv = make_double2(fma(-c161h, srx, Px), fma(-c161h, sry, Py));
             mv = T{fma(-c161h, pcv.x, Px), fma(-c161h, pcv.y, Py)};
           } else {

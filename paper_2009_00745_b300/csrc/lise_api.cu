@@ -173,6 +173,7 @@ int timed(lise_ctx* c, int cls, F f) {
 PencilArgs pencil_base(const lise_ctx* c) {
   PencilArgs a;
   std::memset(&a, 0, sizeof(a));
+  a.err = c->err;
   a.txy = c->TXY;
   a.W = c->W;
   a.D = c->Dl;

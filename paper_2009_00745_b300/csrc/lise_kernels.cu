@@ -159,18 +159,6 @@ __device__ __forceinline__ void dens_fold(const DensF& d, double& sn, double& sr
   si += d.i.value();
 }
 
-// Asynchronous global -> shared copies (no register staging).  Each thread copies
-// and later reads only its own elements, so its own wait suffices.
-__device__ __forceinline__ void cp_async(void* smem, const void* gmem, int bytes) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  if (bytes == 16)
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-  else
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_but_last() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
 // Padded-plane tile count per block for the planes kernel.
 template <int N> struct PlanesPB { static constexpr int v = N <= 8 ? 8 : (N <= 16 ? 4 : (N <= 32 ? 2 : 1)); };
@@ -181,7 +169,7 @@ __global__ void __launch_bounds__(NT) k_planes(PlanesArgs a) {
   using T = typename Cx<R>::T;
   constexpr int NP = N + 1;   // padded row stride (conflict-free row and column lines)
   constexpr int PS = N * NP;  // plane stride
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   T* buf = reinterpret_cast<T*>(smem_raw);
   T* tw = buf + PB * PS;
   R* hk = reinterpret_cast<R*>(tw + N);
@@ -246,7 +234,7 @@ __global__ void __launch_bounds__(256) k_planes_oz(PlanesArgs a) {
   // x-adjacent element pairs per thread (two digits per 32-bit shared store) where the 2 NT
   // elements of one pass lie in one plane
   constexpr bool kPair = N * N % (2 * NT) == 0;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned short* dig = reinterpret_cast<unsigned short*>(smem_raw);  // [S][G][N][RS]
   long long* acc64 = reinterpret_cast<long long*>(smem_raw + P::dig_bytes);  // [G][N][N]
   __shared__ unsigned ered[NW][G];
@@ -412,7 +400,7 @@ template <int N>
 __global__ void __launch_bounds__(256, kPlanesTcBlocksPerSM) k_planes_tc(PlanesArgs a) {
   using P = TcPlanes<N>;
   constexpr int NT = 256, NW = NT / 32, S = oz::S, AP = P::AP;
-  extern __shared__ __align__(16) unsigned char smem_raw[];  // no-swizzle operands: 16-byte alignment
+  extern __shared__ __align__(128) unsigned char smem_raw[];  // (no-swizzle operands need 16 bytes)
   unsigned char* sA = smem_raw;                    // [S][M rows][K], core-matrix layout
   unsigned char* sB = smem_raw + S * P::A_BYTES;   // [S][N][K], core-matrix layout
   long long* accx = reinterpret_cast<long long*>(sB + S * P::B_BYTES);  // [g][x][y (AP)]
@@ -646,10 +634,11 @@ __device__ __forceinline__ void oz_pencils_tz(const double2 (&xr)[QB][2], double
 
 // ----------------------------------------------------------------- pencils --
 // Byte offset of the prefetch staging area in the pencils kernel's shared memory
-// (after the FFT buffer, the twiddles and the kinetic factors), 16-byte aligned.
+// (after the FFT buffer, the twiddles and the kinetic factors), 128-byte aligned (the
+// staging arrays are destinations of tensor-map copies).
 template <typename T, int N, int TX, int QB>
 __host__ __device__ constexpr int pencil_stage_offset() {
-  return (((QB * 2 * (N * TX + (sizeof(T) == 8 ? 8 : 0)) + N) * (int)sizeof(T) + N * (int)sizeof(T) / 2) + 15) / 16 * 16;
+  return (((QB * 2 * (N * TX + (sizeof(T) == 8 ? 8 : 0)) + N) * (int)sizeof(T) + N * (int)sizeof(T) / 2) + 127) / 128 * 128;
 }
 // FP64 tensor-core path (lise_ozaki.cuh) on lattices with N % 16 == 0
 template <typename R, int N>
@@ -665,14 +654,14 @@ __host__ __device__ constexpr int pencil_smem_bytes() {
 }
 
 template <typename R, int N, int TX, int QB, int MODE>
-__global__ void __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N * TX == 256 ? 2 : ((sizeof(R) == 8 && N * TX == 128) ? 7 : ((sizeof(R) == 8 && N * TX == 192) ? 3 : 1))) k_pencils(PencilArgs a) {
+__global__ void __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N * TX == 256 ? 2 : ((sizeof(R) == 8 && N * TX == 128) ? 7 : ((sizeof(R) == 8 && N * TX == 192) ? 3 : 1))) k_pencils(const __grid_constant__ PencilArgs a) {
   using T = typename Cx<R>::T;
   constexpr int NT = N * TX;
   // one component block [z][x] in shared memory; for 8-byte elements the blocks are
   // padded by 64 bytes so the four blocks a warp touches fall on different banks
   constexpr int CS = N * TX + (sizeof(T) == 8 ? 8 : 0);
   constexpr int LINES = QB * 2 * TX;   // z-lines per batch
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   T* buf = reinterpret_cast<T*>(smem_raw);  // [QB][2][N][TX]
   T* tw = buf + QB * 2 * CS;
   R* hz = reinterpret_cast<R*>(tw + N);
@@ -726,30 +715,39 @@ __global__ void __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N
   const R r0c = h48 * R(68), r1c = h48 * R(-102), r2c = h48 * R(68), r3c = h48 * R(-17);
   const R c161h = c161_ * h48;
   auto base = [](int l) { return (l / TX) * CS + (l % TX); };
-  // issue the asynchronous copies of one batch's operand and T_xy (own site only)
-  auto prefetch = [&](int qb) {
-#pragma unroll
-    for (int j = 0; j < QB; ++j) {
-      const int q = qb + j;
-      if (q < q_end) {
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          const long gi = (long)(2 * q + c) * nxyz + site;
-          const int si_ = (2 * j + c) * NT + threadIdx.x;
-          if (a.xr)
-            cp_async(reinterpret_cast<T*>(xstage) + si_, reinterpret_cast<const T*>(a.xr) + gi, (int)sizeof(T));
-          else
-            cp_async(xstage + si_, a.x + gi, 16);
-          cp_async(tstage + si_, txy + gi, (int)sizeof(T));
-        }
-      }
-    }
-    cp_async_commit();
-  };
-  // the prefetch pays in the memory-bound mixed path; the FP64 path is FP64-pipe bound and
-  // keeps its registers for occupancy (plain loads)
+  // The prefetch pays in the memory-bound mixed path; the FP64 path is FP64-pipe bound and
+  // keeps its registers for occupancy (plain loads).  Staging by the tensor memory
+  // accelerator: one thread copies the batch's box [2 QB planes][N z][TX x] of the operand
+  // and of T_xy (and, in the corrector, of Q and R) into shared memory; completion on an
+  // mbarrier per staged pair (bounded waits: a wait that runs out sets bit 4 of the error word).
   constexpr bool kPrefetch = sizeof(R) == 4;
-  if (kPrefetch && q_begin < q_end) prefetch(q_begin);
+  __shared__ __align__(8) uint64_t mb_stage[2];  // [0] operand + T_xy, [1] Q + R
+  uint32_t ph_x = 0, ph_q = 0;
+  const uint32_t bytes_x = 2u * QB * NT * ((a.xr ? (uint32_t)sizeof(T) : 16u) + (uint32_t)sizeof(T));
+  const uint32_t bytes_q = 2u * QB * NT * (16u + (uint32_t)sizeof(T));
+  // tensor copies need 128-byte aligned destinations: checked, never assumed (a block whose
+  // staging is misaligned copies nothing and reports through the error word)
+  const bool stage_ok = (um::su32(xstage) & 127u) == 0;
+  auto prefetch = [&](int qb) {
+    if (threadIdx.x == 0 && stage_ok) {
+      um::fence_proxy_async();  // the staging reads of the previous batch before the copies
+      um::mbar_expect_tx(&mb_stage[0], bytes_x);
+      um::tma_load_4d(xstage, &a.tm_x, 2 * x0, y, 0, 2 * qb, &mb_stage[0]);
+      um::tma_load_4d(tstage, &a.tm_t, 2 * x0, y, 0, 2 * qb, &mb_stage[0]);
+    }
+  };
+  auto wait_stage = [&](int k, uint32_t& ph) {
+    if (stage_ok && !um::mbar_wait(&mb_stage[k], ph, 1L << 22) && a.err) atomicOr(a.err, 4);
+    ph ^= 1u;
+  };
+  if constexpr (kPrefetch) {
+    if (!stage_ok && threadIdx.x == 0 && a.err) atomicOr(a.err, 4);
+    if (threadIdx.x == 0) {
+      um::mbar_init(&mb_stage[0], 1);
+      um::mbar_init(&mb_stage[1], 1);
+    }
+    if (q_begin < q_end) prefetch(q_begin);
+  }
   __syncthreads();
 
   for (int qb0 = q_begin; qb0 < q_end; qb0 += QB) {
@@ -759,7 +757,7 @@ __global__ void __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N
     T xr[QB][2];  // the operand in compute precision (FP64 values are reloaded where needed)
     T tr[QB][2];  // T_xy of this batch (prefetch path)
     if constexpr (kPrefetch) {
-      cp_async_wait_all();
+      wait_stage(0, ph_x);
 #pragma unroll
       for (int j = 0; j < QB; ++j) {
         const int q = qb0 + j;
@@ -778,22 +776,13 @@ __global__ void __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N
       }
       __syncthreads();  // also orders the staging reads above before the next batch's copies
       if constexpr (MODE == M_CORRECT) {
-        // this batch's Q and R: committed before the next batch's operand so that
-        // waiting for all but the last group finds them complete
-#pragma unroll
-        for (int j = 0; j < QB; ++j) {
-          const int q = qb0 + j;
-          if (q < q_end) {
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {
-              const long gi = (long)(2 * q + c) * nxyz + site;
-              const int si_ = (2 * j + c) * NT + threadIdx.x;
-              cp_async(qstage + si_, a.q + gi, 16);
-              cp_async(rstage + si_, reinterpret_cast<const T*>(a.r) + gi, (int)sizeof(T));
-            }
-          }
+        // this batch's Q and R (read in the epilogue, after the line transforms)
+        if (threadIdx.x == 0 && stage_ok) {
+          um::fence_proxy_async();
+          um::mbar_expect_tx(&mb_stage[1], bytes_q);
+          um::tma_load_4d(qstage, &a.tm_q, 2 * x0, y, 0, 2 * qb0, &mb_stage[1]);
+          um::tma_load_4d(rstage, &a.tm_r, 2 * x0, y, 0, 2 * qb0, &mb_stage[1]);
         }
-        cp_async_commit();
       }
       // the staging buffers are free again: fetch the next batch while this one computes
       if (qb0 + QB < q_end) prefetch(qb0 + QB);
@@ -821,13 +810,7 @@ __global__ void __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N
       });
       fft_lines<N, +1, R, LINES, NT>(buf, base, TX, tw, Identity());
     }
-    if constexpr (kPrefetch && MODE == M_CORRECT) {
-      // Q, R of this batch (own elements); the next batch's copies may still be in flight
-      if (qb0 + QB < q_end)
-        cp_async_wait_but_last();
-      else
-        cp_async_wait_all();
-    }
+    if constexpr (kPrefetch && MODE == M_CORRECT) wait_stage(1, ph_q);  // Q, R of this batch
 
 #pragma unroll
     for (int j = 0; j < QB; ++j) {
@@ -1384,6 +1367,32 @@ void pencil_qb_set(int N, int mixed, int qb) {
   if (N >= 0 && N <= 64) g_qb_tuned[mixed ? 1 : 0][N].store(qb, std::memory_order_relaxed);
 }
 
+// Tensor map of a state-shaped array [2 n_qp planes][N z][N y][N x] of complex values
+// (complex64, or complex128 when c128) for the pencils kernel's staging boxes
+// [2 QB planes][N z][1 y][TX x]; the innermost dimension counts real words.
+static bool encode_stage_map(CUtensorMap* m, const void* base, bool c128, int N, int n_qp, int TX, int QB) {
+  using Fn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*, const cuuint64_t*,
+                          const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                          CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static const Fn encode = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return (Fn) nullptr;
+    return reinterpret_cast<Fn>(f);
+  }();
+  if (!encode || !base) return false;
+  const cuuint64_t w = c128 ? 8 : 4;
+  const cuuint64_t dims[4] = {(cuuint64_t)2 * N, (cuuint64_t)N, (cuuint64_t)N, (cuuint64_t)2 * n_qp};
+  const cuuint64_t strides[3] = {2 * N * w, 2 * (cuuint64_t)N * N * w, 2 * (cuuint64_t)N * N * N * w};
+  const cuuint32_t box[4] = {(cuuint32_t)(2 * TX), 1, (cuuint32_t)N, (cuuint32_t)(2 * QB)};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  return encode(m, c128 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(base),
+                dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <typename R, int N, int MODE, int QB>
 static int pencils_nmq(const PencilArgs& a, cudaStream_t s) {
   using T = typename Cx<R>::T;
@@ -1396,7 +1405,18 @@ static int pencils_nmq(const PencilArgs& a, cudaStream_t s) {
   if (attr != cudaSuccess) return 3;
   const int n_groups = (a.n_qp + a.qg - 1) / a.qg;
   dim3 grid((N / TX) * N, n_groups);
-  kern<<<grid, N * TX, smem, s>>>(a);
+  if constexpr (sizeof(R) == 4) {
+    // the staged arrays of the FP32 compute precision: tensor maps for this launch
+    PencilArgs b = a;
+    const bool ok = encode_stage_map(&b.tm_x, a.xr ? a.xr : (const void*)a.x, !a.xr, N, a.n_qp, TX, QB) &&
+                    encode_stage_map(&b.tm_t, a.txy, false, N, a.n_qp, TX, QB) &&
+                    (MODE != M_CORRECT || (encode_stage_map(&b.tm_q, a.q, true, N, a.n_qp, TX, QB) &&
+                                           encode_stage_map(&b.tm_r, a.r, false, N, a.n_qp, TX, QB)));
+    if (!ok) return 3;
+    kern<<<grid, N * TX, smem, s>>>(b);
+  } else {
+    kern<<<grid, N * TX, smem, s>>>(a);
+  }
   return cudaGetLastError() == cudaSuccess ? 0 : 3;
 }
 

@@ -13,6 +13,7 @@
 // right-hand side) plus per-group partial sums of the densities
 // n = 2 sum |v|^2 and nu = sum u v^* (Eqs. rho_t, nu_t).
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -65,6 +66,13 @@ struct PencilArgs {
   int dens;               // accumulate density partials of the mode's output state
   const double* eta;      // if non-null: apply H - eta_q (trivial-phase removal), eta per state
   double* eta_part;       // M_ETA output: [state][block] partial sums
+  int* err;               // device error word: bit 4 set when a bounded wait ran out
+  // FP32 compute precision: tensor maps of the batch staging copies (operand, T_xy, and the
+  // corrector's Q and R), written by launch_pencils from the pointers above
+  CUtensorMap tm_x;
+  CUtensorMap tm_t;
+  CUtensorMap tm_q;
+  CUtensorMap tm_r;
 };
 
 struct PlanesArgs {

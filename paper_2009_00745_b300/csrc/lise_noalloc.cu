@@ -202,6 +202,7 @@ extern "C" int lise_rhs_noalloc(const lise_params* p, const double* psi_dev, dou
   ka.tw = tw;
   ka.hz = hz;
   ka.ozb = ozb;
+  ka.err = err;
   ka.oz_sD = oz_sD;
   ka.n_qp = p->n_qp;
   ka.qg = qg;

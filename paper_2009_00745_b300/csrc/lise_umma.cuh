@@ -9,6 +9,7 @@
 // are adjacent along K, the stride byte offset the distance between core matrices adjacent
 // along M (or N).
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -96,6 +97,21 @@ __device__ __forceinline__ void wait_ld_deps(uint32_t (&r)[L][8]) {
   for (int l = 0; l < L; ++l)
     asm volatile("" : "+r"(r[l][0]), "+r"(r[l][1]), "+r"(r[l][2]), "+r"(r[l][3]), "+r"(r[l][4]), "+r"(r[l][5]),
                  "+r"(r[l][6]), "+r"(r[l][7]));
+}
+
+// Tensor memory accelerator: arrive on the mbarrier announcing `bytes` of asynchronous
+// copies; then box copies of a 4-D tensor map (the map lives in kernel parameter space,
+// __grid_constant__) into shared memory (128-byte aligned), completing on that mbarrier.
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(mbar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint64_t* mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(su32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(su32(mbar))
+      : "memory");
 }
 
 }  // namespace um

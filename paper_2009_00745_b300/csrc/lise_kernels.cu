@@ -184,11 +184,22 @@ __global__ void __launch_bounds__(NT) k_planes(PlanesArgs a) {
   const int np = left < PB ? (int)left : PB;
   const double2* src = a.x + plane0 * N * N;
   const T* srcr = a.xr ? reinterpret_cast<const T*>(a.xr) + plane0 * N * N : nullptr;
-  for (int i = threadIdx.x; i < PB * N * N; i += NT) {
-    int pl = i / (N * N), r = i % (N * N);
-    T v = T{R(0), R(0)};
-    if (pl < np) v = srcr ? srcr[i] : to_r_hw<R>(src[i]);
-    buf[pl * PS + (r / N) * NP + (r % N)] = v;
+  // a compile-time count of elements per thread: all of a thread's loads are issued
+  // before the first store (several global loads in flight per thread)
+  constexpr int EPT = (PB * N * N + NT - 1) / NT;
+  T v[EPT];
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) {
+    const int i = threadIdx.x + e * NT;
+    const int pl = i / (N * N);
+    v[e] = T{R(0), R(0)};
+    if (i < PB * N * N && pl < np) v[e] = srcr ? srcr[i] : to_r_hw<R>(src[i]);
+  }
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) {
+    const int i = threadIdx.x + e * NT;
+    const int pl = i / (N * N), r = i % (N * N);
+    if (i < PB * N * N) buf[pl * PS + (r / N) * NP + (r % N)] = v[e];
   }
   __syncthreads();
   auto rows = [](int l) { return (l / N) * PS + (l % N) * NP; };

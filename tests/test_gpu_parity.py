@@ -80,6 +80,23 @@ def test_rhs_mixed_precision_bound():
     assert err > 1e-12  # it is really FP32 arithmetic
 
 
+@pytest.mark.parametrize("N,n_qp", [(8, 5), (12, 7), (20, 3), (32, 3), (64, 1)])
+def test_rhs_mixed_all_lattices(N, n_qp):
+    # the FP32 compute precision on the other lattice families: z-pencil tiles 8 wide (8^3,
+    # 32^3, 64^3) and 4 wide (12^3, 20^3), i.e. both widths of the staged batch boxes, and the
+    # radix plans 2x4, 4x3, 4x5, 4x8, 8x8
+    psi = random_state(N, n_qp, seed=N + 100, kmax=max(1, N // 4))
+    kw = dict(a=0.9, alpha=1.0, beta=-0.5, mu=0.3, g=1.0)
+    rng = np.random.default_rng(2)
+    vs = rng.uniform(-1, 1, (N, N, N))
+    with L.Context(N, n_qp, precision="mixed", v_static=vs, **kw) as ctx:
+        got = ctx.rhs(psi, 0.0)
+    ref = O.rhs(O.Params(N, N, N, n_qp=n_qp, v_static=vs, **kw), psi, 0.0)
+    err = rel(got, ref)
+    assert err < 2e-6, err
+    assert err > 1e-12
+
+
 # ------------------------------------------------------------ full runs ----
 
 def run_gpu(w, steps, precision="fp64"):

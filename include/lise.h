@@ -108,12 +108,13 @@ int lise_set_state(lise_ctx *c, const double *psi, double t0, double dt);
 int lise_set_state_device(lise_ctx *c, const double *psi_dev, double t0, double dt);
 
 /* Pencil-kernel tile autotuning.  The states per batch of the pencils kernel (2 or 4,
- * where the variant fits in shared memory) are chosen per lattice size and precision
+ * where the variant fits in shared memory, and 1 for the FP64 tensor-core kernel of
+ * lattices with N a multiple of 16) are chosen per lattice size and precision
  * by timing the two pencils launches of an ABM step for each candidate, once per
  * process, on the first lise_set_state of that lattice and precision.  The choice
  * does not change any result (bitwise).  lise_pencil_batch returns the batch size in
  * use (the tuned one, else the default; 0 for an unsupported N or precision).
- * lise_set_pencil_batch forces qb (2 or 4; LISE_EINVAL if that variant does not
+ * lise_set_pencil_batch forces qb (1, 2 or 4; LISE_EINVAL if that variant does not
  * exist) or, with qb = 0, clears the choice so that the next lise_set_state tunes. */
 int lise_pencil_batch(int N, int precision);
 int lise_set_pencil_batch(int N, int precision, int qb);

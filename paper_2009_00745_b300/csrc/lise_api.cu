@@ -715,12 +715,13 @@ static int tune_pencils(lise_ctx* c, double t0) {
   if (pencil_qb_get(c->N, c->mixed)) return LISE_OK;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   if (pencil_qb_get(c->N, c->mixed)) return LISE_OK;
-  const int cands[2] = {2, 4};
-  int n_valid = 0;
-  for (int qb : cands) n_valid += pencil_qb_valid(c->N, c->mixed, qb) ? 1 : 0;
+  // candidate states per batch: 2 and 4, and 1 for the FP64 tensor-core kernels
+  // (whose per-state digit groups make one state per batch a valid tile)
+  int cands[3], n_valid = 0;
+  for (int qb : {1, 2, 4})
+    if (pencil_qb_valid(c->N, c->mixed, qb)) cands[n_valid++] = qb;
   if (n_valid < 2) {  // nothing to choose
-    for (int qb : cands)
-      if (pencil_qb_valid(c->N, c->mixed, qb)) pencil_qb_set(c->N, c->mixed, qb);
+    if (n_valid == 1) pencil_qb_set(c->N, c->mixed, cands[0]);
     return LISE_OK;
   }
   // valid potentials and T_xy of the input for representative launches
@@ -758,7 +759,8 @@ static int tune_pencils(lise_ctx* c, double t0) {
   }
   int best = 0, rc = LISE_OK;
   float best_ms = 0.f;
-  for (int qb : cands) {
+  for (int ci = 0; ci < n_valid; ++ci) {
+    const int qb = cands[ci];
     auto run = [&] {
       return launch_pencils(c->N, c->mixed, M_CORRECT, a, c->stream, qb) ||
              launch_pencils(c->N, c->mixed, mode_b, b, c->stream, qb);

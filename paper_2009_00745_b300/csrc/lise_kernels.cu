@@ -1437,6 +1437,8 @@ static int pencils_nm(const PencilArgs& a, cudaStream_t s, int qb) {
   constexpr bool kTunable = MODE == M_RHS || MODE == M_CORRECT || MODE == M_DERIV_PREDICT;
   if constexpr (kTunable) {
     if (qb == 0) qb = pencil_qb_get(N, sizeof(R) == 4);
+    if constexpr (pencil_oz<R, N>())
+      if (qb == 1) return pencils_nmq<R, N, MODE, 1>(a, s);
     if constexpr (qb_fits<R, N, 2>())
       if (qb == 2) return pencils_nmq<R, N, MODE, 2>(a, s);
     if constexpr (qb_fits<R, N, 4>())
@@ -1461,6 +1463,7 @@ static int pencils_n(int mode, const PencilArgs& a, cudaStream_t s, int qb) {
 
 template <typename R, int N>
 static bool qb_valid_n(int qb) {
+  if (qb == 1) return pencil_oz<R, N>();
   if (qb == 2) return qb_fits<R, N, 2>();
   if (qb == 4) return qb_fits<R, N, 4>();
   return false;

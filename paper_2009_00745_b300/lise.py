@@ -127,7 +127,8 @@ def pencil_batch(N, precision="fp64") -> int:
 
 
 def set_pencil_batch(N, precision="fp64", qb=0):
-    """Force the pencils batch size (2 or 4), or qb = 0 to re-tune at the next set_state."""
+    """Force the pencils batch size (1 for the FP64 tensor-core kernels, 2 or 4), or qb = 0 to
+    re-tune at the next set_state."""
     _check(load().lise_set_pencil_batch(int(N), {"fp64": FP64, "mixed": MIXED}[precision], int(qb)),
            "lise_set_pencil_batch")
 

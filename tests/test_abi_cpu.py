@@ -99,3 +99,12 @@ def test_pencil_batch_controls_host_only():
     assert L.pencil_batch(16, "mixed") == 4
     L.set_pencil_batch(16, "mixed", 0)                   # back to the default / next tuning
     assert L.pencil_batch(16, "mixed") in (2, 4)
+    L.set_pencil_batch(32, "fp64", 1)                    # one state per batch: FP64 tensor-core kernel only
+    assert L.pencil_batch(32, "fp64") == 1
+    L.set_pencil_batch(32, "fp64", 0)
+    with pytest.raises(L.LiseError) as e:
+        L.set_pencil_batch(16, "mixed", 1)
+    assert e.value.status == L.EINVAL
+    with pytest.raises(L.LiseError) as e:
+        L.set_pencil_batch(24, "fp64", 1)                # 24 % 16 != 0: FFT kernels
+    assert e.value.status == L.EINVAL

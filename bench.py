@@ -473,6 +473,8 @@ def main():
     ap.add_argument("--batch-budget-gb", type=float, default=200.0)
     ap.add_argument("--batch-max-active", type=int, default=8)
     ap.add_argument("--batch-max-skips", type=int, default=8)
+    ap.add_argument("--pencil-batch", type=int, default=0,
+                    help="force the pencils kernel's states per batch (default: autotuned)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -481,6 +483,9 @@ def main():
     w = Wl.named(args.workload, n_qp=args.n_qp)
     if args.precision:
         w.precision = args.precision
+    if args.pencil_batch and args.impl != "reference":
+        from paper_2009_00745_b300 import lise as L
+        L.set_pencil_batch(w.nx, w.precision, args.pencil_batch)
 
     if args.impl == "reference":
         return run_reference(args, w)

@@ -429,6 +429,25 @@ int or_set_state(or_solver *s, const double complex *psi, double t0, double dt) 
   return 0;
 }
 
+int or_set_history(or_solver *s, const double complex *yn, const double complex *ynm1,
+                   const double complex *d0, const double complex *d1, const double complex *d2,
+                   const double complex *d3, const double complex *pc, double t, double dt) {
+  if (!(dt == dt) || dt == 0.0) return 1;
+  size_t bytes = sizeof(double complex) * s->ns;
+  const double complex *d[4] = {d0, d1, d2, d3};
+  memcpy(s->y0, yn, bytes);
+  memcpy(s->y1, ynm1, bytes);
+  for (int k = 0; k < 4; ++k) memcpy(s->d[k], d[k], bytes);
+  if (pc)
+    memcpy(s->pc, pc, bytes);
+  else
+    memset(s->pc, 0, bytes);
+  s->t = t;
+  s->dt = dt;
+  s->ready = 1;
+  return 0;
+}
+
 void or_gradient(const or_params *p, const double complex *in, int axis, double complex *out) {
   int nx = p->nx, ny = p->ny, nz = p->nz;
   long nt = (long)nx * ny * nz;

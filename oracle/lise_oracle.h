@@ -79,7 +79,11 @@ void or_kinetic(const or_params *p, const double complex *in, double complex *ou
 void or_densities(const or_params *p, const double complex *psi, double *n,
                   double complex *nu);
 
-/* V_ext(r, t) = v_static(r) + A sin(Omega t) (i_z - nz/2) a. */
+/* V_ext(r, t) = v_static(r) + A sin(Omega t) (i_z - nz/2) a (z measured from the box
+ * centre).  Pinned by tests/test_oracle_drive.py: with alpha = beta = g = 0 every site
+ * rotates by the exact phase int (V_ext - mu) dt, which fixes the origin of z, the drive's
+ * form and the times at which the integrator evaluates it (t_{n+1} for both right-hand
+ * sides of an ABM step, t + dt/2 for the series start's corrector Hamiltonian). */
 double or_vext(const or_params *p, int ix, int iy, int iz, double t);
 
 /* W(r) = beta (3 pi^2 n)^(2/3)/2 + (d g_eff/dn) |nu|^2 - mu + V_ext(r, t) (the diagonal
@@ -111,6 +115,13 @@ void or_destroy(or_solver *s);
 int or_set_state(or_solver *s, const double complex *psi, double t0, double dt);
 /* n_steps ABM steps of size dt (must equal the set_state dt). */
 int or_step(or_solver *s, int n_steps);
+/* Loads an ABM history directly instead of running the series start, so that the
+ * steps of Eqs. p, m, c, y can be tested on their own: y_n = yn, y_{n-1} = ynm1,
+ * y'_{n-k} = d[k] (k = 0..3), p_n - c_n = pc (NULL: zero), current time t_n = t,
+ * step dt (non-zero).  Copies every array. */
+int or_set_history(or_solver *s, const double complex *yn, const double complex *ynm1,
+                   const double complex *d0, const double complex *d1, const double complex *d2,
+                   const double complex *d3, const double complex *pc, double t, double dt);
 /* First derivative along axis (0 = x, 1 = y, 2 = z): F^-1[(ik) F f] with the
  * Nyquist coefficient set to zero (Sec. "Discretization", odd derivatives). */
 void or_gradient(const or_params *p, const double complex *in, int axis, double complex *out);

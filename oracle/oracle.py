@@ -47,6 +47,8 @@ def lib():
         L.or_set_state.restype = i
         L.or_step.argtypes = [vp, i]
         L.or_step.restype = i
+        L.or_set_history.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, d, d]
+        L.or_set_history.restype = i
         L.or_get_state.argtypes = [vp, vp]
         L.or_time.argtypes = [vp]
         L.or_time.restype = d
@@ -299,6 +301,17 @@ class Solver:
         rc = lib().or_set_state(self._h, psi.ctypes.data, float(t0), float(dt))
         if rc:
             raise ValueError("oracle set_state failed")
+
+    def set_history(self, yn, ynm1, d, t, dt, pc=None):
+        """Load an ABM history directly (no series start): y_n, y_{n-1}, the four
+        derivatives d = [y'_n, y'_{n-1}, y'_{n-2}, y'_{n-3}], p_n - c_n (None: zero),
+        at time t with step dt."""
+        arrs = [_c128(x, self.p.shape) for x in [yn, ynm1] + list(d)]
+        pcp = None if pc is None else _c128(pc, self.p.shape)
+        rc = lib().or_set_history(self._h, *[a.ctypes.data for a in arrs],
+                                  None if pcp is None else pcp.ctypes.data, float(t), float(dt))
+        if rc:
+            raise ValueError("oracle set_history failed")
 
     def kick(self, chi):
         """Eq. kick on the current state, then a new series start at the current time."""

@@ -15,11 +15,17 @@ e2e          the same metric through the C ABI with host buffers: lise_set_state
              from pinned host memory (including the start procedure), K steps,
              lise_get_state back to pinned host memory and lise_energy.
 roofline     the kernel class with the largest share of device time (per-launch
-             CUDA events): algorithmic flops or bytes per launch (see
-             algorithmic_per_qp_site) over the mean launch time, against the
-             FP64/FP32 unit peak or the measured HBM copy bandwidth; traffic is
-             the DRAM bytes per launch from the committed ncu summary
+             CUDA events).  frac: the fully fused step's algorithmic bytes
+             (FUSED_BYTES per state and site, over the two pencils launches of a
+             step) per launch over the mean launch time, against the measured HBM
+             copy bandwidth; step: the same bytes over the whole step time;
+             fp64_pipe (FP64 path): the FP64 flops the pencils kernel executes
+             against the FP64 FMA peak measured by the library's probe kernel;
+             traffic: DRAM bytes per launch from the committed ncu summary
              (profiles/traffic.json) when it was taken on the current sources.
+pair         the metric's comparison: the driven 48^3 x 4096 workload timed in
+             FP64 and in the mixed path (same K and W), mixed / FP64, and the mixed
+             path's energy against the FP64 trajectory over 100 steps.
 cpu_baseline the FP64 CPU oracle on a bounded sample of the same workload, on the
              host cores (thread count reported).
 clocks       SM clocks and throttle reasons sampled during the timed region.
@@ -48,17 +54,19 @@ METRIC = "qp·site·steps/s, FP64 vs mixed at ≤1e-6 rel energy drift; p50/p99 
 UNIT = "qp·site·steps/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 HBM_FALLBACK_GBS = 6400.0
-# FP64 peak from unit counts and clock: 148 SMs x 2 DFMA/clk x 2 flop x 2.032 GHz
-FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12
-# FP32 peak: 148 SMs x 128 FFMA/clk x 2 flop x 2.032 GHz
-FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
+# Algorithmic HBM bytes per (state, site, step) of a fully fused step (each kinetic
+# operator in one on-chip pass): 15 state-array passes of 32 B in FP64 (the corrector
+# launch reads m, Q, R and writes y_{n+1}, p - c; the derivative/predictor launch reads
+# y_{n+1}, y_n, y'_n..y'_{n-2}, p - c and writes y'_{n+1}, m, Q, R), 448 B with the
+# mixed path's complex64 m and transform intermediates.  Keys: mixed (False/True).
+FUSED_BYTES = {False: 480, True: 448}
 
 
 def log2(n):
     return math.log2(n)
 
 
-def algorithmic_per_qp_site(N, mixed):
+def algorithmic_per_qp_site(N, mixed, strict=False):
     """Algorithmic flops and HBM bytes per (state, site) of each kernel class
     for one ABM step (two right-hand sides), for the kernels as designed:
 
@@ -71,7 +79,7 @@ def algorithmic_per_qp_site(N, mixed):
                p - c; write m, Q, R.
     complex128 = 16 B per component.  The states y and Q are complex128; T_xy,
     m, the y' ring, R and p - c are kept in the compute precision (complex64
-    in the mixed path).
+    in the mixed path; R and p - c complex128 in its strict split).
     FFT convention: 5 n log2 n real flops per complex length-n transform.
 
     FP64 path on lattices with N % 16 == 0: the kinetic operator runs on the
@@ -87,15 +95,16 @@ def algorithmic_per_qp_site(N, mixed):
     per (state, site): 2 components x 2 reals."""
     L = log2(N)
     c16, cr = 16, (8 if mixed else 16)   # complex128 / compute-precision component
+    hr = 16 if (strict or not mixed) else 8  # R and p - c
     tensor = (not mixed) and N % 16 == 0
     planes_bytes = 2 * (cr + cr) + 2 * (c16 + cr)          # operand m, then operand y_{n+1}
-    correct_bytes = 2 * (cr + cr + c16 + cr) + 2 * (c16 + cr)
+    correct_bytes = 2 * (cr + cr + c16 + hr) + 2 * (c16 + hr)
     fft_bdg = 2 * (2 * 5 * L + 4) + 24                     # z fwd+inv + multiply/add, BdG apply
     planes_flops = 2 * 2 * (2 * 2 * 5 * L + 3)              # 2 launches x 2 comps: 2D fwd+inv, multiply
     predict_flops = 92 + 13                                 # Eq. p/m, Q, R, densities of m
     if mixed:
         deriv_bytes = 2 * (c16 + cr) + 2 * cr
-        predict_bytes = 2 * (2 * c16 + 5 * cr) + 2 * (cr + c16 + cr)
+        predict_bytes = 2 * (2 * c16 + 4 * cr + hr) + 2 * (cr + c16 + hr)
         pencils_flops = 2 * fft_bdg + (16 + 13)
         pointwise = {"flops": predict_flops, "bytes": predict_bytes, "launches_per_step": 1}
     else:
@@ -112,14 +121,6 @@ def algorithmic_per_qp_site(N, mixed):
         out["planes"].update({"flops": 2 * 2 * mma, "kind": "bf16 tensor"})
         out["pencils"].update({"flops": 4 * 10 + 12 + 4 * 13 + 12, "kind": "fp64", "tensor_flops": 2 * mma})
     return out
-
-
-def read_tensor_peak():
-    try:
-        with open(PEAKS_FILE) as f:
-            return float(json.load(f)["bf16_tflops_sustained"])
-    except Exception:
-        return 1400.0
 
 
 def read_peaks():
@@ -269,10 +270,11 @@ def run_reference(args, w):
 
 
 def run_drift(args, w):
-    """Mixed vs FP64 on the same workload: K ABM steps each, the energy sampled
-    every --drift-every steps.  Reports max_t |E_mixed(t) - E_FP64(t)| / |E_FP64(t)|
-    (the energy of a truncated set of states is not an invariant, so the FP64
-    trajectory is the reference) and the final relative errors of psi, n, nu."""
+    """Both mixed splits against FP64 on the same workload: K ABM steps each, the
+    energy sampled every --drift-every steps.  Reports, for LISE_MIXED and
+    LISE_MIXED_STRICT, max_t |E_mixed(t) - E_FP64(t)| / |E_FP64(t)| (the energy of a
+    truncated set of states is not an invariant, so the FP64 trajectory is the
+    reference) and the final relative errors of psi, n, nu."""
     import numpy as np
     import torch
     from paper_2009_00745_b300 import lise as L
@@ -284,7 +286,7 @@ def run_drift(args, w):
     w.initial_state(out=psi_host.numpy())
     K, every = args.steps, args.drift_every
     out = {}
-    for prec in ("fp64", "mixed"):
+    for prec in ("fp64", "mixed", "mixed_strict"):
         t0 = time.perf_counter()
         with L.Context.from_workload(w, precision=prec, device=local) as ctx:
             ctx.set_state(psi_host.numpy(), 0.0, w.dt)
@@ -299,18 +301,19 @@ def run_drift(args, w):
             n, nu = ctx.densities()
         out[prec] = {"E": np.array([e[0] for e in E]), "N": np.array([e[1] for e in E]), "psi": psi, "n": n,
                      "nu": nu, "seconds": time.perf_counter() - t0}
-    f, m = out["fp64"], out["mixed"]
+    f = out["fp64"]
     rel = lambda a, b: float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
-    drift = float(np.max(np.abs(m["E"] - f["E"]) / np.abs(f["E"])))
     line = {"mode": "drift", "workload": w.name, "lattice": f"{w.nx}^3", "n_qp": w.n_qp, "steps": K,
             "dt": w.dt, "sample_every": every,
-            "max_rel_energy_dev_mixed_vs_fp64": drift,
-            "rel_err_psi": rel(m["psi"], f["psi"]), "rel_err_n": rel(m["n"], f["n"]),
-            "rel_err_nu": rel(m["nu"], f["nu"]),
             "fp64_energy_change": float(abs(f["E"][-1] - f["E"][0]) / abs(f["E"][0])),
-            "max_rel_N_dev_mixed_vs_fp64": float(np.max(np.abs(m["N"] - f["N"]) / np.abs(f["N"]))),
             "fp64_N_change": float(abs(f["N"][-1] - f["N"][0]) / abs(f["N"][0])),
-            "seconds": {"fp64": f["seconds"], "mixed": m["seconds"]}}
+            "seconds": {k: v["seconds"] for k, v in out.items()}}
+    for prec in ("mixed", "mixed_strict"):
+        m = out[prec]
+        line[prec] = {"max_rel_energy_dev_vs_fp64": float(np.max(np.abs(m["E"] - f["E"]) / np.abs(f["E"]))),
+                      "rel_err_psi": rel(m["psi"], f["psi"]), "rel_err_n": rel(m["n"], f["n"]),
+                      "rel_err_nu": rel(m["nu"], f["nu"]),
+                      "max_rel_N_dev_vs_fp64": float(np.max(np.abs(m["N"] - f["N"]) / np.abs(f["N"])))}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -441,7 +444,162 @@ def config_of(w, args):
     return {"workload": w.name, "lattice": f"{w.nx}^3", "n_qp": w.n_qp, "dt": w.dt,
             "precision": w.precision, "steps_in_workload": w.steps,
             "l2": "inputs larger than L2 (state + ABM history %.1f GB, no flush)" % (
-                (10 * 16 if w.precision == "fp64" else 3 * 16 + 7 * 8) * w.n_qp * 2 * w.nxyz / 1e9)}
+                {"fp64": 10 * 16, "mixed": 3 * 16 + 7 * 8, "mixed_strict": 5 * 16 + 5 * 8}[w.precision]
+                * w.n_qp * 2 * w.nxyz / 1e9)}
+
+
+def roofline(w, prof, ms_per_step, fp64_peak):
+    """Roofline of the dominant kernel class from the live per-launch event times.
+
+    frac: FP64 path, the fully fused byte model (FUSED_BYTES: 480 B per (state, site,
+    step)) attributed to the two pencils launches of a step (the fused step's two kernels),
+    per launch, over the mean launch time, against the measured HBM copy bandwidth; mixed
+    path (whose step also has a streaming predictor launch), the kernel's own bytes as
+    designed.  step: the fused model's bytes (480 or 448 B) over the whole step time.
+    design: the kernel's own traffic as designed (algorithmic_per_qp_site), for comparison
+    with the ncu traffic.  fp64_pipe (FP64 path): the FP64 flops the pencils kernel
+    executes over its launch time, against the measured FP64 FMA peak."""
+    mixed = w.precision != "fp64"
+    alg = algorithmic_per_qp_site(w.nx, mixed, strict=w.precision == "mixed_strict")
+    dom = max((k for k in ("planes", "pencils", "pointwise") if alg[k]["launches_per_step"]),
+              key=lambda k: prof[k][1])
+    launches, tot_ms = prof[dom]
+    per_launch_ms = tot_ms / max(launches, 1)
+    qp_sites = float(w.n_qp) * w.nxyz
+    hbm_peak, hbm_src = read_peaks()
+    a = alg[dom]
+    design_bytes = a["bytes"] * qp_sites / a["launches_per_step"]
+    fused = FUSED_BYTES[mixed]
+    if dom == "pencils" and not mixed:
+        # the FP64 pencils launches are the fused step's two kernels (the predictor is in the
+        # derivative launch's epilogue); only the in-plane kinetic part runs outside them
+        bytes_per_launch = fused * qp_sites / 2
+        model = "%d B per (state, site, step) fully fused, over 2 pencils launches per step" % fused
+    else:
+        # the mixed path splits the step over pencils, a streaming predictor and the in-plane
+        # kernel: each kernel against its own bytes as designed; the fused model is `step`
+        bytes_per_launch = design_bytes
+        model = "the kernel's own bytes as designed (algorithmic_per_qp_site)"
+    gbs = bytes_per_launch / (per_launch_ms / 1e3) / 1e9
+    step_gbs = fused * qp_sites / (ms_per_step / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+            "peak_source": hbm_src + " (MEASURED_PEAKS.json hbm_gbs)", "kernel": dom,
+            "traffic": recorded_traffic(w.name, dom), "launch_ms": per_launch_ms,
+            "algorithmic_bytes_per_launch": bytes_per_launch, "byte_model": model,
+            "step": {"achieved": step_gbs, "frac": step_gbs / hbm_peak, "bytes_per_step": fused * qp_sites},
+            "design_bytes_per_launch": design_bytes,
+            "kernel_share": {k: v[1] / max(sum(x[1] for x in prof.values()), 1e-30) for k, v in prof.items()}}
+    if not mixed and dom == "pencils" and fp64_peak:
+        tflops = a["flops"] * qp_sites / a["launches_per_step"] / (per_launch_ms / 1e3) / 1e12
+        roof["fp64_pipe"] = {"achieved_tflops": tflops, "peak_tflops": fp64_peak, "frac": tflops / fp64_peak,
+                             "peak_source": "measured (lise_measure_fp64_peak, FMA chains)",
+                             "flops_per_launch": a["flops"] * qp_sites / a["launches_per_step"]}
+    return roof
+
+
+def measure(L, w, psi_dev, args, local, stream, drift_steps=0, drift_every=25, clocks=True, barrier=None):
+    """Device throughput of w (CUDA events on the context stream around K profiled steps after
+    W warm-up steps), plus, with drift_steps, the energy sampled at fixed step counts of one
+    evolution (0, then every drift_every steps up to drift_steps; the timed steps are part of
+    it).  Returns a dict; the context is freed."""
+    ctx = L.Context.from_workload(w, device=local, stream=stream.cuda_stream)
+    ctx.set_state(psi_dev, 0.0, w.dt)
+    done, E = 0, []
+    sample_at = set(range(0, drift_steps + 1, drift_every)) if drift_steps else set()
+
+    def advance(k):
+        nonlocal done
+        while k > 0:
+            nxt = min([s for s in sample_at if s > done] + [done + k])
+            ctx.step(nxt - done)
+            k -= nxt - done
+            done = nxt
+            if done in sample_at:
+                E.append((done, ctx.energy()[0]))
+
+    if 0 in sample_at:
+        E.append((0, ctx.energy()[0]))
+    advance(args.warmup)
+    ctx.sync()
+    sampler = ClockSampler(local) if clocks else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.4)
+    if barrier:
+        barrier()
+    torch_sync()
+    ctx.profile(True)
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx.step(args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    torch_sync()
+    if barrier:
+        barrier()
+    clk = sampler.stop() if sampler else None
+    ms = e0.elapsed_time(e1)
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    done += args.steps
+    if done in sample_at:
+        E.append((done, ctx.energy()[0]))
+    if drift_steps > done:
+        advance(drift_steps - done)
+    E_end, N_end = ctx.energy()
+    ctx.close()
+    return {"ms": ms, "prof": prof, "clocks": clk, "E": E, "E_end": E_end, "N_end": N_end,
+            "units": float(w.n_qp) * w.nxyz * args.steps}
+
+
+def torch_sync():
+    import torch
+    torch.cuda.synchronize()
+
+
+def upload_state(w, local):
+    import torch
+    psi_host = torch.empty((w.n_qp, 2, w.nz, w.ny, w.nx), dtype=torch.complex128, pin_memory=True)
+    w.initial_state(out=psi_host.numpy())
+    psi_dev = psi_host.to(f"cuda:{local}")
+    torch.cuda.synchronize()
+    return psi_host, psi_dev
+
+
+def run_pair(L, args, local, stream, fp64_peak):
+    """The metric's comparison: one workload in both precisions (default: the driven 48^3
+    lattice with 4096 states), same K and W, each timed like the headline, and the mixed
+    path's energy against the FP64 trajectory over --pair-drift-steps steps."""
+    from paper_2009_00745_b300 import workloads as Wl
+    import torch
+    w = Wl.named(args.pair_workload)
+    psi_host, psi_dev = upload_state(w, local)
+    del psi_host
+    out = {"workload": w.name, "lattice": f"{w.nx}^3", "n_qp": w.n_qp, "steps": args.steps,
+           "warmup": args.warmup, "drift_steps": args.pair_drift_steps}
+    res = {}
+    for prec in ("fp64", "mixed"):
+        w.precision = prec
+        r = measure(L, w, psi_dev, args, local, stream, drift_steps=args.pair_drift_steps,
+                    drift_every=args.pair_drift_every)
+        res[prec] = r
+        out[prec] = {"value": r["units"] / (r["ms"] / 1e3), "ms_per_step": r["ms"] / args.steps,
+                     "roofline": roofline(w, r["prof"], r["ms"] / args.steps, fp64_peak), "clocks": r["clocks"],
+                     "gpu_launches": int(sum(v[0] for v in r["prof"].values())),
+                     "tuned": {"pencils_states_per_batch": L.pencil_batch(w.nx, prec)}}
+        torch.cuda.empty_cache()
+    del psi_dev
+    torch.cuda.empty_cache()
+    f, m = res["fp64"], res["mixed"]
+    ef, em = dict(f["E"]), dict(m["E"])
+    common = sorted(set(ef) & set(em))
+    dev = max(abs(em[k] - ef[k]) / abs(ef[k]) for k in common) if common else None
+    out["mixed_over_fp64"] = out["mixed"]["value"] / out["fp64"]["value"]
+    out["energy_drift"] = {"max_rel_dev_mixed_vs_fp64": dev, "samples_at_steps": common,
+                           "criterion": 1e-6, "fp64_energy": [ef[k] for k in common],
+                           "note": "energy of a truncated state set is not conserved: the FP64 trajectory is the reference"}
+    return out
 
 
 def main():
@@ -450,12 +608,16 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="trap32_vortex_fp64")
-    ap.add_argument("--precision", default=None, choices=[None, "fp64", "mixed"])
+    ap.add_argument("--precision", default=None, choices=[None, "fp64", "mixed", "mixed_strict"])
     ap.add_argument("--n-qp", type=int, default=None, help="override the workload's state count")
     ap.add_argument("--impl", default="lise", choices=["lise", "reference"])
     ap.add_argument("--ref-states", type=int, default=32)
     ap.add_argument("--cpu-baseline-states", type=int, default=32)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--pair-workload", default="drive48_mixed",
+                    help="workload timed in both precisions for the 'pair' object ('' to skip)")
+    ap.add_argument("--pair-drift-steps", type=int, default=100)
+    ap.add_argument("--pair-drift-every", type=int, default=25)
     ap.add_argument("--drift", action="store_true",
                     help="compare mixed with FP64 over --steps steps instead of timing")
     ap.add_argument("--drift-every", type=int, default=50)
@@ -496,7 +658,6 @@ def main():
     if args.batch:
         return run_batch(args)
 
-    import numpy as np
     import torch
     from paper_2009_00745_b300 import lise as L
 
@@ -506,81 +667,20 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
     stream = torch.cuda.Stream()
-    mixed = w.precision == "mixed"
+    mixed = w.precision != "fp64"
+    fp64_peak = L.measure_fp64_peak(local)
 
     # initial state built on the host, uploaded once (not timed for `value`)
-    psi_host = torch.empty((w.n_qp, 2, w.nz, w.ny, w.nx), dtype=torch.complex128, pin_memory=True)
-    w.initial_state(out=psi_host.numpy())
-    psi_dev = psi_host.to(f"cuda:{local}")
-    torch.cuda.synchronize()
+    psi_host, psi_dev = upload_state(w, local)
 
-    ctx = L.Context.from_workload(w, device=local, stream=stream.cuda_stream)
-    ctx.set_state(psi_dev, 0.0, w.dt)
-    ctx.step(args.warmup)
-    ctx.sync()
-
-    # ---- timed region: K steps, device events on the context stream
-    sampler = ClockSampler(local)
-    sampler.start()
-    time.sleep(0.4)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    ctx.profile(True)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    ctx.step(args.steps)
-    e1.record(stream)
-    e1.synchronize()
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    clocks = sampler.stop()
-    ms = e0.elapsed_time(e1)
-    prof = ctx.profile_read()
-    ctx.profile(False)
-    E_dev, N_dev = ctx.energy()
-    units = float(w.n_qp) * w.nxyz * args.steps
-    value, ms = whole_job_value(ms, units, world, device=f"cuda:{local}")
-    ctx.close()
+    # ---- timed region: K steps, device events on the context stream (barriers around it)
+    r = measure(L, w, psi_dev, args, local, stream, barrier=dist.barrier if world > 1 else None)
+    ms = r["ms"]
+    value, ms = whole_job_value(ms, r["units"], world, device=f"cuda:{local}")
     del psi_dev
     torch.cuda.empty_cache()
-
-    # ---- roofline of the dominant kernel class, from the live event timings
-    alg = algorithmic_per_qp_site(w.nx, mixed)
-    dom = max((k for k in ("planes", "pencils", "pointwise") if alg[k]["launches_per_step"]),
-              key=lambda k: prof[k][1])
-    launches, tot_ms = prof[dom]
-    per_launch_ms = tot_ms / max(launches, 1)
-    qp_sites = float(w.n_qp) * w.nxyz
-    a = alg[dom]
-    bytes_per_launch = a["bytes"] * qp_sites / a["launches_per_step"]
-    flops_per_launch = a["flops"] * qp_sites / a["launches_per_step"]
-    hbm_peak, hbm_src = read_peaks()
-    gbs = bytes_per_launch / (per_launch_ms / 1e3) / 1e9
-    tflops = flops_per_launch / (per_launch_ms / 1e3) / 1e12
-    alu_peak = FP32_PEAK_TFLOPS if mixed else FP64_PEAK_TFLOPS
-    if a.get("kind") == "bf16 tensor":
-        alu_peak = read_tensor_peak()
-    hbm_frac, alu_frac = gbs / hbm_peak, tflops / alu_peak
-    traffic = recorded_traffic(w.name, dom)
-    if alu_frac >= hbm_frac:
-        tensor_kind = a.get("kind") == "bf16 tensor"
-        roof = {"bound": "tensor" if tensor_kind else "alu", "achieved": tflops, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": alu_frac,
-                "peak_source": "measured bf16 (sustained)" if tensor_kind else
-                ("FP32" if mixed else "FP64") + " unit counts x 2.032 GHz (derived)",
-                "hbm_frac_of_measured": hbm_frac}
-        if "tensor_flops" in a:
-            roof["tensor_tflops_bf16"] = a["tensor_flops"] * qp_sites / a["launches_per_step"] / (per_launch_ms / 1e3) / 1e12
-    else:
-        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_frac,
-                "peak_source": hbm_src, "alu_frac": alu_frac}
-    roof.update({"kernel": dom, "traffic": traffic, "launch_ms": per_launch_ms,
-                 "algorithmic_bytes_per_launch": bytes_per_launch,
-                 "algorithmic_flops_per_launch": flops_per_launch,
-                 "kernel_share": {k: v[1] / max(sum(x[1] for x in prof.values()), 1e-30) for k, v in prof.items()}})
-    gpu_launches = int(sum(v[0] for v in prof.values()))
+    roof = roofline(w, r["prof"], ms / args.steps, fp64_peak)
+    gpu_launches = int(sum(v[0] for v in r["prof"].values()))
 
     # ---- e2e through the C ABI with host buffers
     e2e = None
@@ -596,10 +696,17 @@ def main():
         t_e2e = time.perf_counter() - t0
         ctx2.close()
         state_bytes = 16 * w.n_qp * 2 * w.nxyz
-        e2e = {"value": world * units / t_e2e, "unit": UNIT,
+        e2e = {"value": world * r["units"] / t_e2e, "unit": UNIT,
                "h2d_bytes_per_step": state_bytes / args.steps, "d2h_bytes_per_step": (state_bytes + 16) / args.steps,
                "includes": "set_state from pinned host (H2D + 3 series-expansion start steps), K ABM steps, "
                            "get_state to pinned host, energy"}
+        del out_host
+    del psi_host
+
+    # ---- the same comparison the metric names: one workload in both precisions
+    pair = None
+    if args.pair_workload and rank == 0 and world == 1:
+        pair = run_pair(L, args, local, stream, fp64_peak)
 
     # ---- CPU baseline: the oracle on a bounded sample of the same workload
     cpu = None
@@ -616,8 +723,9 @@ def main():
             "vs_baseline": None, "dtype": "f64" if not mixed else "f64+c64",
             "data": "synthetic", "config": config_of(w, args), "roofline": roof, "cpu_baseline": cpu,
             "tuned": {"pencils_states_per_batch": L.pencil_batch(w.nx, w.precision)},
-            "e2e": e2e, "clocks": clocks, "gpu_launches": gpu_launches,
-            "energy_after_timed_steps": E_dev, "particle_number": N_dev,
+            "e2e": e2e, "clocks": r["clocks"], "gpu_launches": gpu_launches,
+            "energy_after_timed_steps": r["E_end"], "particle_number": r["N_end"],
+            "fp64_fma_peak_tflops": fp64_peak, "pair": pair,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -27,7 +27,8 @@
  *   - The caller owns every host buffer passed in; the library reads or writes
  *     it only during the call (host copies complete before the call returns).
  *   - The context owns all device memory it allocates (lise_footprint_bytes
- *     tells how much); it allocates only in lise_create.
+ *     tells how much); it allocates in lise_create (and lise_set_shard, which
+ *     replaces the density partial-sum arrays).
  *   - A context is not thread-safe: do not use one context from two threads at
  *     once.  Different contexts are independent.
  *   - Work is enqueued on the context's stream.  lise_step returns after
@@ -51,12 +52,25 @@ extern "C" {
 #define LISE_ECUDA 3      /* a CUDA runtime call or kernel launch failed */
 #define LISE_ENONFINITE 4 /* a density or the input state is NaN or infinite */
 #define LISE_ETIMEOUT 5   /* a bounded device wait ran out (the tensor-memory planes kernel's
-                             wait for its MMAs); sticky like LISE_ENONFINITE */
+                             wait for its MMAs, the staged pencils kernel's wait for its
+                             tensor-memory-accelerator copies); sticky like LISE_ENONFINITE */
 #define LISE_ESTATE 6     /* call out of order (e.g. lise_step before lise_set_state) */
+#define LISE_EEXCHANGE 7  /* the shard exchange callback (lise_set_shard) returned non-zero */
 
 #define LISE_FP64 0       /* FFTs, H psi, ABM history, densities: all in FP64 */
-#define LISE_MIXED 1      /* FFTs and H psi in complex64 (FP32 accumulation); ABM history,
-                             state update and densities in FP64 */
+#define LISE_MIXED 1      /* FFTs and H psi in complex64 (FP32 accumulation), so the
+                             derivatives y' are FP32 values (stored exactly in complex64);
+                             the states y_n, y_{n-1}, Q and every sum with a state value
+                             (y_{n+1} = Q + k1 m', Q = (y_n + y_{n-1})/2 + Y) in FP64; the
+                             derivative combinations of Eqs. p, c (Y, R, p - c) and the
+                             density products in FP32 (Kahan-compensated per thread, FP64
+                             Neumaier across groups); m (the next H psi operand) in FP32 */
+#define LISE_MIXED_STRICT 2 /* FFTs and H psi as LISE_MIXED; the whole ABM history and
+                             state update in FP64: the derivative combinations as exact
+                             integer sums of the FP32 derivatives rounded once to FP64, R and
+                             p - c in complex128, P, Q, m and y_{n+1} in FP64 (m rounded to
+                             FP32 only as the H psi operand), density products and sums in
+                             FP64.  More bytes (R and p - c) and FP64 work than LISE_MIXED */
 
 typedef struct lise_ctx lise_ctx;
 
@@ -71,7 +85,7 @@ typedef struct {
   const double *v_static;   /* host array of N^3 doubles (static V_ext), or NULL; copied */
   double drive_A;           /* V_ext(r, t) += drive_A sin(drive_Omega t) z_c */
   double drive_Omega;
-  int precision;            /* LISE_FP64 or LISE_MIXED */
+  int precision;            /* LISE_FP64, LISE_MIXED or LISE_MIXED_STRICT */
   int device;               /* CUDA device ordinal */
   size_t hbm_budget_bytes;  /* 0 = no limit; otherwise lise_create fails with LISE_ENOMEM
                                (allocating nothing) if the footprint exceeds it */
@@ -102,6 +116,8 @@ int lise_create(const lise_params *p, lise_ctx **out);
  * procedure: 3 series-expansion steps of size dt (8 H psi each), storing
  * y'_k = f(t_k, y_k) for k = 0..3, so the context is at t0 + 3 dt and ready for
  * ABM steps.  dt may be negative (backward evolution) but not 0.
+ * A sticky LISE_ENONFINITE or LISE_ETIMEOUT from earlier work is cleared first (the
+ * new state replaces the whole history); LISE_ECUDA stays sticky.
  * Synchronises.  Errors: LISE_EINVAL, LISE_ENONFINITE (psi has NaN/Inf), LISE_ECUDA. */
 int lise_set_state(lise_ctx *c, const double *psi, double t0, double dt);
 /* Same with psi a device pointer (same layout) on the context's device. */
@@ -249,11 +265,70 @@ const char *lise_kernel_class_name(int kernel_class);
 /* Waits for enqueued work and reports sticky errors. */
 int lise_sync(lise_ctx *c);
 
+/* Sharded densities: the states of one evolution split over several contexts (one per GPU
+ * or process), as the paper splits the quasiparticle wavefunctions over GPUs and sums the
+ * partial densities over all of them before the potentials are built (Sec. "CPU-GPU
+ * hybrid structure"; Eqs. rho_t, nu_t are sums over all states).
+ * Each context holds n_qp of the states.  Its density sums run in groups of group_size
+ * states (the same on every shard); the groups of all shards, in the order of the states,
+ * are numbered 0 .. n_groups_all - 1 and this context's are first_group ..
+ * first_group + ceil(n_qp / group_size) - 1.  The partial sums are kept for all groups,
+ * as three arrays [n_groups_all][N^3] (n, Re nu, Im nu) in one block `parts` of
+ * 3 n_groups_all N^3 doubles.  Before every density reduction (two per ABM step, the
+ * start, lise_densities, lise_energy, lise_currents, lise_rhs) the library calls
+ *   exchange(user, parts, on_device, stream, N^3, first_group, n_local, n_groups_all)
+ * on the calling thread, with this context's groups filled in; the callee fills in every
+ * other group (from the other shards) and returns 0, or non-zero to fail the call with
+ * LISE_EEXCHANGE.  on_device = 1: parts is the device block and the callee enqueues its
+ * transfers (e.g. NCCL collectives) on `stream` (a cudaStream_t); capturable = 1 lets
+ * lise_step capture them into its CUDA graphs.  on_device = 0: parts is a pinned host
+ * copy (the library copies this context's groups out first and the whole block back
+ * afterwards; stream is NULL) and lise_step uses no graphs.  Each group is summed in a
+ * fixed order and the groups are reduced in their global order, so a sharded evolution
+ * gives bit-for-bit the result of one context holding all states with the same
+ * group_size.  With exchange = NULL the call only sets the group size (n_groups_all must
+ * then equal this context's group count, first_group 0).
+ * lise_set_shard replaces the partial-sum arrays (device, and pinned host memory for a host
+ * exchange) and invalidates the history: call it before lise_set_state.  Every shard
+ * must make the same sequence of calls.  Errors: LISE_EINVAL (group_size outside
+ * 1..64, a group range outside 0..n_groups_all), LISE_ENOMEM, LISE_ECUDA. */
+typedef int (*lise_exchange_fn)(void *user, double *parts, int on_device, void *stream, long nxyz,
+                                int first_group, int n_groups_local, int n_groups_all);
+typedef struct {
+  int group_size;             /* states per density group, 1..64, equal on all shards */
+  int first_group;            /* this context's first group among all shards' groups */
+  int n_groups_all;           /* groups over all shards */
+  lise_exchange_fn exchange;  /* NULL: no other shard (sets the group size only) */
+  void *user;                 /* passed to exchange */
+  int on_device;              /* 1: exchange works on the device block, 0: on a host copy */
+  int capturable;             /* on_device only: 1 if the enqueued transfers can be graph-captured */
+} lise_shard;
+int lise_set_shard(lise_ctx *c, const lise_shard *s);
+
+/* Bounded device waits.  The kernels that wait on the hardware (the tensor-memory planes
+ * kernel for its MMAs, the staged pencils kernel for its tensor-memory-accelerator copies)
+ * give up after a number of polls of their barrier, set the context's error word and
+ * stop; the next synchronising call then reports LISE_ETIMEOUT.  polls > 0 sets that
+ * number, polls == 0 makes every such wait give up at once (a way to exercise this error
+ * path), polls < 0 restores the default (4194304 polls, far beyond any healthy wait).  A
+ * block that gives up still lets the MMAs and copies it has in flight finish before it
+ * frees its tensor memory and exits.  Applies to work enqueued after the call
+ * (synchronises the context's stream when the limit changes).  Errors: LISE_EINVAL
+ * (null context), LISE_ECUDA. */
+int lise_set_wait_limit(lise_ctx *c, long polls);
+
 /* Static description of a status code. */
 const char *lise_strerror(int status);
 
 /* Frees the context and its device memory (synchronises first).  NULL is a no-op. */
 void lise_destroy(lise_ctx *c);
+
+/* ---- Measurement (no counterpart in the paper) ----
+ * FP64 fused multiply-add throughput of `device` under its current clock (TFLOP/s, an FMA
+ * counts 2), timed with CUDA events on a kernel of independent FMA chains (best of 5
+ * launches of about 10 ms after a warm-up): the denominator of the FP64-pipe fraction of
+ * the benchmark's roofline.  Errors: LISE_EINVAL (null pointer, no such device), LISE_ECUDA. */
+int lise_measure_fp64_peak(int device, double *tflops);
 
 /* ---- Right-hand side without any allocation (no counterpart in the paper) ----
  * For callers that must not allocate device memory while they run: a host
@@ -279,8 +354,9 @@ void lise_destroy(lise_ctx *c);
  *   (the error word is cleared at the start of each call); calls that overlap
  *   on the GPU (other streams, other host threads) race on it, so serialise
  *   them.  p->hbm_budget_bytes is ignored.  Synchronises p->stream.
- *   Errors: LISE_EINVAL, LISE_ENOMEM (too large for the array), LISE_ECUDA,
- *   LISE_ENONFINITE (a density is NaN or infinite). */
+ *   Errors: LISE_EINVAL (the checks of lise_create, or a null buffer), LISE_ENOMEM (too
+ *   large for the array), LISE_ECUDA, LISE_ENONFINITE (a density is NaN or infinite),
+ *   LISE_ETIMEOUT (a bounded device wait ran out). */
 #define LISE_NOALLOC_SCRATCH_BYTES (64u << 20)
 int lise_rhs_noalloc(const lise_params *p, const double *psi_dev, double t, double *dpsi_dev);
 

@@ -30,12 +30,33 @@
 
 using namespace lise;
 
+namespace lise {
+
+int check_params(const lise_params* p) {
+  if (!p) return LISE_EINVAL;
+  if (p->nx != p->ny || p->ny != p->nz) return LISE_EINVAL;
+  if (!supported_n(p->nx)) return LISE_EINVAL;
+  if (!(p->dx > 0.0) || !std::isfinite(p->dx) || p->n_qp < 1) return LISE_EINVAL;
+  if (p->precision != LISE_FP64 && p->precision != LISE_MIXED && p->precision != LISE_MIXED_STRICT)
+    return LISE_EINVAL;
+  if (!std::isfinite(p->alpha) || !std::isfinite(p->beta) || !std::isfinite(p->mu) ||
+      !std::isfinite(p->g) || !std::isfinite(p->drive_A) || !std::isfinite(p->drive_Omega))
+    return LISE_EINVAL;
+  if (p->pair_lattice && !(p->alpha > 0.0)) return LISE_EINVAL;
+  if (p->pair_alpha != 0.0 && !(std::isfinite(p->pair_alpha) && p->pair_n0 > 0.0 && std::isfinite(p->pair_n0)))
+    return LISE_EINVAL;
+  return LISE_OK;
+}
+
+}  // namespace lise
+
 struct lise_ctx {
   lise_params p;
   int N = 0;
   long nxyz = 0;
   long ns = 0;  // complex elements per state array
-  int mixed = 0;
+  int mixed = 0;   // FP32 compute precision (LISE_MIXED and LISE_MIXED_STRICT)
+  int strict = 0;  // LISE_MIXED_STRICT: R and p - c in complex128, FP64 history arithmetic
   int device = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
@@ -50,7 +71,16 @@ struct lise_ctx {
   void* RPC = nullptr;
   void *R = nullptr, *PC = nullptr;
   void* TXY = nullptr;
+  // density partial sums [3][n_groups_all][N^3] (n, Re nu, Im nu) in one allocation; part_*
+  // view this context's groups [first_group, first_group + n_groups) of each array
+  double* parts = nullptr;
   double *part_n = nullptr, *part_nr = nullptr, *part_ni = nullptr;
+  int n_groups_all = 0, first_group = 0;
+  // sharded densities (lise_set_shard): the exchange that fills the other shards' groups
+  lise_exchange_fn exch = nullptr;
+  void* exch_user = nullptr;
+  int exch_on_device = 0, exch_capturable = 0;
+  double* host_parts = nullptr;  // pinned [3][n_groups_all][N^3] for a host-side exchange
   double* dn[2] = {nullptr, nullptr};
   double2* dnu[2] = {nullptr, nullptr};
   double* W = nullptr;
@@ -61,6 +91,7 @@ struct lise_ctx {
   int oz_sD = 0;
   double* e_site = nullptr;
   int* err = nullptr;
+  long wait_polls = 0;  // bounded device waits (PencilArgs::wait_polls): 0 = the default limit
   double t = 0.0, dt = 0.0;
   int ready = 0;
   int sticky = LISE_OK;
@@ -87,31 +118,6 @@ struct lise_ctx {
 
 namespace {
 
-constexpr long double PI_L = 3.141592653589793238462643383279502884L;
-
-int check_params(const lise_params* p) {
-  if (!p) return LISE_EINVAL;
-  if (p->nx != p->ny || p->ny != p->nz) return LISE_EINVAL;
-  if (!supported_n(p->nx)) return LISE_EINVAL;
-  if (!(p->dx > 0.0) || p->n_qp < 1) return LISE_EINVAL;
-  if (p->precision != LISE_FP64 && p->precision != LISE_MIXED) return LISE_EINVAL;
-  if (!std::isfinite(p->alpha) || !std::isfinite(p->beta) || !std::isfinite(p->mu) ||
-      !std::isfinite(p->g) || !std::isfinite(p->drive_A) || !std::isfinite(p->drive_Omega))
-    return LISE_EINVAL;
-  if (p->pair_lattice && !(p->alpha > 0.0)) return LISE_EINVAL;
-  if (p->pair_alpha != 0.0 && !(std::isfinite(p->pair_alpha) && p->pair_n0 > 0.0)) return LISE_EINVAL;
-  return LISE_OK;
-}
-
-void choose_groups(int N, int n_qp, int mixed, int* qg, int* n_groups) {
-  const int tiles = (N / pencil_tx(N, mixed)) * N;
-  int q = 64;
-  while (q > 4 && (long)tiles * ((n_qp + q - 1) / q) < 2048) q /= 2;
-  if (q > n_qp) q = n_qp;
-  *qg = q;
-  *n_groups = (n_qp + q - 1) / q;
-}
-
 constexpr int kNormBlocks = 32;  // blocks per state of the norm reduction (renormalisation)
 
 struct Footprint {
@@ -124,20 +130,26 @@ Footprint footprint(const lise_params* p) {
   const long nxyz = N * N * N;
   const long ns = (long)p->n_qp * 2 * nxyz;
   int qg, ng;
-  choose_groups((int)N, p->n_qp, p->precision == LISE_MIXED, &qg, &ng);
-  // 2 y slots and Q in complex128; 4 y', m, R and P-C in the compute precision
-  const size_t rc = p->precision == LISE_MIXED ? sizeof(float2) : sizeof(double2);
-  f.state = 3 * (size_t)ns * sizeof(double2) + 7 * (size_t)ns * rc;
-  f.txy = (size_t)ns * (p->precision == LISE_MIXED ? sizeof(float2) : sizeof(double2));
+  choose_groups((int)N, p->n_qp, p->precision != LISE_FP64, &qg, &ng);
+  // 2 y slots and Q in complex128; 4 y', m in the compute precision; R and P-C in the compute
+  // precision (complex128 in the strict split)
+  const bool mixed = p->precision != LISE_FP64;
+  const size_t rc = mixed ? sizeof(float2) : sizeof(double2);
+  const size_t rh = (p->precision == LISE_MIXED) ? sizeof(float2) : sizeof(double2);
+  f.state = 3 * (size_t)ns * sizeof(double2) + 5 * (size_t)ns * rc + 2 * (size_t)ns * rh;
+  f.txy = (size_t)ns * rc;
   f.partials = 3 * (size_t)ng * nxyz * sizeof(double);
   f.small = (size_t)nxyz * (2 * sizeof(double) + 2 * sizeof(double2) + sizeof(double) + sizeof(double2) +
                             sizeof(double) + 2 * sizeof(double)) +
             3 * (size_t)N * sizeof(double2) + 256;
-  if (p->remove_phase) f.small += (size_t)p->n_qp * (1 + pencil_blocks_x((int)N, p->precision == LISE_MIXED)) * sizeof(double);
+  if (p->remove_phase) f.small += (size_t)p->n_qp * (1 + pencil_blocks_x((int)N, p->precision != LISE_FP64)) * sizeof(double);
   if (p->renormalize) f.small += (size_t)p->n_qp * (1 + kNormBlocks) * sizeof(double);
   f.total = f.state + f.txy + f.partials + f.small;
   return f;
 }
+
+// bytes per complex element of R and p - c: the compute precision, complex128 in the strict split
+size_t hist_elem(const lise_ctx* c) { return (c->mixed && !c->strict) ? sizeof(float2) : sizeof(double2); }
 
 double drive_at(const lise_ctx* c, double t) {
   return c->p.drive_A == 0.0 ? 0.0 : c->p.drive_A * std::sin(c->p.drive_Omega * t);
@@ -174,6 +186,8 @@ PencilArgs pencil_base(const lise_ctx* c) {
   PencilArgs a;
   std::memset(&a, 0, sizeof(a));
   a.err = c->err;
+  a.wait_polls = c->wait_polls;
+  a.strict = c->strict;
   a.txy = c->TXY;
   a.W = c->W;
   a.D = c->Dl;
@@ -201,6 +215,7 @@ int run_planes(lise_ctx* c, const double2* x, const void* xr = nullptr) {
   a.oz_sD = c->oz_sD;
   a.n_planes = (long)c->p.n_qp * 2 * c->N;
   a.err = c->err;
+  a.wait_polls = c->wait_polls;
   return timed(c, LISE_KC_PLANES, [&] { return launch_planes(c->N, c->mixed, a, c->stream) ? LISE_ECUDA : LISE_OK; });
 }
 
@@ -225,14 +240,45 @@ int run_eta(lise_ctx* c, const double2* x, const void* xr = nullptr) {
   });
 }
 
+// The other shards' groups of the partial sums (a no-op for an unsharded context): a
+// device exchange enqueues its work on the context stream; a host exchange gets this
+// context's groups in a pinned host copy and fills in the others, which are copied back.
+int exchange_parts(lise_ctx* c) {
+  if (!c->exch) return LISE_OK;
+  const size_t plane = (size_t)c->n_groups_all * c->nxyz;  // doubles per array
+  if (c->exch_on_device)
+    return c->exch(c->exch_user, c->parts, 1, (void*)c->stream, c->nxyz, c->first_group, c->n_groups, c->n_groups_all)
+               ? LISE_EEXCHANGE
+               : LISE_OK;
+  const size_t off = (size_t)c->first_group * c->nxyz, cnt = (size_t)c->n_groups * c->nxyz;
+  for (int k = 0; k < 3; ++k)
+    TRY(cu(cudaMemcpyAsync(c->host_parts + k * plane + off, c->parts + k * plane + off, cnt * sizeof(double),
+                           cudaMemcpyDeviceToHost, c->stream)));
+  TRY(cu(cudaStreamSynchronize(c->stream)));
+  if (c->exch(c->exch_user, c->host_parts, 0, nullptr, c->nxyz, c->first_group, c->n_groups, c->n_groups_all))
+    return LISE_EEXCHANGE;
+  return cu(cudaMemcpyAsync(c->parts, c->host_parts, 3 * plane * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+}
+
 // Reduce the density partials; optionally average with (avg_n, avg_nu); write
 // the densities to slot `dslot` and, if potentials is true, W and Delta at t.
-int run_reduce(lise_ctx* c, int dslot, const double* avg_n, const double2* avg_nu, bool potentials, double t) {
+// all_shards = false reduces this context's own groups only (no exchange).
+int run_reduce(lise_ctx* c, int dslot, const double* avg_n, const double2* avg_nu, bool potentials, double t,
+               bool all_shards = true) {
   ReduceArgs r;
-  r.part_n = c->part_n;
-  r.part_nr = c->part_nr;
-  r.part_ni = c->part_ni;
-  r.n_groups = c->n_groups;
+  if (all_shards) {
+    TRY(exchange_parts(c));
+    const size_t plane = (size_t)c->n_groups_all * c->nxyz;
+    r.part_n = c->parts;
+    r.part_nr = c->parts + plane;
+    r.part_ni = c->parts + 2 * plane;
+    r.n_groups = c->n_groups_all;
+  } else {
+    r.part_n = c->part_n;
+    r.part_nr = c->part_nr;
+    r.part_ni = c->part_ni;
+    r.n_groups = c->n_groups;
+  }
   r.nxyz = c->nxyz;
   r.N = c->N;
   r.a = c->p.dx;
@@ -333,6 +379,7 @@ PointwiseArgs predict_args(lise_ctx* c, const double2* y0, const double2* y1, co
   w.r = c->R;
   w.m = c->M;
   w.mixed = c->mixed;
+  w.strict = c->strict;
   w.h = h;
   w.part_n = c->part_n;
   w.part_nr = c->part_nr;
@@ -384,7 +431,7 @@ int start_procedure(lise_ctx* c, double t0, double dt) {
   TRY(run_pencils(c, M_RHS, a));
   c->y0_slot = (cur == c->slot[0]) ? 0 : 1;
   // p_3 - c_3 := 0; predictor and modifier of the first ABM step
-  TRY(cu(cudaMemsetAsync(c->PC, 0, (size_t)c->ns * (c->mixed ? sizeof(float2) : sizeof(double2)), c->stream)));
+  TRY(cu(cudaMemsetAsync(c->PC, 0, (size_t)c->ns * hist_elem(c), c->stream)));
   PointwiseArgs w = predict_args(c, c->slot[c->y0_slot], c->slot[1 - c->y0_slot], c->D[0], c->D[1], c->D[2],
                                  c->D[3], dt);
   TRY(timed(c, LISE_KC_POINTWISE, [&] { return launch_predict(w, c->stream) ? LISE_ECUDA : LISE_OK; }));
@@ -532,44 +579,17 @@ int graph_steps(lise_ctx* c) {
 void free_ctx(lise_ctx* c) {
   drop_graphs(c);
   void* ptrs[] = {c->norm_part, c->norm_scale, c->drive_dev, c->eta, c->eta_part, c->slot[0], c->slot[1], c->D[0], c->D[1], c->D[2], c->D[3], c->M, c->RPC, c->Q, c->TXY,
-                  c->part_n, c->part_nr, c->part_ni, c->dn[0], c->dn[1], c->dnu[0], c->dnu[1], c->W,
+                  c->parts, c->dn[0], c->dn[1], c->dnu[0], c->dnu[1], c->W,
                   c->Dl, c->v_static, c->tw, c->hxy, c->hz, c->ozb, c->e_site, c->err};
   // stream-ordered frees: no device-wide synchronisation (work of other contexts,
   // e.g. the other requests of a server, keeps running)
   for (void* q : ptrs)
     if (q) cudaFreeAsync(q, c->stream);
   cudaStreamSynchronize(c->stream);
+  if (c->host_parts) cudaFreeHost(c->host_parts);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   std::free(c->host_e);
-}
-
-template <typename R>
-void fill_tables(int N, double a, double alpha, R* tw, R* hxy, R* hz) {
-  // twiddles tw[j2 * N1 + k1] = exp(-2 pi i (j2 k1 mod N) / N); the four-step
-  // plan reads entries with j2 < N2, k1 < N1 only.
-  int N1 = 0;
-  switch (N) {
-    case 8: N1 = 2; break;
-    case 12: case 16: case 20: case 24: case 32: N1 = 4; break;
-    default: N1 = 8; break;
-  }
-  const int N2 = N / N1;
-  for (int j2 = 0; j2 < N2; ++j2)
-    for (int k1 = 0; k1 < N1; ++k1) {
-      long e = ((long)j2 * k1) % N;
-      long double ang = -2.0L * PI_L * (long double)e / (long double)N;
-      tw[2 * (j2 * N1 + k1)] = (R)cosl(ang);
-      tw[2 * (j2 * N1 + k1) + 1] = (R)sinl(ang);
-    }
-  const long double L = (long double)N * a;
-  for (int k = 0; k < N; ++k) {
-    // Sec. "Discretization": k = 2 pi n / L over n = -N/2 .. N/2-1 (index n mod N)
-    long double kk = 2.0L * PI_L * (long double)(k < N / 2 ? k : k - N) / L;
-    long double f = 0.5L * alpha * kk * kk;
-    hxy[k] = (R)(f / ((long double)N * N));
-    hz[k] = (R)(f / (long double)N);
-  }
 }
 
 }  // namespace
@@ -590,6 +610,7 @@ const char* lise_strerror(int s) {
     case LISE_ENONFINITE: return "non-finite state or density";
     case LISE_ETIMEOUT: return "bounded device wait timed out";
     case LISE_ESTATE: return "call out of order (no state set)";
+    case LISE_EEXCHANGE: return "the shard exchange callback failed";
     default: return "unknown status";
   }
 }
@@ -610,7 +631,8 @@ int lise_create(const lise_params* p, lise_ctx** out) {
   c->N = p->nx;
   c->nxyz = (long)c->N * c->N * c->N;
   c->ns = (long)p->n_qp * 2 * c->nxyz;
-  c->mixed = p->precision == LISE_MIXED;
+  c->mixed = p->precision != LISE_FP64;
+  c->strict = p->precision == LISE_MIXED_STRICT;
   c->device = p->device;
   choose_groups(c->N, p->n_qp, c->mixed, &c->qg, &c->n_groups);
   int rc = LISE_OK;
@@ -639,16 +661,20 @@ int lise_create(const lise_params* p, lise_ctx** out) {
   alloc((void**)&c->drive_dev, 2 * kGraphSteps * sizeof(double));
   alloc(&c->M, sr);
   alloc((void**)&c->Q, sb);
-  alloc(&c->RPC, 2 * sr);  // R, P-C; at least one complex128 state (start procedure)
+  const size_t sh = (size_t)c->ns * hist_elem(c);  // R or P-C
+  alloc(&c->RPC, 2 * sh);  // R, P-C; at least one complex128 state (start procedure)
   if (c->RPC) {
     c->R = c->RPC;
-    c->PC = static_cast<char*>(c->RPC) + sr;
+    c->PC = static_cast<char*>(c->RPC) + sh;
   }
   alloc(&c->TXY, (size_t)c->ns * (c->mixed ? sizeof(float2) : sizeof(double2)));
-  const size_t pb = (size_t)c->n_groups * c->nxyz * sizeof(double);
-  alloc((void**)&c->part_n, pb);
-  alloc((void**)&c->part_nr, pb);
-  alloc((void**)&c->part_ni, pb);
+  c->n_groups_all = c->n_groups;
+  alloc((void**)&c->parts, 3 * (size_t)c->n_groups * c->nxyz * sizeof(double));
+  if (c->parts) {
+    c->part_n = c->parts;
+    c->part_nr = c->parts + (size_t)c->n_groups * c->nxyz;
+    c->part_ni = c->parts + 2 * (size_t)c->n_groups * c->nxyz;
+  }
   for (int k = 0; k < 2; ++k) {
     alloc((void**)&c->dn[k], c->nxyz * sizeof(double));
     alloc((void**)&c->dnu[k], c->nxyz * sizeof(double2));
@@ -682,10 +708,7 @@ int lise_create(const lise_params* p, lise_ctx** out) {
   if (rc == LISE_OK) {
     // tables
     std::vector<char> tw(2 * c->N * rs), hxy(c->N * rs), hz(c->N * rs);
-    if (c->mixed)
-      fill_tables<float>(c->N, p->dx, p->alpha, (float*)tw.data(), (float*)hxy.data(), (float*)hz.data());
-    else
-      fill_tables<double>(c->N, p->dx, p->alpha, (double*)tw.data(), (double*)hxy.data(), (double*)hz.data());
+    fill_fft_tables(c->N, p->dx, p->alpha, c->mixed, tw.data(), hxy.data(), hz.data());
     rc = cu(cudaMemcpyAsync(c->tw, tw.data(), tw.size(), cudaMemcpyHostToDevice, c->stream));
     if (rc == LISE_OK) rc = cu(cudaMemcpyAsync(c->hxy, hxy.data(), hxy.size(), cudaMemcpyHostToDevice, c->stream));
     if (rc == LISE_OK) rc = cu(cudaMemcpyAsync(c->hz, hz.data(), hz.size(), cudaMemcpyHostToDevice, c->stream));
@@ -724,9 +747,10 @@ static int tune_pencils(lise_ctx* c, double t0) {
     if (n_valid == 1) pencil_qb_set(c->N, c->mixed, cands[0]);
     return LISE_OK;
   }
-  // valid potentials and T_xy of the input for representative launches
+  // valid potentials and T_xy of the input for representative launches (this context's
+  // own density groups: no shard exchange while tuning)
   TRY(run_density(c, c->slot[0]));
-  TRY(run_reduce(c, 0, nullptr, nullptr, true, t0));
+  TRY(run_reduce(c, 0, nullptr, nullptr, true, t0, false));
   TRY(run_planes(c, c->slot[0]));
   TRY(cu(cudaMemsetAsync(c->M, 0, (size_t)c->ns * (c->mixed ? sizeof(float2) : sizeof(double2)), c->stream)));
   PencilArgs a = pencil_base(c);  // corrector on m = 0: y_{n+1}, p - c into free arrays
@@ -789,10 +813,21 @@ static int tune_pencils(lise_ctx* c, double t0) {
   return rc;
 }
 
+// A non-finite density or a bounded wait that ran out leaves the device and the context's
+// memory intact: a new state (series start, fresh history) clears it.  A CUDA error stays.
+static int clear_recoverable(lise_ctx* c) {
+  if (c->sticky != LISE_ENONFINITE && c->sticky != LISE_ETIMEOUT) return c->sticky;
+  TRY(cu(cudaStreamSynchronize(c->stream)));
+  TRY(cu(cudaMemsetAsync(c->err, 0, sizeof(int), c->stream)));
+  TRY(cu(cudaStreamSynchronize(c->stream)));
+  c->sticky = LISE_OK;
+  return LISE_OK;
+}
+
 static int set_state_common(lise_ctx* c, const double* psi, double t0, double dt, cudaMemcpyKind kind) {
   if (!c || !psi || !(dt != 0.0) || !std::isfinite(dt) || !std::isfinite(t0)) return LISE_EINVAL;
-  if (c->sticky) return c->sticky;
   if (cudaSetDevice(c->device) != cudaSuccess) return LISE_ECUDA;
+  TRY(clear_recoverable(c));
   c->ready = 0;
   TRY(cu(cudaMemcpyAsync(c->slot[0], psi, (size_t)c->ns * sizeof(double2), kind, c->stream)));
   TRY(launch_finite_check(c->slot[0], c->ns, c->err, c->stream) ? LISE_ECUDA : LISE_OK);
@@ -843,13 +878,15 @@ int lise_set_state_device(lise_ctx* c, const double* psi_dev, double t0, double 
 }
 
 int lise_pencil_batch(int N, int precision) {
-  if (!supported_n(N) || (precision != LISE_FP64 && precision != LISE_MIXED)) return 0;
-  return pencil_qb(N, precision == LISE_MIXED);
+  if (!supported_n(N) || (precision != LISE_FP64 && precision != LISE_MIXED && precision != LISE_MIXED_STRICT))
+    return 0;
+  return pencil_qb(N, precision != LISE_FP64);
 }
 
 int lise_set_pencil_batch(int N, int precision, int qb) {
-  if (!supported_n(N) || (precision != LISE_FP64 && precision != LISE_MIXED)) return LISE_EINVAL;
-  const int mixed = precision == LISE_MIXED;
+  if (!supported_n(N) || (precision != LISE_FP64 && precision != LISE_MIXED && precision != LISE_MIXED_STRICT))
+    return LISE_EINVAL;
+  const int mixed = precision != LISE_FP64;
   if (qb != 0 && !pencil_qb_valid(N, mixed, qb)) return LISE_EINVAL;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   pencil_qb_set(N, mixed, qb);
@@ -876,8 +913,10 @@ int lise_currents(lise_ctx* c, double* j_out) {
   if (rc == LISE_OK && launch_currents(c->slot[c->y0_slot], d1, c->N, c->p.n_qp, c->qg, c->part_n, c->part_nr,
                                        c->part_ni, c->stream))
     rc = LISE_ECUDA;
-  if (rc == LISE_OK &&
-      launch_sum_groups3(c->part_n, c->part_nr, c->part_ni, c->n_groups, c->nxyz, out, c->stream))
+  if (rc == LISE_OK) rc = exchange_parts(c);
+  const size_t plane = (size_t)c->n_groups_all * c->nxyz;
+  if (rc == LISE_OK && launch_sum_groups3(c->parts, c->parts + plane, c->parts + 2 * plane, c->n_groups_all, c->nxyz,
+                                          out, c->stream))
     rc = LISE_ECUDA;
   if (rc == LISE_OK)
     rc = cu(cudaMemcpyAsync(j_out, out, 3 * c->nxyz * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -921,7 +960,7 @@ int lise_step(lise_ctx* c, int n_steps, double dt) {
     int rc;
     // replay captured graphs for runs of kGraphSteps steps (plain launches while profiling,
     // so that every kernel is bracketed by its own events)
-    if (!c->prof && n_steps - k >= kGraphSteps) {
+    if (!c->prof && n_steps - k >= kGraphSteps && (!c->exch || (c->exch_on_device && c->exch_capturable))) {
       rc = graph_steps(c);
       k += kGraphSteps;
     } else {
@@ -985,7 +1024,8 @@ int lise_energy(lise_ctx* c, double* E, double* Nout) {
   a.x = y;
   a.dens = 1;
   TRY(run_pencils(c, M_ENERGY, a));
-  TRY(launch_energy_sites(c->part_n, c->n_groups, c->dn[0], c->dnu[0], c->v_static, drive_at(c, c->t), c->p.beta,
+  TRY(exchange_parts(c));  // the other shards' kinetic partials
+  TRY(launch_energy_sites(c->parts, c->n_groups_all, c->dn[0], c->dnu[0], c->v_static, drive_at(c, c->t), c->p.beta,
                           c->p.g, c->p.pair_alpha != 0.0 ? c->p.pair_alpha / c->p.pair_n0 : 0.0,
                           c->p.pair_lattice ? pairing_lattice_c(c->p.dx, c->p.alpha) : 0.0, c->N, c->p.dx,
                           c->e_site, c->stream)
@@ -1051,17 +1091,20 @@ void ckpt_arrays(lise_ctx* c, void* arr[kCkptArrays], size_t sz[kCkptArrays]) {
   arr[7] = c->PC;
   arr[8] = c->Q;
   arr[9] = c->R;
-  // y_n, y_{n-1} and Q are complex128; the y' ring, m, P-C and R the compute precision
+  // y_n, y_{n-1} and Q are complex128; the y' ring and m the compute precision; P-C and R
+  // the compute precision, complex128 in the strict split
   const size_t sr = (size_t)c->ns * (c->mixed ? sizeof(float2) : sizeof(double2));
   for (int k = 0; k < kCkptArrays; ++k) sz[k] = sr;
   sz[0] = sz[1] = sz[8] = (size_t)c->ns * sizeof(double2);
+  sz[7] = sz[9] = (size_t)c->ns * hist_elem(c);
 }
 }  // namespace
 
 size_t lise_checkpoint_bytes(const lise_ctx* c) {
   if (!c) return 0;
   return sizeof(CkptHeader) + 3 * (size_t)c->ns * sizeof(double2) +
-         (kCkptArrays - 3) * (size_t)c->ns * (c->mixed ? sizeof(float2) : sizeof(double2)) +
+         (kCkptArrays - 5) * (size_t)c->ns * (c->mixed ? sizeof(float2) : sizeof(double2)) +
+         2 * (size_t)c->ns * hist_elem(c) +
          (size_t)c->nxyz * (sizeof(double) + sizeof(double2));
 }
 
@@ -1152,6 +1195,65 @@ int lise_profile_read(lise_ctx* c, int cls, long* launches, double* total_ms) {
 const char* lise_kernel_class_name(int cls) {
   static const char* names[LISE_KC_COUNT] = {"planes", "pencils", "reduce", "pointwise"};
   return (cls >= 0 && cls < LISE_KC_COUNT) ? names[cls] : nullptr;
+}
+
+int lise_set_shard(lise_ctx* c, const lise_shard* sh) {
+  if (!c || !sh) return LISE_EINVAL;
+  if (sh->group_size < 1 || sh->group_size > 64) return LISE_EINVAL;
+  const int n_local = (c->p.n_qp + sh->group_size - 1) / sh->group_size;
+  if (sh->first_group < 0 || sh->n_groups_all < 1 || (long)sh->first_group + n_local > (long)sh->n_groups_all)
+    return LISE_EINVAL;
+  if (cudaSetDevice(c->device) != cudaSuccess) return LISE_ECUDA;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return LISE_ECUDA;
+  // new partial-sum arrays for all shards' groups (zeroed), and the host copy of a host exchange
+  const size_t bytes = 3 * (size_t)sh->n_groups_all * c->nxyz * sizeof(double);
+  double* parts = nullptr;
+  double* host = nullptr;
+  if (cudaMallocAsync((void**)&parts, bytes, c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return LISE_ENOMEM;
+  }
+  if (sh->exchange && !sh->on_device && cudaHostAlloc((void**)&host, bytes, cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFreeAsync(parts, c->stream);
+    return LISE_ENOMEM;
+  }
+  if (cudaMemsetAsync(parts, 0, bytes, c->stream) != cudaSuccess) {
+    cudaFreeAsync(parts, c->stream);
+    if (host) cudaFreeHost(host);
+    return LISE_ECUDA;
+  }
+  cudaFreeAsync(c->parts, c->stream);
+  if (c->host_parts) cudaFreeHost(c->host_parts);
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return LISE_ECUDA;
+  drop_graphs(c);  // the captured launches point at the old arrays
+  c->parts = parts;
+  c->host_parts = host;
+  c->qg = sh->group_size;
+  c->n_groups = n_local;
+  c->n_groups_all = sh->n_groups_all;
+  c->first_group = sh->first_group;
+  const size_t plane = (size_t)c->n_groups_all * c->nxyz, off = (size_t)c->first_group * c->nxyz;
+  c->part_n = parts + off;
+  c->part_nr = parts + plane + off;
+  c->part_ni = parts + 2 * plane + off;
+  c->exch = sh->exchange;
+  c->exch_user = sh->user;
+  c->exch_on_device = sh->on_device;
+  c->exch_capturable = sh->capturable;
+  c->ready = 0;  // the history was built with the old groups
+  return LISE_OK;
+}
+
+int lise_set_wait_limit(lise_ctx* c, long polls) {
+  if (!c) return LISE_EINVAL;
+  const long w = polls < 0 ? 0 : (polls == 0 ? -1 : polls);
+  if (w != c->wait_polls) {
+    if (cudaSetDevice(c->device) != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess) return LISE_ECUDA;
+    drop_graphs(c);  // the limit is a kernel parameter of the captured launches
+    c->wait_polls = w;
+  }
+  return LISE_OK;
 }
 
 int lise_sync(lise_ctx* c) {

@@ -9,3 +9,10 @@
 // word, reported as LISE_ENONFINITE by the next synchronising call (lise_sync,
 // lise_get_state, ...).  psi must stay valid until the stream has consumed it.
 extern "C" int lise_set_state_enqueue(lise_ctx* c, const double* psi, double t0, double dt);
+
+namespace lise {
+// Validation of lise_params shared by lise_create and lise_rhs_noalloc: LISE_OK or LISE_EINVAL
+// (lattice, spacing, state count, precision, finiteness of every physical parameter, the
+// pairing options).
+int check_params(const lise_params* p);
+}  // namespace lise

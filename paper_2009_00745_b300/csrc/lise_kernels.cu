@@ -534,7 +534,7 @@ __global__ void __launch_bounds__(256, kPlanesTcBlocksPerSM) k_planes_tc(PlanesA
     }
     // the previous plane's T_xy while this plane's MMAs run
     if (prev >= 0) final_pass(prev, ps0, ps1);
-    const bool ok = um::mbar_wait(&mbar, parity, 1L << 22);
+    const bool ok = um::mbar_wait(&mbar, parity, wait_limit(a.wait_polls));
     parity ^= 1u;
     if (__syncthreads_or(!ok)) {  // (also: every thread is done with the sums of the previous plane)
       failed = true;
@@ -573,7 +573,7 @@ __global__ void __launch_bounds__(256, kPlanesTcBlocksPerSM) k_planes_tc(PlanesA
   }
   if (failed) {
     if (tid == 0 && a.err) atomicOr(a.err, 4);
-    um::mbar_wait(&mbar, parity ^ 1u, 1L << 22);  // let the MMAs in flight finish, bounded
+    um::mbar_wait(&mbar, parity ^ 1u, kDrainPolls);  // let the MMAs in flight finish, bounded
   }
   um::fence_before();
   __syncthreads();
@@ -664,7 +664,10 @@ __host__ __device__ constexpr int pencil_smem_bytes() {
                          : (N % 16 == 0 ? oz::S * QB * 4 * TX * (N + 8) * 2 : 0));
 }
 
-template <typename R, int N, int TX, int QB, int MODE>
+// ST (FP32 compute precision, corrector mode only): the strict split of LISE_MIXED_STRICT --
+// R and p - c in complex128 (units of h/48), y_{n+1} = Q + k1 m' and p - c = R - 17 m' in
+// FP64 from the exact FP64 value of m', densities of y_{n+1} from its FP64 values.
+template <typename R, int N, int TX, int QB, int MODE, bool ST = false>
 __global__ void __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N * TX == 256 ? 2 : ((sizeof(R) == 8 && N * TX == 128) ? 7 : ((sizeof(R) == 8 && N * TX == 192) ? 3 : 1))) k_pencils(const __grid_constant__ PencilArgs a) {
   using T = typename Cx<R>::T;
   constexpr int NT = N * TX;
@@ -735,20 +738,35 @@ __global__ void __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N
   __shared__ __align__(8) uint64_t mb_stage[2];  // [0] operand + T_xy, [1] Q + R
   uint32_t ph_x = 0, ph_q = 0;
   const uint32_t bytes_x = 2u * QB * NT * ((a.xr ? (uint32_t)sizeof(T) : 16u) + (uint32_t)sizeof(T));
-  const uint32_t bytes_q = 2u * QB * NT * (16u + (uint32_t)sizeof(T));
+  const uint32_t bytes_q = 2u * QB * NT * (16u + (ST ? 0u : (uint32_t)sizeof(T)));  // Q (and R unless ST)
   // tensor copies need 128-byte aligned destinations: checked, never assumed (a block whose
   // staging is misaligned copies nothing and reports through the error word)
   const bool stage_ok = (um::su32(xstage) & 127u) == 0;
+  // A wait that runs out sets bit 4 of the error word and `failed`; the block then stops at
+  // its next barrier (__syncthreads_or, so all its threads stop together), consumes no more
+  // staged data and issues no further copy.  Thread 0, which issues the copies, first waits
+  // (bounded) for the copy it gave up on, and before the block exits for any copy still in
+  // flight, so that no copy lands in the shared memory of a block that has exited.
+  bool failed = kPrefetch && !stage_ok;
+  bool pend[2] = {false, false};  // thread 0: copies issued on stage k that have not completed
   auto prefetch = [&](int qb) {
     if (threadIdx.x == 0 && stage_ok) {
       um::fence_proxy_async();  // the staging reads of the previous batch before the copies
       um::mbar_expect_tx(&mb_stage[0], bytes_x);
       um::tma_load_4d(xstage, &a.tm_x, 2 * x0, y, 0, 2 * qb, &mb_stage[0]);
       um::tma_load_4d(tstage, &a.tm_t, 2 * x0, y, 0, 2 * qb, &mb_stage[0]);
+      pend[0] = true;
     }
   };
   auto wait_stage = [&](int k, uint32_t& ph) {
-    if (stage_ok && !um::mbar_wait(&mb_stage[k], ph, 1L << 22) && a.err) atomicOr(a.err, 4);
+    if (stage_ok) {
+      if (!um::mbar_wait(&mb_stage[k], ph, wait_limit(a.wait_polls))) {
+        failed = true;
+        if (a.err) atomicOr(a.err, 4);
+        if (threadIdx.x == 0) um::mbar_wait(&mb_stage[k], ph, kDrainPolls);
+      }
+      if (threadIdx.x == 0) pend[k] = false;
+    }
     ph ^= 1u;
   };
   if constexpr (kPrefetch) {
@@ -785,14 +803,16 @@ __global__ void __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N
           buf[(2 * j + c) * CS + z * TX + xl] = v;
         }
       }
-      __syncthreads();  // also orders the staging reads above before the next batch's copies
+      // (also orders the staging reads above before the next batch's copies)
+      if (__syncthreads_or(failed)) break;
       if constexpr (MODE == M_CORRECT) {
         // this batch's Q and R (read in the epilogue, after the line transforms)
         if (threadIdx.x == 0 && stage_ok) {
           um::fence_proxy_async();
           um::mbar_expect_tx(&mb_stage[1], bytes_q);
           um::tma_load_4d(qstage, &a.tm_q, 2 * x0, y, 0, 2 * qb0, &mb_stage[1]);
-          um::tma_load_4d(rstage, &a.tm_r, 2 * x0, y, 0, 2 * qb0, &mb_stage[1]);
+          if constexpr (!ST) um::tma_load_4d(rstage, &a.tm_r, 2 * x0, y, 0, 2 * qb0, &mb_stage[1]);
+          pend[1] = true;
         }
       }
       // the staging buffers are free again: fetch the next batch while this one computes
@@ -891,25 +911,39 @@ __global__ void __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N
       } else if (MODE == M_CORRECT) {
         // Eq. c and Eq. y through Q, R:  y_{n+1} = Q + k1 m',  p - c = R - k2 m'
         const R k2 = kc2, k1 = kc1;
-        T yo[2];  // y_{n+1} in the compute precision, for its densities
+        T yo[2];          // y_{n+1} in the compute precision, for its densities
+        double2 yd[2];    // (ST: the FP64 values)
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
           const long i = c ? iv : iu;
           const T f = c ? fvr : fur;
           const int si_ = (2 * j + c) * NT + threadIdx.x;
-          const T rr = kPrefetch ? rstage[si_] : reinterpret_cast<const T*>(a.r)[i];
           double2 yn;
-          if constexpr (sizeof(R) == 8) {
-            const double2 qv = a.q[i];
-            yn = make_double2(fma((double)k1, (double)f.x, qv.x), fma((double)k1, (double)f.y, qv.y));
+          if constexpr (ST) {
+            // FP64 history arithmetic from the exact FP64 value of m'
+            const double2 fd = to_d(f), qv = kPrefetch ? qstage[si_] : a.q[i];
+            const double2 rr = reinterpret_cast<const double2*>(a.r)[i];
+            // (R and p - c in units of h/48, as in the FP64 path: p - c = R - 17 m')
+            const double k1d = 161.0 / 170.0 * 17.0 / 48.0 * a.h;
+            yn = make_double2(fma(k1d, fd.x, qv.x), fma(k1d, fd.y, qv.y));
+            reinterpret_cast<double2*>(a.pc)[i] = make_double2(fma(-17.0, fd.x, rr.x), fma(-17.0, fd.y, rr.y));
+            yd[c] = yn;
           } else {
-            yn = dadd(kPrefetch ? qstage[si_] : a.q[i], to_d(T{k1 * f.x, k1 * f.y}));
+            const T rr = kPrefetch ? rstage[si_] : reinterpret_cast<const T*>(a.r)[i];
+            if constexpr (sizeof(R) == 8) {
+              const double2 qv = a.q[i];
+              yn = make_double2(fma((double)k1, (double)f.x, qv.x), fma((double)k1, (double)f.y, qv.y));
+            } else {
+              yn = dadd(kPrefetch ? qstage[si_] : a.q[i], to_d(T{k1 * f.x, k1 * f.y}));
+            }
+            reinterpret_cast<T*>(a.pc)[i] = T{rr.x - k2 * f.x, rr.y - k2 * f.y};
           }
           a.ynew[i] = yn;
-          reinterpret_cast<T*>(a.pc)[i] = T{rr.x - k2 * f.x, rr.y - k2 * f.y};
           yo[c] = to_r<R>(yn);
         }
-        if constexpr (sizeof(R) == 4)
+        if constexpr (ST)
+          dens_acc(yd[0], yd[1], sn, sr, si);
+        else if constexpr (sizeof(R) == 4)
           dens_acc(yo[0], yo[1], dF);
         else
           dens_acc(yo[0], yo[1], sn, sr, si);
@@ -977,7 +1011,19 @@ __global__ void __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N
         a.eta_part[(long)(qb0 + threadIdx.x) * gridDim.x + blockIdx.x] = t;
       }
     }
-    __syncthreads();  // the batch buffer is reused
+    // the batch buffer is reused
+    if constexpr (kPrefetch) {
+      if (__syncthreads_or(failed)) break;
+    } else {
+      __syncthreads();
+    }
+  }
+  if constexpr (kPrefetch) {
+    // a block that stopped early lets the copies it issued land before it exits
+    if (threadIdx.x == 0) {
+      if (pend[0]) um::mbar_wait(&mb_stage[0], ph_x, kDrainPolls);
+      if (pend[1]) um::mbar_wait(&mb_stage[1], ph_q, kDrainPolls);
+    }
   }
   if (a.dens) {
     if constexpr (sizeof(R) == 4) dens_fold(dF, sn, sr, si);
@@ -1041,7 +1087,14 @@ __global__ void k_reduce(ReduceArgs a) {
 // mixed path, as the second half of every derivative/predictor step.  As in the
 // fused epilogue, the derivative combinations run in the compute precision R and
 // every sum with a state value in FP64.
-template <typename R>
+//
+// ST (FP32 compute precision): the strict split of LISE_MIXED_STRICT.  The derivative sums
+// are taken exactly in integers from the FP32 derivatives (pred_sums on their exact FP64
+// values: sp = 48 pt / h, sr = 48 R / h, each rounded once), R and p - c are complex128 in
+// units of h/48 (as in the FP64 path), P = hf + pt, Q = P - (161/170) R and
+// m = P - (161/170)(p - c) in FP64; m is rounded to FP32 only as the operand of the next
+// FP32 H psi, and its densities are taken from its FP64 value.
+template <typename R, bool ST = false>
 __global__ void k_predict(PointwiseArgs a) {
   using T = typename Cx<R>::T;
   const long s = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1052,6 +1105,34 @@ __global__ void k_predict(PointwiseArgs a) {
   const R c161 = (R)(161.0 / 170.0), c9 = (R)(9.0 / 170.0);
   double sn = 0, sr = 0, si = 0;
   DensF dF;  // FP32 operands (mixed path)
+  if constexpr (ST) {
+    const double h48d = a.h / 48.0, c161h = 161.0 / 170.0 * h48d;
+    for (int q = q_begin; q < q_end; ++q) {
+      double2 md[2];
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const long i = (long)(2 * q + c) * a.nxyz + s;
+        const double2 e0 = to_d(reinterpret_cast<const T*>(a.d0)[i]), e1 = to_d(reinterpret_cast<const T*>(a.d1)[i]),
+                      e2 = to_d(reinterpret_cast<const T*>(a.d2)[i]), e3 = to_d(reinterpret_cast<const T*>(a.d3)[i]);
+        double spx, srx, spy, sry;
+        pred_sums(e0.x, e1.x, e2.x, e3.x, spx, srx);
+        pred_sums(e0.y, e1.y, e2.y, e3.y, spy, sry);
+        const double2 pcv = reinterpret_cast<const double2*>(a.pc)[i];
+        const double2 y0 = a.y0[i], y1 = a.y1[i];
+        const double Px = fma(h48d, spx, half_exp(y0.x + y1.x)), Py = fma(h48d, spy, half_exp(y0.y + y1.y));
+        a.q[i] = make_double2(fma(-c161h, srx, Px), fma(-c161h, sry, Py));
+        reinterpret_cast<double2*>(a.r)[i] = make_double2(srx, sry);
+        md[c] = make_double2(fma(-c161h, pcv.x, Px), fma(-c161h, pcv.y, Py));
+        reinterpret_cast<T*>(a.m)[i] = to_r<R>(md[c]);
+      }
+      dens_acc(md[0], md[1], sn, sr, si);
+    }
+    const long o = (long)g * a.nxyz + s;
+    a.part_n[o] = 2.0 * sn;
+    a.part_nr[o] = sr;
+    a.part_ni[o] = si;
+    return;
+  }
   for (int q = q_begin; q < q_end; ++q) {
     T mo[2];  // m in the compute precision, for its densities
 #pragma unroll
@@ -1283,6 +1364,18 @@ __global__ void k_finite(const double2* x, long count, int* err) {
 }
 
 // ---------------------------------------------------------------- launchers --
+// cudaFuncSetAttribute acts on the current device only: raise a kernel's dynamic shared
+// memory limit once on every device it is launched on (done: one bit per device ordinal).
+static int smem_attr(const void* kern, size_t bytes, std::atomic<unsigned long long>& done) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 3;
+  const unsigned long long bit = dev >= 0 && dev < 64 ? (1ull << dev) : 0ull;
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return 0;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess) return 3;
+  if (bit) done.fetch_or(bit, std::memory_order_acq_rel);
+  return 0;
+}
+
 bool supported_n(int N) {
   switch (N) {
     case 8: case 12: case 16: case 20: case 24: case 32: case 40: case 48: case 64: return true;
@@ -1301,9 +1394,8 @@ template <int N>
 static int planes_oz_n(const PlanesArgs& a, cudaStream_t s) {
   using P = OzPlanes<N>;
   auto kern = k_planes_oz<N>;
-  // once per process (thread-safe initialisation of a function-local static)
-  static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P::smem);
-  if (attr != cudaSuccess) return 3;
+  static std::atomic<unsigned long long> attr_done{0};
+  if (smem_attr((const void*)kern, P::smem, attr_done)) return 3;
   const long blocks = (a.n_planes + P::PB - 1) / P::PB;
   if (blocks <= 0) return 0;
   if (!a.ozb) return 1;
@@ -1316,8 +1408,8 @@ template <int N>
 static int planes_tc_n(const PlanesArgs& a, cudaStream_t s) {
   using P = TcPlanes<N>;
   auto kern = k_planes_tc<N>;
-  static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P::smem);
-  if (attr != cudaSuccess) return 3;
+  static std::atomic<unsigned long long> attr_done{0};
+  if (smem_attr((const void*)kern, P::smem, attr_done)) return 3;
   if (a.n_planes <= 0) return 0;
   if (!a.ozb) return 1;
   int dev = 0, sms = 0;
@@ -1341,9 +1433,8 @@ static int planes_n(const PlanesArgs& a, cudaStream_t s) {
   constexpr int NT = 256;
   const size_t smem = (size_t)PB * N * (N + 1) * sizeof(T) + N * sizeof(T) + N * sizeof(R);
   auto kern = k_planes<R, N, PB, NT>;
-  // once per process (thread-safe initialisation of a function-local static)
-  static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (attr != cudaSuccess) return 3;
+  static std::atomic<unsigned long long> attr_done{0};
+  if (smem_attr((const void*)kern, smem, attr_done)) return 3;
   const long blocks = (a.n_planes + PB - 1) / PB;
   if (blocks <= 0) return 0;
   kern<<<(unsigned)blocks, NT, smem, s>>>(a);
@@ -1404,16 +1495,15 @@ static bool encode_stage_map(CUtensorMap* m, const void* base, bool c128, int N,
                 CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <typename R, int N, int MODE, int QB>
+template <typename R, int N, int MODE, int QB, bool ST>
 static int pencils_nmq(const PencilArgs& a, cudaStream_t s) {
   using T = typename Cx<R>::T;
   constexpr int TX = (pencil_oz<R, N>() || N % 8 != 0) ? 4 : 8;  // = pencil_tx
   const size_t smem = (size_t)pencil_smem_bytes<T, N, TX, QB>();
-  auto kern = k_pencils<R, N, TX, QB, MODE>;
+  auto kern = k_pencils<R, N, TX, QB, MODE, ST>;
   if (pencil_oz<R, N>() && !a.ozb) return 1;
-  // once per process (thread-safe initialisation of a function-local static)
-  static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (attr != cudaSuccess) return 3;
+  static std::atomic<unsigned long long> attr_done{0};
+  if (smem_attr((const void*)kern, smem, attr_done)) return 3;
   const int n_groups = (a.n_qp + a.qg - 1) / a.qg;
   dim3 grid((N / TX) * N, n_groups);
   if constexpr (sizeof(R) == 4) {
@@ -1422,13 +1512,21 @@ static int pencils_nmq(const PencilArgs& a, cudaStream_t s) {
     const bool ok = encode_stage_map(&b.tm_x, a.xr ? a.xr : (const void*)a.x, !a.xr, N, a.n_qp, TX, QB) &&
                     encode_stage_map(&b.tm_t, a.txy, false, N, a.n_qp, TX, QB) &&
                     (MODE != M_CORRECT || (encode_stage_map(&b.tm_q, a.q, true, N, a.n_qp, TX, QB) &&
-                                           encode_stage_map(&b.tm_r, a.r, false, N, a.n_qp, TX, QB)));
+                                           (ST || encode_stage_map(&b.tm_r, a.r, false, N, a.n_qp, TX, QB))));
     if (!ok) return 3;
     kern<<<grid, N * TX, smem, s>>>(b);
   } else {
     kern<<<grid, N * TX, smem, s>>>(a);
   }
   return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}
+
+// the strict-split corrector (LISE_MIXED_STRICT) of the FP32 compute precision, else the plain one
+template <typename R, int N, int MODE, int QB>
+static int pencils_nmq_st(const PencilArgs& a, cudaStream_t s) {
+  if constexpr (sizeof(R) == 4 && MODE == M_CORRECT)
+    if (a.strict) return pencils_nmq<R, N, MODE, QB, true>(a, s);
+  return pencils_nmq<R, N, MODE, QB, false>(a, s);
 }
 
 // the step's modes have QB = 2 and QB = 4 variants (where they fit); the others use the default
@@ -1438,13 +1536,13 @@ static int pencils_nm(const PencilArgs& a, cudaStream_t s, int qb) {
   if constexpr (kTunable) {
     if (qb == 0) qb = pencil_qb_get(N, sizeof(R) == 4);
     if constexpr (pencil_oz<R, N>())
-      if (qb == 1) return pencils_nmq<R, N, MODE, 1>(a, s);
+      if (qb == 1) return pencils_nmq_st<R, N, MODE, 1>(a, s);
     if constexpr (qb_fits<R, N, 2>())
-      if (qb == 2) return pencils_nmq<R, N, MODE, 2>(a, s);
+      if (qb == 2) return pencils_nmq_st<R, N, MODE, 2>(a, s);
     if constexpr (qb_fits<R, N, 4>())
-      if (qb == 4) return pencils_nmq<R, N, MODE, 4>(a, s);
+      if (qb == 4) return pencils_nmq_st<R, N, MODE, 4>(a, s);
   }
-  return pencils_nmq<R, N, MODE, qb_default<R, N>()>(a, s);
+  return pencils_nmq_st<R, N, MODE, qb_default<R, N>()>(a, s);
 }
 
 template <typename R, int N>
@@ -1511,7 +1609,9 @@ int launch_reduce(const ReduceArgs& a, cudaStream_t s) {
 int launch_predict(const PointwiseArgs& a, cudaStream_t s) {
   const int nt = 256;
   dim3 grid((unsigned)((a.nxyz + nt - 1) / nt), (a.n_qp + a.qg - 1) / a.qg);
-  if (a.mixed)
+  if (a.mixed && a.strict)
+    k_predict<float, true><<<grid, nt, 0, s>>>(a);
+  else if (a.mixed)
     k_predict<float><<<grid, nt, 0, s>>>(a);
   else
     k_predict<double><<<grid, nt, 0, s>>>(a);
@@ -1671,6 +1771,51 @@ int launch_eta_reduce(const double* eta_part, int n_qp, int n_blocks, double a3,
 }
 
 int pencil_blocks_x(int N, int mixed) { return (N / pencil_tx(N, mixed)) * N; }
+
+void choose_groups(int N, int n_qp, int mixed, int* qg, int* n_groups) {
+  const int tiles = pencil_blocks_x(N, mixed);
+  int q = 64;
+  while (q > 4 && (long)tiles * ((n_qp + q - 1) / q) < 2048) q /= 2;
+  if (q > n_qp) q = n_qp;
+  *qg = q;
+  *n_groups = (n_qp + q - 1) / q;
+}
+
+template <typename R>
+static void fft_tables_r(int N, double a, double alpha, R* tw, R* hxy, R* hz) {
+  const long double PI = 3.141592653589793238462643383279502884L;
+  // twiddles tw[j2 N1 + k1] = exp(-2 pi i (j2 k1 mod N) / N); the four-step plan reads
+  // entries with j2 < N2, k1 < N1 only
+  int N1 = 0;
+  switch (N) {
+    case 8: N1 = 2; break;
+    case 12: case 16: case 20: case 24: case 32: N1 = 4; break;
+    default: N1 = 8; break;
+  }
+  const int N2 = N / N1;
+  for (int j2 = 0; j2 < N2; ++j2)
+    for (int k1 = 0; k1 < N1; ++k1) {
+      const long e = ((long)j2 * k1) % N;
+      const long double ang = -2.0L * PI * (long double)e / (long double)N;
+      tw[2 * (j2 * N1 + k1)] = (R)cosl(ang);
+      tw[2 * (j2 * N1 + k1) + 1] = (R)sinl(ang);
+    }
+  const long double L = (long double)N * a;
+  for (int k = 0; k < N; ++k) {
+    // Sec. "Discretization": k = 2 pi n / L over n = -N/2 .. N/2-1 (index n mod N)
+    const long double kk = 2.0L * PI * (long double)(k < N / 2 ? k : k - N) / L;
+    const long double f = 0.5L * alpha * kk * kk;
+    hxy[k] = (R)(f / ((long double)N * N));
+    hz[k] = (R)(f / (long double)N);
+  }
+}
+
+void fill_fft_tables(int N, double a, double alpha, int mixed, void* tw, void* hxy, void* hz) {
+  if (mixed)
+    fft_tables_r<float>(N, a, alpha, (float*)tw, (float*)hxy, (float*)hz);
+  else
+    fft_tables_r<double>(N, a, alpha, (double*)tw, (double*)hxy, (double*)hz);
+}
 
 int launch_finite_check(const double2* x, long count, int* err, cudaStream_t s) {
   k_finite<<<148 * 4, 256, 0, s>>>(x, count, err);

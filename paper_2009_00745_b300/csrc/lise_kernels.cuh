@@ -21,6 +21,15 @@
 
 namespace lise {
 
+// Bounded waits on the hardware (tensor-core completion, tensor-memory-accelerator copies):
+// polls before a wait gives up.  The drain waits that let work already in flight finish
+// before a block frees its tensor memory or exits always use kDrainPolls.
+constexpr long kDefaultWaitPolls = 1L << 22;
+constexpr long kDrainPolls = 1L << 22;
+__host__ __device__ inline long wait_limit(long wait_polls) {
+  return wait_polls == 0 ? kDefaultWaitPolls : (wait_polls < 0 ? 0L : wait_polls);
+}
+
 enum PencilMode : int {
   M_RHS = 0,            // out = -i H x
   M_TAYLOR_FIRST = 1,   // h = H x; [dslot = -i h]; term = coef h -> out; acc = x + term
@@ -67,6 +76,9 @@ struct PencilArgs {
   const double* eta;      // if non-null: apply H - eta_q (trivial-phase removal), eta per state
   double* eta_part;       // M_ETA output: [state][block] partial sums
   int* err;               // device error word: bit 4 set when a bounded wait ran out
+  long wait_polls;        // bounded waits: 0 = kDefaultWaitPolls, < 0 = give up at once, else polls
+  int strict;             // FP32 compute precision: the strict split (LISE_MIXED_STRICT), R and
+                          // p - c in complex128 (units of h/48), the corrector's update in FP64
   // FP32 compute precision: tensor maps of the batch staging copies (operand, T_xy, and the
   // corrector's Q and R), written by launch_pencils from the pointers above
   CUtensorMap tm_x;
@@ -85,6 +97,7 @@ struct PlanesArgs {
   int oz_sD;
   long n_planes;
   int* err;               // device error word: bit 4 set when a bounded wait ran out
+  long wait_polls;        // as in PencilArgs
 };
 
 struct ReduceArgs {
@@ -127,6 +140,7 @@ struct PointwiseArgs {
   void* r;                 // compute precision
   void* m;                 // m in the compute precision of the path
   int mixed;
+  int strict;              // mixed only: the strict split (k_predict's ST)
   double h;
   // density partials of `src` (for the plain density pass) or of m
   const double2* src;
@@ -200,5 +214,13 @@ int ozaki_table(int N, double a, double alpha, uint32_t* out);
 int pencil_tx(int N, int mixed);
 int pencil_qb(int N, int mixed);
 bool supported_n(int N);
+// Density groups of a context (and of the no-allocation right-hand side): at most 64 states
+// per group, fewer while the pencils grid would have fewer than 2048 blocks.
+void choose_groups(int N, int n_qp, int mixed, int* qg, int* n_groups);
+// Host tables of the FFT kernels for lattice N, spacing a: twiddles tw[2 N]
+// (tw[j2 N1 + k1] = exp(-2 pi i j2 k1 / N) of the four-step plan, re/im interleaved) and the
+// kinetic factors hxy[k] = (alpha/2) k^2 / N^2, hz[k] = (alpha/2) k^2 / N (Sec.
+// "Discretization" k grid), in the compute precision (float if mixed); no heap use.
+void fill_fft_tables(int N, double a, double alpha, int mixed, void* tw, void* hxy, void* hz);
 
 }  // namespace lise

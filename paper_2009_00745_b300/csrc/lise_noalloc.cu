@@ -19,6 +19,7 @@
 #include <cstring>
 
 #include "../../include/lise.h"
+#include "lise_internal.h"
 #include "lise_kernels.cuh"
 
 using namespace lise;
@@ -30,8 +31,6 @@ namespace {
 constexpr int kMaxDevices = 64;
 unsigned char* g_scratch_dev[kMaxDevices] = {};  // device address of g_rhs_scratch per device
 
-constexpr long double kPi = 3.141592653589793238462643383279502884L;
-
 // FFT twiddles and kinetic factors, built on the host into static storage (no
 // heap allocation) and copied into the scratch array on every call.
 alignas(16) double g_tab_d[4 * 64];
@@ -39,48 +38,21 @@ alignas(16) float g_tab_f[4 * 64];
 // D2 digit fragments of the FP64 tensor-core path (largest lattice: 64)
 alignas(16) uint32_t g_tab_oz[7 * 8 * 4 * 32 * 2];
 
-template <typename R>
-void tables(int N, double a, double alpha, R* tw, R* hxy, R* hz) {
-  const int N1 = (N == 8) ? 2 : ((N == 12 || N == 16 || N == 20 || N == 24 || N == 32) ? 4 : 8);
-  const int N2 = N / N1;
-  for (int j2 = 0; j2 < N2; ++j2)
-    for (int k1 = 0; k1 < N1; ++k1) {
-      const long e = ((long)j2 * k1) % N;
-      const long double ang = -2.0L * kPi * (long double)e / (long double)N;
-      tw[2 * (j2 * N1 + k1)] = (R)cosl(ang);
-      tw[2 * (j2 * N1 + k1) + 1] = (R)sinl(ang);
-    }
-  const long double L = (long double)N * a;
-  for (int k = 0; k < N; ++k) {
-    const long double kk = 2.0L * kPi * (long double)(k < N / 2 ? k : k - N) / L;
-    const long double f = 0.5L * alpha * kk * kk;
-    hxy[k] = (R)(f / ((long double)N * N));
-    hz[k] = (R)(f / (long double)N);
-  }
-}
-
 size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 }  // namespace
 
 extern "C" int lise_rhs_noalloc(const lise_params* p, const double* psi_dev, double t, double* dpsi_dev) {
-  if (!p || !psi_dev || !dpsi_dev || !std::isfinite(t)) return LISE_EINVAL;
-  if (p->nx != p->ny || p->ny != p->nz || !supported_n(p->nx) || !(p->dx > 0.0) || p->n_qp < 1) return LISE_EINVAL;
-  if (p->precision != LISE_FP64 && p->precision != LISE_MIXED) return LISE_EINVAL;
+  if (!psi_dev || !dpsi_dev || !std::isfinite(t)) return LISE_EINVAL;
+  if (check_params(p) != LISE_OK) return LISE_EINVAL;  // the same validation as lise_create
   if (p->device < 0 || p->device >= kMaxDevices) return LISE_EINVAL;
-  if (p->pair_lattice && !(p->alpha > 0.0)) return LISE_EINVAL;
-  if (p->pair_alpha != 0.0 && !(p->pair_n0 > 0.0)) return LISE_EINVAL;
   const int N = p->nx;
   const long nxyz = (long)N * N * N;
   const long ns = (long)p->n_qp * 2 * nxyz;
-  const bool mixed = p->precision == LISE_MIXED;
-  // density groups: same rule as a context (at most 64 states per group,
-  // enough groups to fill the GPU)
-  const int tiles = (N / pencil_tx(N, mixed)) * N;
-  int qg = 64;
-  while (qg > 4 && (long)tiles * ((p->n_qp + qg - 1) / qg) < 2048) qg /= 2;
-  if (qg > p->n_qp) qg = p->n_qp;
-  const int n_groups = (p->n_qp + qg - 1) / qg;
+  const bool mixed = p->precision != LISE_FP64;  // (one right-hand side: both mixed splits alike)
+  // density groups: the rule of a context
+  int qg = 0, n_groups = 0;
+  choose_groups(N, p->n_qp, mixed, &qg, &n_groups);
 
   // carve the scratch array; reject problems that do not fit
   const size_t rs = mixed ? sizeof(float) : sizeof(double);
@@ -117,10 +89,10 @@ extern "C" int lise_rhs_noalloc(const lise_params* p, const double* psi_dev, dou
   // tables and the static potential into the scratch; the error word starts at zero
   void* tab_host;
   if (mixed) {
-    tables<float>(N, p->dx, p->alpha, g_tab_f, g_tab_f + 2 * N, g_tab_f + 3 * N);
+    fill_fft_tables(N, p->dx, p->alpha, 1, g_tab_f, g_tab_f + 2 * N, g_tab_f + 3 * N);
     tab_host = g_tab_f;
   } else {
-    tables<double>(N, p->dx, p->alpha, g_tab_d, g_tab_d + 2 * N, g_tab_d + 3 * N);
+    fill_fft_tables(N, p->dx, p->alpha, 0, g_tab_d, g_tab_d + 2 * N, g_tab_d + 3 * N);
     tab_host = g_tab_d;
   }
   if (cudaMemcpyAsync(base + o_tab, tab_host, 4 * (size_t)N * rs, cudaMemcpyHostToDevice, s) != cudaSuccess)
@@ -192,6 +164,7 @@ extern "C" int lise_rhs_noalloc(const lise_params* p, const double* psi_dev, dou
   pa.oz_sD = oz_sD;
   pa.n_planes = (long)p->n_qp * 2 * N;
   pa.err = err;
+  pa.wait_polls = 0;  // the default bound
   if (launch_planes(N, mixed, pa, s)) return LISE_ECUDA;
   PencilArgs ka;
   std::memset(&ka, 0, sizeof(ka));

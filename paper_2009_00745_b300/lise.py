@@ -17,8 +17,10 @@ LIB_PATH = os.path.join(_HERE, "liblise.so")
 
 FP64 = 0
 MIXED = 1
+MIXED_STRICT = 2
+PRECISIONS = {"fp64": FP64, "mixed": MIXED, "mixed_strict": MIXED_STRICT}
 
-OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ESTATE = range(7)
+OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ESTATE, EEXCHANGE = range(8)
 ADMIT_FIFO, ADMIT_FIRST_FIT = 0, 1
 KC_PLANES, KC_PENCILS, KC_REDUCE, KC_POINTWISE, KC_COUNT = range(5)
 
@@ -39,6 +41,16 @@ class _Params(C.Structure):
                 ("pair_lattice", C.c_int), ("renormalize", C.c_int)]
 
 
+# lise_exchange_fn and lise_shard (sharded densities)
+EXCHANGE_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_long, C.c_int, C.c_int,
+                          C.c_int)
+
+
+class _Shard(C.Structure):
+    _fields_ = [("group_size", C.c_int), ("first_group", C.c_int), ("n_groups_all", C.c_int),
+                ("exchange", EXCHANGE_FN), ("user", C.c_void_p), ("on_device", C.c_int), ("capturable", C.c_int)]
+
+
 # Exported functions with their ctypes signatures (mirrors include/lise.h).
 SIGNATURES = {
     "lise_footprint_bytes": (C.c_size_t, [C.c_void_p]),
@@ -57,12 +69,15 @@ SIGNATURES = {
     "lise_energy": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "lise_rhs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_void_p]),
     "lise_sync": (C.c_int, [C.c_void_p]),
+    "lise_set_wait_limit": (C.c_int, [C.c_void_p, C.c_long]),
+    "lise_set_shard": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lise_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "lise_profile_read": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_long), C.POINTER(C.c_double)]),
     "lise_kernel_class_name": (C.c_char_p, [C.c_int]),
     "lise_strerror": (C.c_char_p, [C.c_int]),
     "lise_destroy": (None, [C.c_void_p]),
     "lise_rhs_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_void_p]),
+    "lise_measure_fp64_peak": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
     "lise_checkpoint_bytes": (C.c_size_t, [C.c_void_p]),
     "lise_checkpoint_save": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "lise_checkpoint_load": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
@@ -108,7 +123,7 @@ def _check(rc, where):
 def _params(N, n_qp, a, alpha, beta, mu, g, v_static, drive_A, drive_Omega, precision, device,
             hbm_budget_bytes, stream, remove_phase=False, pair_alpha=0.0, pair_n0=1.0, pair_lattice=False,
             renormalize=False):
-    prec = {"fp64": FP64, "mixed": MIXED}.get(precision, precision)
+    prec = PRECISIONS.get(precision, precision)
     vs = None
     if v_static is not None:
         vs = np.ascontiguousarray(v_static, dtype=np.float64).reshape(-1)
@@ -123,14 +138,21 @@ def _params(N, n_qp, a, alpha, beta, mu, g, v_static, drive_A, drive_Omega, prec
 
 def pencil_batch(N, precision="fp64") -> int:
     """States per batch the pencils kernel uses for this lattice and precision (tuned or default)."""
-    return int(load().lise_pencil_batch(int(N), {"fp64": FP64, "mixed": MIXED}[precision]))
+    return int(load().lise_pencil_batch(int(N), PRECISIONS[precision]))
 
 
 def set_pencil_batch(N, precision="fp64", qb=0):
     """Force the pencils batch size (1 for the FP64 tensor-core kernels, 2 or 4), or qb = 0 to
     re-tune at the next set_state."""
-    _check(load().lise_set_pencil_batch(int(N), {"fp64": FP64, "mixed": MIXED}[precision], int(qb)),
+    _check(load().lise_set_pencil_batch(int(N), PRECISIONS[precision], int(qb)),
            "lise_set_pencil_batch")
+
+
+def measure_fp64_peak(device=0) -> float:
+    """FP64 FMA throughput of the device (TFLOP/s) from the library's probe kernel."""
+    t = C.c_double()
+    _check(load().lise_measure_fp64_peak(int(device), C.byref(t)), "lise_measure_fp64_peak")
+    return t.value
 
 
 def footprint_bytes(N, n_qp, precision="fp64", **kw) -> int:
@@ -282,6 +304,37 @@ class Context:
 
     def sync(self):
         _check(load().lise_sync(self._h), "lise_sync")
+
+    def set_shard(self, group_size, first_group=0, n_groups_all=None, exchange=None, on_device=False,
+                  capturable=False):
+        """Sharded densities (lise_set_shard): this context holds n_qp of the evolution's states,
+        its density groups are first_group .. of n_groups_all groups of group_size states.
+        exchange(parts, on_device, stream, nxyz, first_group, n_local, n_groups_all) fills the
+        other shards' groups of the partial-sum block at address `parts` (see shard.py); an
+        exception in it fails the library call with EEXCHANGE.  Call before set_state."""
+        n_local = -(-self.n_qp // int(group_size))
+        if n_groups_all is None:
+            n_groups_all = first_group + n_local
+        if exchange is None:
+            cb = EXCHANGE_FN()
+        else:
+            def cb_py(user, parts, on_dev, stream, nxyz, first, nloc, nall):
+                try:
+                    exchange(parts, bool(on_dev), stream, nxyz, first, nloc, nall)
+                    return 0
+                except Exception:
+                    import traceback
+                    traceback.print_exc()
+                    return 1
+            cb = EXCHANGE_FN(cb_py)
+        sh = _Shard(int(group_size), int(first_group), int(n_groups_all), cb, None, int(bool(on_device)),
+                    int(bool(capturable)))
+        _check(load().lise_set_shard(self._h, C.byref(sh)), "lise_set_shard")
+        self._exchange_cb = cb  # kept alive while the library may call it
+
+    def set_wait_limit(self, polls):
+        """Polls before a bounded device wait gives up (> 0), 0 = give up at once, < 0 = default."""
+        _check(load().lise_set_wait_limit(self._h, int(polls)), "lise_set_wait_limit")
 
 
 class RequestInfo(C.Structure):

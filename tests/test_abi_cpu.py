@@ -48,6 +48,9 @@ def test_footprint_model():
     fm = L.footprint_bytes(48, 4096, precision="mixed")
     # mixed: y_n, y_{n-1}, Q in complex128; the y' ring, m, R, p - c and T_xy in complex64
     assert abs(fm - (3 * 16 + 8 * 8) * 4096 * 2 * 48 ** 3) / fm < 0.02
+    fs = L.footprint_bytes(48, 4096, precision="mixed_strict")
+    # strict split: R and p - c in complex128 as well
+    assert abs(fs - (5 * 16 + 6 * 8) * 4096 * 2 * 48 ** 3) / fs < 0.02
     assert L.footprint_bytes(30, 8) == 0  # unsupported lattice
 
 
@@ -85,7 +88,22 @@ def test_null_arguments(lib):
     assert lib.lise_create(None, None) == L.EINVAL
     assert lib.lise_step(None, 1, 0.1) == L.EINVAL
     assert lib.lise_sync(None) == L.EINVAL
+    assert lib.lise_set_wait_limit(None, 0) == L.EINVAL
     lib.lise_destroy(None)
+
+
+@pytest.mark.parametrize("field", ["alpha", "beta", "mu", "g", "drive_A", "drive_Omega", "dx"])
+def test_noalloc_validates_parameters_before_any_device_call(lib, field):
+    # lise_rhs_noalloc applies lise_create's checks first: a non-finite parameter is
+    # rejected without touching the (here absent) device; the buffer addresses are never used
+    p, _ = L._params(16, 4, 1.0, 1.0, -0.5, 0.2, 0.7, None, 0.01, 0.3, "fp64", 0, 0, None)
+    setattr(p, field, float("nan"))
+    fake = C.c_void_p(4096)
+    assert lib.lise_rhs_noalloc(C.byref(p), fake, 0.0, fake) == L.EINVAL
+    p.dx = 1.0
+    p.alpha = p.beta = p.mu = p.g = p.drive_A = p.drive_Omega = 0.0
+    p.pair_alpha, p.pair_n0 = 0.5, 0.0   # Eq. g0 needs n0 > 0
+    assert lib.lise_rhs_noalloc(C.byref(p), fake, 0.0, fake) == L.EINVAL
 
 
 def test_pencil_batch_controls_host_only():

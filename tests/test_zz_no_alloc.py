@@ -26,12 +26,13 @@ def _noalloc(p, psi_dev, t, out_dev):
     return L.load().lise_rhs_noalloc(C.byref(p), psi_dev.data_ptr(), float(t), out_dev.data_ptr())
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", TOL_RHS), ("mixed", TOL_RHS)])
-def test_noalloc_matches_context_rhs_twice(precision, tol):
+@pytest.mark.parametrize("N,n_qp,precision,tol", [(16, 24, "fp64", TOL_RHS), (16, 24, "mixed", TOL_RHS),
+                                                  (32, 24, "fp64", TOL_RHS)])
+def test_noalloc_matches_context_rhs_twice(N, n_qp, precision, tol):
+    # (32^3 FP64 runs the tensor-memory planes kernel with its core-matrix D2 table)
     import torch
     from paper_2009_00745_b300 import build
     build.build()
-    N, n_qp = 16, 24
     kw = dict(a=0.9, alpha=1.2, beta=-0.5, mu=0.35, g=0.8, drive_A=0.02, drive_Omega=0.3)
     vs = np.random.default_rng(5).uniform(-0.5, 0.5, (N, N, N))
     psis = [random_state(N, n_qp, seed=11), random_state(N, n_qp, seed=12, kmax=5)]
@@ -44,11 +45,17 @@ def test_noalloc_matches_context_rhs_twice(precision, tol):
     p, keep = L._params(N, n_qp, kw["a"], kw["alpha"], kw["beta"], kw["mu"], kw["g"], vs, kw["drive_A"],
                         kw["drive_Omega"], precision, 0, 0, None)
     out = torch.empty((n_qp, 2, N, N, N), dtype=torch.complex128, device="cuda:0")
-    for psi, t, ref in zip(psis, times, refs):
-        x = torch.from_numpy(psi).to("cuda:0")
+    xs = [torch.from_numpy(psi).to("cuda:0") for psi in psis]
+    for k, (x, t, ref) in enumerate(zip(xs, times, refs)):
         out.fill_(float("nan"))
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info(0)[0]
         rc = _noalloc(p, x, t, out)
+        free1 = torch.cuda.mem_get_info(0)[0]
         assert rc == L.OK, L.strerror(rc)
+        if k > 0:
+            # after the first call (module loading, the symbol lookup) a call allocates nothing
+            assert free1 == free0
         got = out.cpu().numpy()
         assert np.isfinite(got).all()
         assert rel(got, ref) < tol
@@ -77,3 +84,13 @@ def test_noalloc_phase_removal_matches_context():
         out.fill_(float("nan"))
         assert _noalloc(p, x, 0.7, out) == L.OK
         assert rel(out.cpu().numpy(), ref) < TOL_RHS
+
+
+def test_noalloc_rejects_non_finite_parameters():
+    # the same parameter checks as lise_create: a NaN coefficient never reaches a kernel
+    import torch
+    x = torch.zeros(1, dtype=torch.complex128, device="cuda:0")
+    for field in ("alpha", "beta", "mu", "g", "drive_A", "drive_Omega", "pair_alpha"):
+        p, _ = L._params(8, 2, 1.0, 1.0, -0.5, 0.1, 0.5, None, 0.01, 0.3, "fp64", 0, 0, None)
+        setattr(p, field, float("nan"))
+        assert _noalloc(p, x, 0.0, x) == L.EINVAL, field

@@ -326,7 +326,8 @@ def run_serve(args):
     [256, 4096], and runs 100 mixed-precision ABM steps; the server admits them
     under a 150 GB budget.  Each request evolves the first n_qp states of its
     lattice's 4096-state homogeneous BCS workload (built before the clock starts).
-    Latency = done - arrival (arrival = the scheduled Poisson time)."""
+    Latency = done - arrival (arrival = the scheduled Poisson time).  The active requests are
+    stepped together in shared launches (the server's batching) unless --serve-separate."""
     import numpy as np
     from paper_2009_00745_b300 import lise as L
     from paper_2009_00745_b300 import workloads as Wl
@@ -343,6 +344,8 @@ def run_serve(args):
     budget = int(args.serve_budget_gb * 1e9)
     lag, sub_host, ids = [], [], []
     with L.Server(budget, max_active=args.serve_max_active, steps_per_turn=args.serve_turn) as srv:
+        if not args.serve_separate:
+            srv.set_batching(True)
         t0 = time.perf_counter()
         for i in range(R):
             delay = t0 + arrivals[i] - time.perf_counter()
@@ -361,6 +364,7 @@ def run_serve(args):
     units = sum(float(n) * int(l) ** 3 * args.serve_steps for n, l in zip(nqps, lattices))
     makespan = max(inf["done_s"] for inf in infos) - min(inf["submit_s"] for inf in infos)
     line = {"mode": "serve", "requests": R, "rate_per_s": args.serve_rate, "steps_per_request": args.serve_steps,
+            "stepping": "separate contexts" if args.serve_separate else "shared launches (lise_batch)",
             "precision": "mixed", "hbm_budget_gb": args.serve_budget_gb, "max_active": args.serve_max_active,
             "steps_per_turn": args.serve_turn,
             "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
@@ -385,7 +389,8 @@ def run_batch(args):
     with at most --batch-max-skips passes over any one evolution.  All are
     submitted at t = 0 without host copies (the server reads each initial state
     from the caller's array at admission).  Reported: aggregate throughput,
-    makespan and the schedule."""
+    makespan and the schedule.  The active evolutions are stepped together in shared
+    launches (lise_batch through the server's batching) unless --batch-separate."""
     import numpy as np
     from paper_2009_00745_b300 import lise as L
     from paper_2009_00745_b300 import workloads as Wl
@@ -403,6 +408,8 @@ def run_batch(args):
     fps = [L.footprint_bytes(int(l), int(nq), precision="mixed") for l, nq in zip(lattices, nqps)]
     with L.Server(budget, max_active=args.batch_max_active, steps_per_turn=args.serve_turn) as srv:
         srv.set_admission("first_fit", max_skips=args.batch_max_skips)
+        if not args.batch_separate:
+            srv.set_batching(True)
         t0 = time.perf_counter()
         ids = []
         for i in range(R):
@@ -429,6 +436,7 @@ def run_batch(args):
         timeline.append({"t_s": round(tk, 2), "active": len(live),
                          "resident_gb": round(sum(fps[i] for i in live) / 1e9, 1)})
     line = {"mode": "batch", "evolutions": R, "steps_per_evolution": args.batch_steps, "precision": "mixed",
+            "stepping": "separate contexts" if args.batch_separate else "shared launches (lise_batch)",
             "hbm_budget_gb": args.batch_budget_gb, "max_active": args.batch_max_active,
             "admission": "first fit, max %d skips" % args.batch_max_skips,
             "steps_per_turn": args.serve_turn, "sum_footprint_gb": round(sum(fps) / 1e9, 1),
@@ -628,6 +636,8 @@ def main():
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     ap.add_argument("--serve-max-active", type=int, default=8)
     ap.add_argument("--serve-turn", type=int, default=5)
+    ap.add_argument("--serve-separate", action="store_true",
+                    help="step every request on its own (no shared launches)")
     ap.add_argument("--batch", action="store_true",
                     help="run a batch of uneven evolutions through the server in HBM-budgeted waves")
     ap.add_argument("--batch-evolutions", type=int, default=64)
@@ -635,6 +645,8 @@ def main():
     ap.add_argument("--batch-budget-gb", type=float, default=200.0)
     ap.add_argument("--batch-max-active", type=int, default=8)
     ap.add_argument("--batch-max-skips", type=int, default=8)
+    ap.add_argument("--batch-separate", action="store_true",
+                    help="step every evolution on its own (no shared launches)")
     ap.add_argument("--pencil-batch", type=int, default=0,
                     help="force the pencils kernel's states per batch (default: autotuned)")
     args = ap.parse_args()

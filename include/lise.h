@@ -134,6 +134,15 @@ int lise_set_state_device(lise_ctx *c, const double *psi_dev, double t0, double 
  * exist) or, with qb = 0, clears the choice so that the next lise_set_state tunes. */
 int lise_pencil_batch(int N, int precision);
 int lise_set_pencil_batch(int N, int precision, int qb);
+/* The same for the planes per block of the FFT planes kernel (the in-plane part T_xy on
+ * lattices that do not use the tensor-core planes kernels: the mixed path, and FP64 with N
+ * not a multiple of 16): candidates 1, 2, 4, 8 where the variant fits in shared memory and
+ * registers, tuned on the first lise_set_state of each lattice and precision; results do
+ * not depend on it (every plane is transformed on its own).  lise_planes_per_block returns
+ * the value in use (0 for the tensor-core lattices or an unsupported N); the setter forces
+ * pb or clears it with pb = 0 (LISE_EINVAL for a variant that does not exist). */
+int lise_planes_per_block(int N, int precision);
+int lise_set_planes_per_block(int N, int precision, int pb);
 
 /* Current density of Eq. j of the current state (spin factor 2):
  * j(r) = 2 sum_k Im(v_k grad v_k^*), with the spectral first derivative
@@ -242,10 +251,40 @@ int lise_server_poll(lise_server *s, long id, int *done);
 #define LISE_ADMIT_FIFO 0
 #define LISE_ADMIT_FIRST_FIT 1
 int lise_server_set_admission(lise_server *s, int policy, int max_skips);
+/* Batched stepping (off by default; set before the first submission, else LISE_ESTATE):
+ * the active requests of each FP32 compute precision (LISE_MIXED, LISE_MIXED_STRICT;
+ * without remove_phase or renormalize) are stepped together through one lise_batch,
+ * rebuilt whenever a request joins (once its series start has finished) or leaves; the
+ * others are stepped one by one.  Results are unchanged (bitwise). */
+int lise_server_set_batching(lise_server *s, int enable);
 /* Largest sum of admitted footprints and largest number of active requests seen. */
 int lise_server_stats(lise_server *s, size_t *peak_used_bytes, int *peak_active);
 /* Finishes every submitted request, stops the worker and frees the server. */
 void lise_server_destroy(lise_server *s);
+
+/* Batched evolutions: several contexts (any lattice sizes and state counts) of the FP32
+ * compute precision (all LISE_MIXED or all LISE_MIXED_STRICT, on one device, without
+ * remove_phase, renormalize or sharding), each after lise_set_state, stepped together.
+ * Every kernel of an ABM step runs as one launch per lattice size over all evolutions of
+ * that size (a device work table maps each block to an evolution and state group), and
+ * four steps are captured as one CUDA graph; each evolution keeps its own dt, drive and
+ * time.  The arguments are those lise_step uses, so every evolution's result is bitwise
+ * the same as stepping its context alone.  No counterpart in the paper, which batches
+ * the FFTs of one evolution's states (Sec. "FFT in batch").
+ * lise_batch_create waits for the contexts' pending work and builds the work tables
+ * (device memory owned by the batch).  While a context belongs to a live batch, use it
+ * only through the batch until lise_batch_sync (or lise_batch_destroy) returns; after
+ * that every context call works as usual (the contexts' times and histories have moved
+ * on), and a context stepped on its own can no longer be stepped by the batch
+ * (LISE_ESTATE).  lise_batch_step enqueues n_steps steps of every member on the batch's
+ * stream; lise_batch_sync waits and reports the first member's sticky error.
+ * Errors: LISE_EINVAL (null, duplicate or unsuitable contexts), LISE_ESTATE (a context
+ * without a state, or moved on outside the batch), LISE_ENOMEM, LISE_ECUDA. */
+typedef struct lise_batch lise_batch;
+int lise_batch_create(lise_ctx *const *ctxs, int n, lise_batch **out);
+int lise_batch_step(lise_batch *b, int n_steps);
+int lise_batch_sync(lise_batch *b);
+void lise_batch_destroy(lise_batch *b);
 
 /* Per-launch timing.  Kernel classes of the path: */
 #define LISE_KC_PLANES 0    /* in-plane 2D FFT -> kinetic multiply -> inverse (T_xy) */

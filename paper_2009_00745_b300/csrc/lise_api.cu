@@ -17,6 +17,8 @@
 //   planes(y_{n+1}), pencils[DERIV_PREDICT]
 //                                      y'_{n+1}; m_{n+2}, Q, R; densities of m_{n+2}
 //   reduce                             W, Delta of m_{n+2} at t_{n+2}
+#include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -204,7 +206,7 @@ PencilArgs pencil_base(const lise_ctx* c) {
   return a;
 }
 
-int run_planes(lise_ctx* c, const double2* x, const void* xr = nullptr) {
+PlanesArgs planes_args(const lise_ctx* c, const double2* x, const void* xr) {
   PlanesArgs a;
   a.x = x;
   a.xr = xr;
@@ -216,6 +218,11 @@ int run_planes(lise_ctx* c, const double2* x, const void* xr = nullptr) {
   a.n_planes = (long)c->p.n_qp * 2 * c->N;
   a.err = c->err;
   a.wait_polls = c->wait_polls;
+  return a;
+}
+
+int run_planes(lise_ctx* c, const double2* x, const void* xr = nullptr) {
+  const PlanesArgs a = planes_args(c, x, xr);
   return timed(c, LISE_KC_PLANES, [&] { return launch_planes(c->N, c->mixed, a, c->stream) ? LISE_ECUDA : LISE_OK; });
 }
 
@@ -260,14 +267,13 @@ int exchange_parts(lise_ctx* c) {
   return cu(cudaMemcpyAsync(c->parts, c->host_parts, 3 * plane * sizeof(double), cudaMemcpyHostToDevice, c->stream));
 }
 
-// Reduce the density partials; optionally average with (avg_n, avg_nu); write
-// the densities to slot `dslot` and, if potentials is true, W and Delta at t.
-// all_shards = false reduces this context's own groups only (no exchange).
-int run_reduce(lise_ctx* c, int dslot, const double* avg_n, const double2* avg_nu, bool potentials, double t,
-               bool all_shards = true) {
+// The reduction's arguments without the drive (drive = 0, no drive pointer): the partial
+// sums of all shards' groups (or of this context's own with all_shards = false), densities
+// into slot dslot, averaged with (avg_n, avg_nu) if given, potentials if requested.
+ReduceArgs reduce_args(const lise_ctx* c, int dslot, const double* avg_n, const double2* avg_nu, bool potentials,
+                       bool all_shards) {
   ReduceArgs r;
   if (all_shards) {
-    TRY(exchange_parts(c));
     const size_t plane = (size_t)c->n_groups_all * c->nxyz;
     r.part_n = c->parts;
     r.part_nr = c->parts + plane;
@@ -289,19 +295,30 @@ int run_reduce(lise_ctx* c, int dslot, const double* avg_n, const double2* avg_n
   r.W = potentials ? c->W : nullptr;
   r.D = potentials ? c->Dl : nullptr;
   r.v_static = c->v_static;
-  r.drive = drive_at(c, t);
+  r.drive = 0.0;
   r.drive_ptr = nullptr;
-  if (c->capturing) {  // inside a graph: the amplitude is refreshed before every replay
-    if (c->p.drive_A != 0.0) r.drive_ptr = c->drive_dev + (c->capturing - 1);
-    c->drive_host_t[c->capturing - 1] = t;
-    ++c->capturing;
-  }
   r.beta = c->p.beta;
   r.mu = c->p.mu;
   r.g = c->p.g;
   r.pair_alpha_n0 = c->p.pair_alpha != 0.0 ? c->p.pair_alpha / c->p.pair_n0 : 0.0;
   r.pair_c = c->p.pair_lattice ? pairing_lattice_c(c->p.dx, c->p.alpha) : 0.0;
   r.err = c->err;
+  return r;
+}
+
+// Reduce the density partials; optionally average with (avg_n, avg_nu); write
+// the densities to slot `dslot` and, if potentials is true, W and Delta at t.
+// all_shards = false reduces this context's own groups only (no exchange).
+int run_reduce(lise_ctx* c, int dslot, const double* avg_n, const double2* avg_nu, bool potentials, double t,
+               bool all_shards = true) {
+  if (all_shards) TRY(exchange_parts(c));
+  ReduceArgs r = reduce_args(c, dslot, avg_n, avg_nu, potentials, all_shards);
+  r.drive = drive_at(c, t);
+  if (c->capturing) {  // inside a graph: the amplitude is refreshed before every replay
+    if (c->p.drive_A != 0.0) r.drive_ptr = c->drive_dev + (c->capturing - 1);
+    c->drive_host_t[c->capturing - 1] = t;
+    ++c->capturing;
+  }
   return timed(c, LISE_KC_REDUCE, [&] { return launch_reduce(r, c->stream) ? LISE_ECUDA : LISE_OK; });
 }
 
@@ -734,7 +751,54 @@ int lise_create(const lise_params* p, lise_ctx** out) {
 // input state in slot 0; uses the other arrays as scratch.  Results do not depend on it.
 static std::mutex g_tune_mu;
 
+// Planes per block of the FFT planes kernel (lattices that do not use the tensor-core
+// planes kernels), tuned like the pencils batch size: every compiled candidate timed on
+// this context's operand (3 launches after a warm-up), the fastest kept.
+static int tune_planes(lise_ctx* c) {
+  if (ozaki_path(c->N, c->mixed) || planes_pb_get(c->N, c->mixed)) return LISE_OK;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  if (planes_pb_get(c->N, c->mixed)) return LISE_OK;
+  int cands[4], n_valid = 0;
+  for (int pb : {1, 2, 4, 8})
+    if (planes_pb_valid(c->N, c->mixed, pb)) cands[n_valid++] = pb;
+  if (n_valid < 2) {
+    if (n_valid == 1) planes_pb_set(c->N, c->mixed, cands[0]);
+    return LISE_OK;
+  }
+  const PlanesArgs a = planes_args(c, c->slot[0], nullptr);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return LISE_ECUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return LISE_ECUDA;
+  }
+  int best = 0, rc = LISE_OK;
+  float best_ms = 0.f;
+  for (int ci = 0; ci < n_valid && rc == LISE_OK; ++ci) {
+    const int pb = cands[ci];
+    if (launch_planes(c->N, c->mixed, a, c->stream, pb)) rc = LISE_ECUDA;  // warm-up
+    cudaEventRecord(e0, c->stream);
+    for (int k = 0; k < 3 && rc == LISE_OK; ++k)
+      if (launch_planes(c->N, c->mixed, a, c->stream, pb)) rc = LISE_ECUDA;
+    cudaEventRecord(e1, c->stream);
+    float ms = 0.f;
+    if (rc != LISE_OK || cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      rc = LISE_ECUDA;
+      break;
+    }
+    if (!best || ms < best_ms) {
+      best = pb;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc == LISE_OK && best) planes_pb_set(c->N, c->mixed, best);
+  return rc;
+}
+
 static int tune_pencils(lise_ctx* c, double t0) {
+  TRY(tune_planes(c));
   if (pencil_qb_get(c->N, c->mixed)) return LISE_OK;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   if (pencil_qb_get(c->N, c->mixed)) return LISE_OK;
@@ -890,6 +954,23 @@ int lise_set_pencil_batch(int N, int precision, int qb) {
   if (qb != 0 && !pencil_qb_valid(N, mixed, qb)) return LISE_EINVAL;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   pencil_qb_set(N, mixed, qb);
+  return LISE_OK;
+}
+
+int lise_planes_per_block(int N, int precision) {
+  if (!supported_n(N) || (precision != LISE_FP64 && precision != LISE_MIXED && precision != LISE_MIXED_STRICT))
+    return 0;
+  const int mixed = precision != LISE_FP64;
+  return ozaki_path(N, mixed) ? 0 : planes_pb(N, mixed);
+}
+
+int lise_set_planes_per_block(int N, int precision, int pb) {
+  if (!supported_n(N) || (precision != LISE_FP64 && precision != LISE_MIXED && precision != LISE_MIXED_STRICT))
+    return LISE_EINVAL;
+  const int mixed = precision != LISE_FP64;
+  if (pb != 0 && !planes_pb_valid(N, mixed, pb)) return LISE_EINVAL;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  planes_pb_set(N, mixed, pb);
   return LISE_OK;
 }
 
@@ -1275,6 +1356,367 @@ void lise_destroy(lise_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   free_ctx(c);
   delete c;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------- batches --
+// Several evolutions stepped together (FP32 compute precision): every kernel class of an
+// ABM step runs as one launch per lattice size over all evolutions of that size, from a
+// device work table (PencilBatch and friends in lise_kernels.cuh) holding each evolution's
+// arguments for each of the four history configurations of a 4-step period; four steps
+// are captured as one CUDA graph.  The arguments are exactly those of abm_step's mixed
+// branch, so each evolution's result is bitwise that of lise_step on its own context.
+namespace {
+
+constexpr size_t kTableAlign = 256;  // (tensor maps need 64-byte alignment)
+
+struct MixedStepArgs {
+  PlanesArgs pl_m, pl_y;
+  PencilArgs corr, deriv;
+  PointwiseArgs pred;
+  ReduceArgs red[2];
+};
+
+// abm_step's launches (mixed branch) for the history configuration (y0_slot, D).
+MixedStepArgs mixed_step_args(lise_ctx* c, int y0_slot, void* const D[4]) {
+  MixedStepArgs a;
+  const double h = c->dt;
+  double2* yn = c->slot[y0_slot];
+  double2* ynm1 = c->slot[1 - y0_slot];
+  a.pl_m = planes_args(c, nullptr, c->M);
+  a.corr = pencil_base(c);
+  a.corr.xr = c->M;
+  a.corr.h = h;
+  a.corr.q = c->Q;
+  a.corr.r = c->R;
+  a.corr.pc = c->PC;
+  a.corr.ynew = ynm1;
+  a.corr.dens = 1;
+  a.red[0] = reduce_args(c, 1, nullptr, nullptr, true, true);
+  a.pl_y = planes_args(c, ynm1, nullptr);
+  a.deriv = pencil_base(c);
+  a.deriv.x = ynm1;
+  a.deriv.out = nullptr;
+  a.deriv.dslot = D[3];
+  a.pred = predict_args(c, ynm1, yn, D[3], D[0], D[1], D[2], h);
+  a.red[1] = reduce_args(c, 1, nullptr, nullptr, true, true);
+  return a;
+}
+
+}  // namespace
+
+struct lise_batch {
+  std::vector<lise_ctx*> ctx;
+  std::vector<int> y0_slot0;          // each context's configuration at creation
+  std::vector<std::array<void*, 4>> D0;
+  int device = 0, strict = 0;
+  cudaStream_t stream = nullptr;
+  struct Size {                       // the evolutions of one lattice size
+    int N = 0, qb = 0, pb = 0;         // pencils batch size, planes per block
+    long nxyz = 0;
+    std::vector<int> evo;             // their batch indices
+    int n_items = 0;                  // (evolution, group) items of the pencils and predictor launches
+    long pl_blocks = 0;               // planes blocks over all of them
+    PencilArgs *corr[4] = {}, *deriv[4] = {};
+    PlanesArgs *pl_m[4] = {}, *pl_y[4] = {};
+    PointwiseArgs* pred[4] = {};
+    int2* items = nullptr;
+    long* pl_block0 = nullptr;
+  };
+  std::vector<Size> sizes;
+  ReduceArgs* red[4][2] = {};
+  long* red_block0 = nullptr;
+  long red_blocks = 0;
+  double* drive_dev = nullptr;        // [4 phases][2 reductions][evolutions]
+  std::vector<double> drive_host;
+  void* tables = nullptr;
+  long step = 0;                      // steps taken since creation
+  cudaGraphExec_t graph[4] = {};      // 4 steps from phase k
+};
+
+namespace {
+
+void free_batch(lise_batch* b) {
+  for (auto& g : b->graph)
+    if (g) cudaGraphExecDestroy(g);
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->tables) cudaFree(b->tables);
+  if (b->stream) cudaStreamDestroy(b->stream);
+}
+
+// Launches of one ABM step in history phase k.
+int batch_launch_step(lise_batch* b, int k) {
+  const int E = (int)b->ctx.size();
+  for (auto& z : b->sizes)
+    if (launch_planes_batch(z.N, z.pb, PlanesBatch{z.pl_m[k], z.pl_block0, (int)z.evo.size()}, z.pl_blocks, b->stream))
+      return LISE_ECUDA;
+  for (auto& z : b->sizes)
+    if (launch_pencils_batch(z.N, M_CORRECT, b->strict, PencilBatch{z.corr[k], z.items}, z.n_items, z.qb, b->stream))
+      return LISE_ECUDA;
+  if (launch_reduce_batch(ReduceBatch{b->red[k][0], b->red_block0, E}, b->red_blocks, b->stream)) return LISE_ECUDA;
+  for (auto& z : b->sizes)
+    if (launch_planes_batch(z.N, z.pb, PlanesBatch{z.pl_y[k], z.pl_block0, (int)z.evo.size()}, z.pl_blocks, b->stream))
+      return LISE_ECUDA;
+  for (auto& z : b->sizes)
+    if (launch_pencils_batch(z.N, M_RHS, 0, PencilBatch{z.deriv[k], z.items}, z.n_items, z.qb, b->stream))
+      return LISE_ECUDA;
+  for (auto& z : b->sizes)
+    if (launch_predict_batch(b->strict, PredictBatch{z.pred[k], z.items}, z.nxyz, z.n_items, b->stream))
+      return LISE_ECUDA;
+  if (launch_reduce_batch(ReduceBatch{b->red[k][1], b->red_block0, E}, b->red_blocks, b->stream)) return LISE_ECUDA;
+  return LISE_OK;
+}
+
+// Drive amplitudes of the reductions of the next m steps (phases step .. step + m - 1).
+int batch_refresh_drive(lise_batch* b, int m) {
+  const int E = (int)b->ctx.size();
+  bool any = false;
+  for (int e = 0; e < E; ++e) {
+    lise_ctx* c = b->ctx[e];
+    if (c->p.drive_A == 0.0) continue;
+    any = true;
+    for (int j = 0; j < m; ++j) {
+      const int k = (int)((b->step + j) % 4);
+      const double t1 = c->t + (j + 1) * c->dt;
+      b->drive_host[(size_t)(2 * k) * E + e] = drive_at(c, t1);
+      b->drive_host[(size_t)(2 * k + 1) * E + e] = drive_at(c, t1 + c->dt);
+    }
+  }
+  if (!any) return LISE_OK;
+  return cu(cudaMemcpyAsync(b->drive_dev, b->drive_host.data(), b->drive_host.size() * sizeof(double),
+                            cudaMemcpyHostToDevice, b->stream));
+}
+
+}  // namespace
+
+extern "C" {
+
+static int batch_create(lise_ctx* const* ctxs, int n, lise_batch** out);
+
+int lise_batch_create(lise_ctx* const* ctxs, int n, lise_batch** out) {
+  try {  // (host containers: an allocation failure is reported, not thrown through the C ABI)
+    return batch_create(ctxs, n, out);
+  } catch (...) {
+    if (out) *out = nullptr;
+    return LISE_ENOMEM;
+  }
+}
+
+}  // extern "C"
+
+static int batch_create(lise_ctx* const* ctxs, int n, lise_batch** out) {
+  if (!out) return LISE_EINVAL;
+  *out = nullptr;
+  if (!ctxs || n < 1) return LISE_EINVAL;
+  for (int e = 0; e < n; ++e) {
+    lise_ctx* c = ctxs[e];
+    if (!c) return LISE_EINVAL;
+    for (int f = 0; f < e; ++f)
+      if (ctxs[f] == c) return LISE_EINVAL;
+    if (!c->mixed || c->strict != ctxs[0]->strict || c->device != ctxs[0]->device) return LISE_EINVAL;
+    if (c->p.remove_phase || c->p.renormalize || c->exch || c->n_groups_all != c->n_groups) return LISE_EINVAL;
+    if (c->sticky) return c->sticky;
+    if (!c->ready) return LISE_ESTATE;
+  }
+  lise_batch* b = new (std::nothrow) lise_batch();
+  if (!b) return LISE_ENOMEM;
+  b->device = ctxs[0]->device;
+  b->strict = ctxs[0]->strict;
+  int rc = cudaSetDevice(b->device) == cudaSuccess ? LISE_OK : LISE_ECUDA;
+  for (int e = 0; e < n && rc == LISE_OK; ++e) {
+    lise_ctx* c = ctxs[e];
+    rc = cu(cudaStreamSynchronize(c->stream));  // the contexts' own work is done
+    b->ctx.push_back(c);
+    b->y0_slot0.push_back(c->y0_slot);
+    b->D0.push_back({c->D[0], c->D[1], c->D[2], c->D[3]});
+  }
+  if (rc == LISE_OK && cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) rc = LISE_ECUDA;
+  // lattice sizes in order of first appearance
+  for (int e = 0; e < n && rc == LISE_OK; ++e) {
+    lise_ctx* c = ctxs[e];
+    auto it = std::find_if(b->sizes.begin(), b->sizes.end(), [&](const lise_batch::Size& z) { return z.N == c->N; });
+    if (it == b->sizes.end()) {
+      lise_batch::Size z;
+      z.N = c->N;
+      z.nxyz = c->nxyz;
+      z.qb = pencil_qb(c->N, 1);
+      z.pb = planes_pb(c->N, 1);
+      b->sizes.push_back(z);
+      it = b->sizes.end() - 1;
+    }
+    it->evo.push_back(e);
+  }
+  // host image of every table, then one device copy
+  std::vector<unsigned char> img;
+  auto place = [&](size_t bytes) {
+    const size_t off = (img.size() + kTableAlign - 1) / kTableAlign * kTableAlign;
+    img.resize(off + bytes);
+    return off;
+  };
+  struct Off {
+    size_t corr[4], deriv[4], pl_m[4], pl_y[4], pred[4], items, pl_block0;
+  };
+  std::vector<Off> off(b->sizes.size());
+  for (size_t zi = 0; zi < b->sizes.size(); ++zi) {
+    auto& z = b->sizes[zi];
+    const size_t ne = z.evo.size();
+    for (int k = 0; k < 4; ++k) {
+      off[zi].corr[k] = place(ne * sizeof(PencilArgs));
+      off[zi].deriv[k] = place(ne * sizeof(PencilArgs));
+      off[zi].pl_m[k] = place(ne * sizeof(PlanesArgs));
+      off[zi].pl_y[k] = place(ne * sizeof(PlanesArgs));
+      off[zi].pred[k] = place(ne * sizeof(PointwiseArgs));
+    }
+    z.n_items = 0;
+    for (int e : z.evo) z.n_items += b->ctx[e]->n_groups;
+    off[zi].items = place((size_t)z.n_items * sizeof(int2));
+    off[zi].pl_block0 = place((ne + 1) * sizeof(long));
+  }
+  size_t red_off[4][2];
+  for (int k = 0; k < 4; ++k)
+    for (int r = 0; r < 2; ++r) red_off[k][r] = place((size_t)n * sizeof(ReduceArgs));
+  const size_t red_block0_off = place((size_t)(n + 1) * sizeof(long));
+  const size_t drive_off = place((size_t)8 * n * sizeof(double));
+  if (rc == LISE_OK && cudaMalloc(&b->tables, img.size()) != cudaSuccess) {
+    cudaGetLastError();
+    rc = LISE_ENOMEM;
+  }
+  unsigned char* dev = static_cast<unsigned char*>(b->tables);
+  // fill the image
+  for (size_t zi = 0; zi < b->sizes.size() && rc == LISE_OK; ++zi) {
+    auto& z = b->sizes[zi];
+    int2* items = reinterpret_cast<int2*>(img.data() + off[zi].items);
+    long* pb0 = reinterpret_cast<long*>(img.data() + off[zi].pl_block0);
+    int it = 0;
+    pb0[0] = 0;
+    for (size_t j = 0; j < z.evo.size(); ++j) {
+      lise_ctx* c = b->ctx[z.evo[j]];
+      for (int g = 0; g < c->n_groups; ++g) items[it++] = make_int2((int)j, g);
+      pb0[j + 1] = pb0[j] + planes_blocks((long)c->p.n_qp * 2 * c->N, z.pb);
+    }
+    z.pl_blocks = pb0[z.evo.size()];
+    for (int k = 0; k < 4 && rc == LISE_OK; ++k) {
+      PencilArgs* corr = reinterpret_cast<PencilArgs*>(img.data() + off[zi].corr[k]);
+      PencilArgs* deriv = reinterpret_cast<PencilArgs*>(img.data() + off[zi].deriv[k]);
+      PlanesArgs* plm = reinterpret_cast<PlanesArgs*>(img.data() + off[zi].pl_m[k]);
+      PlanesArgs* ply = reinterpret_cast<PlanesArgs*>(img.data() + off[zi].pl_y[k]);
+      PointwiseArgs* pred = reinterpret_cast<PointwiseArgs*>(img.data() + off[zi].pred[k]);
+      for (size_t j = 0; j < z.evo.size(); ++j) {
+        const int e = z.evo[j];
+        lise_ctx* c = b->ctx[e];
+        // the configuration after k steps: slot parity flips, the derivative ring rotates
+        void* Dk[4];
+        for (int q = 0; q < 4; ++q) Dk[q] = b->D0[e][(q - k + 4) % 4];
+        MixedStepArgs a = mixed_step_args(c, (b->y0_slot0[e] + k) % 2, Dk);
+        if (!pencils_batch_maps(z.N, M_CORRECT, b->strict, z.qb, &a.corr) ||
+            !pencils_batch_maps(z.N, M_RHS, 0, z.qb, &a.deriv)) {
+          rc = LISE_ECUDA;
+          break;
+        }
+        corr[j] = a.corr;
+        deriv[j] = a.deriv;
+        plm[j] = a.pl_m;
+        ply[j] = a.pl_y;
+        pred[j] = a.pred;
+        for (int r = 0; r < 2; ++r) {
+          ReduceArgs ra = a.red[r];
+          if (c->p.drive_A != 0.0)
+            ra.drive_ptr = reinterpret_cast<const double*>(dev + drive_off) + (size_t)(2 * k + r) * n + e;
+          reinterpret_cast<ReduceArgs*>(img.data() + red_off[k][r])[e] = ra;
+        }
+      }
+      z.corr[k] = reinterpret_cast<PencilArgs*>(dev + off[zi].corr[k]);
+      z.deriv[k] = reinterpret_cast<PencilArgs*>(dev + off[zi].deriv[k]);
+      z.pl_m[k] = reinterpret_cast<PlanesArgs*>(dev + off[zi].pl_m[k]);
+      z.pl_y[k] = reinterpret_cast<PlanesArgs*>(dev + off[zi].pl_y[k]);
+      z.pred[k] = reinterpret_cast<PointwiseArgs*>(dev + off[zi].pred[k]);
+    }
+    z.items = reinterpret_cast<int2*>(dev + off[zi].items);
+    z.pl_block0 = reinterpret_cast<long*>(dev + off[zi].pl_block0);
+  }
+  if (rc == LISE_OK) {
+    long* rb0 = reinterpret_cast<long*>(img.data() + red_block0_off);
+    rb0[0] = 0;
+    for (int e = 0; e < n; ++e) rb0[e + 1] = rb0[e] + (b->ctx[e]->nxyz + 255) / 256;
+    b->red_blocks = rb0[n];
+    b->red_block0 = reinterpret_cast<long*>(dev + red_block0_off);
+    for (int k = 0; k < 4; ++k)
+      for (int r = 0; r < 2; ++r) b->red[k][r] = reinterpret_cast<ReduceArgs*>(dev + red_off[k][r]);
+    b->drive_dev = reinterpret_cast<double*>(dev + drive_off);
+    b->drive_host.assign((size_t)8 * n, 0.0);
+    rc = cu(cudaMemcpyAsync(b->tables, img.data(), img.size(), cudaMemcpyHostToDevice, b->stream));
+    if (rc == LISE_OK) rc = cu(cudaStreamSynchronize(b->stream));
+  }
+  if (rc != LISE_OK) {
+    free_batch(b);
+    delete b;
+    return rc;
+  }
+  *out = b;
+  return LISE_OK;
+}
+
+extern "C" {
+
+int lise_batch_step(lise_batch* b, int n_steps) {
+  if (!b || n_steps < 0) return LISE_EINVAL;
+  if (cudaSetDevice(b->device) != cudaSuccess) return LISE_ECUDA;
+  // every member must still be where the batch left it (not stepped on its own)
+  for (size_t e = 0; e < b->ctx.size(); ++e) {
+    lise_ctx* c = b->ctx[e];
+    if (c->sticky) return c->sticky;
+    if (!c->ready || c->y0_slot != (int)((b->y0_slot0[e] + b->step) % 2) || c->D[0] != b->D0[e][(4 - b->step % 4) % 4])
+      return LISE_ESTATE;
+  }
+  int done = 0;
+  while (done < n_steps) {
+    const int phase = (int)(b->step % 4);
+    const int m = (n_steps - done >= 4) ? 4 : 1;
+    TRY(batch_refresh_drive(b, m));
+    if (m == 4) {
+      cudaGraphExec_t& g = b->graph[phase];
+      if (!g) {
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return LISE_ECUDA;
+        int rc = LISE_OK;
+        for (int j = 0; j < 4 && rc == LISE_OK; ++j) rc = batch_launch_step(b, (phase + j) % 4);
+        const cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
+        if (rc == LISE_OK && (e != cudaSuccess || !graph)) rc = LISE_ECUDA;
+        if (rc == LISE_OK && cudaGraphInstantiate(&g, graph, 0) != cudaSuccess) rc = LISE_ECUDA;
+        if (graph) cudaGraphDestroy(graph);
+        TRY(rc);
+      }
+      TRY(cu(cudaGraphLaunch(g, b->stream)));
+    } else {
+      TRY(batch_launch_step(b, phase));
+    }
+    for (lise_ctx* c : b->ctx)
+      for (int j = 0; j < m; ++j) rotate_history(c, c->t + c->dt);
+    b->step += m;
+    done += m;
+  }
+  return LISE_OK;
+}
+
+int lise_batch_sync(lise_batch* b) {
+  if (!b) return LISE_EINVAL;
+  if (cudaSetDevice(b->device) != cudaSuccess || cudaStreamSynchronize(b->stream) != cudaSuccess) return LISE_ECUDA;
+  int first = LISE_OK;
+  for (lise_ctx* c : b->ctx) {
+    const int rc = fetch_err(c);
+    if (first == LISE_OK) first = rc;
+  }
+  return first;
+}
+
+void* lise_batch_stream(lise_batch* b) { return b ? (void*)b->stream : nullptr; }
+
+void lise_batch_destroy(lise_batch* b) {
+  if (!b) return;
+  cudaSetDevice(b->device);
+  free_batch(b);
+  delete b;
 }
 
 }  // extern "C"

@@ -16,3 +16,6 @@ namespace lise {
 // pairing options).
 int check_params(const lise_params* p);
 }  // namespace lise
+
+// The stream a batch (lise_batch_*) enqueues its work on.
+extern "C" void* lise_batch_stream(lise_batch* b);

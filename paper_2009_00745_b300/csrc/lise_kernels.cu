@@ -165,7 +165,7 @@ template <int N> struct PlanesPB { static constexpr int v = N <= 8 ? 8 : (N <= 1
 
 // ------------------------------------------------------------------ planes --
 template <typename R, int N, int PB, int NT>
-__global__ void __launch_bounds__(NT) k_planes(PlanesArgs a) {
+__device__ __forceinline__ void planes_body(const PlanesArgs& a, const long block) {
   using T = typename Cx<R>::T;
   constexpr int NP = N + 1;   // padded row stride (conflict-free row and column lines)
   constexpr int PS = N * NP;  // plane stride
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(NT) k_planes(PlanesArgs a) {
     tw[i] = twg[i];
     hk[i] = hg[i];
   }
-  const long plane0 = (long)blockIdx.x * PB;
+  const long plane0 = block * PB;
   const long left = a.n_planes - plane0;
   const int np = left < PB ? (int)left : PB;
   const double2* src = a.x + plane0 * N * N;
@@ -217,6 +217,20 @@ __global__ void __launch_bounds__(NT) k_planes(PlanesArgs a) {
     int pl = i / (N * N), r = i % (N * N);
     dst[i] = buf[pl * PS + (r / N) * NP + (r % N)];
   }
+}
+
+template <typename R, int N, int PB, int NT>
+__global__ void __launch_bounds__(NT) k_planes(PlanesArgs a) {
+  planes_body<R, N, PB, NT>(a, blockIdx.x);
+}
+
+// Several evolutions' planes in one launch: segment k covers blocks
+// [b.block0[k], b.block0[k + 1]) with the arguments b.seg[k] (one evolution's operand).
+template <typename R, int N, int PB, int NT>
+__global__ void __launch_bounds__(NT) k_planes_batch(PlanesBatch b) {
+  int k = 0;
+  while (k + 1 < b.n_seg && (long)blockIdx.x >= b.block0[k + 1]) ++k;
+  planes_body<R, N, PB, NT>(b.seg[k], (long)blockIdx.x - b.block0[k]);
 }
 
 // --------------------------------------------------------- planes, FP64 MMA --
@@ -379,16 +393,30 @@ __global__ void __launch_bounds__(256) k_planes_oz(PlanesArgs a) {
 }
 
 // T_x + T_y of the FP64 path on the fifth-generation tensor cores (tcgen05), 32^3 lattices.
-// One plane (a state component, N x N complex values) per pass of a persistent block; its
-// exponent groups are the plane's real and imaginary parts.  The digit operand stacks the
-// two axes into M = 128 rows, K = N:
+// One plane (a state component, N x N complex values) at a time; its exponent groups are the
+// plane's real and imaginary parts.  The digit operand stacks the two axes into M = 128 rows,
+// K = N:
 //   rows g N + y       (g = re/im): the data lines along x  -> T_x x  [g][y][x = column]
 //   rows 2N + g N + x:              the data lines along y  -> T_y x  [g][y = column][x]
-// so one chain of MMAs against the D2 digits (B, N x K) forms both products.  Level L of
-// the digit products (pairs k + l = L) accumulates in tensor-memory columns [L N, L N + N)
-// (exact FP32 integers, as in tile_levels); the levels are read back, combined in 64-bit
-// integers per axis, summed and converted to FP64 once.
-constexpr int kPlanesTcBlocksPerSM = 2;
+// so one chain of MMAs against the D2 digits (B, N x K) forms both products.  Level L of the
+// digit products (pairs k + l = L) accumulates in tensor-memory columns [L N, L N + N) of
+// the plane's stage (exact FP32 integers, as in tile_levels); the levels are read back,
+// combined in 64-bit integers per axis, summed and converted to FP64 once.
+//
+// Warp-specialised and persistent, one block per SM holding all 512 tensor-memory columns, so
+// that the digit split, the MMAs and the read-back of different planes overlap:
+//   producers (warps 8-11): load a plane (one plane ahead), find its exponent groups, write its
+//     digits into operand stage s = i % 2 (i: the block's plane counter) and arrive on full[s];
+//   issuer (warp 12, one thread): waits for full[s], issues the plane's 56 MMAs into the
+//     columns [256 s, 256 s + 224) and commits to mma_done[s];
+//   consumers (warps 0-7): wait for mma_done[s], read the levels back (warp w: lanes
+//     32 (w % 4) .., columns 16 (w / 4) ..), write the 64-bit sums into buffer acc[s], release
+//     the stage (tmem_free[s]), then form T_x + T_y of the plane and store it.
+// A producer refills stage s (operand, scales) only after tmem_free[s].  Every wait is bounded
+// (and gives up early once another role has given up): the block then records bit 4 in the
+// error word, the issuer waits (bounded) for its last MMAs, and the tensor memory is freed.
+constexpr int kWsConsumerWarps = 8, kWsProducerWarps = 4;
+constexpr int kWsThreads = 32 * (kWsConsumerWarps + kWsProducerWarps + 1);
 template <int N>
 struct TcPlanes {
   static_assert(N == 32, "two axes x two parts x N lines fill the 128 rows of one MMA only at N = 32");
@@ -396,9 +424,11 @@ struct TcPlanes {
   static constexpr int LBO = 128, SBO = (K / 8) * 128;  // core-matrix strides (bytes), K-major
   static constexpr int A_BYTES = M * K * 2, B_BYTES = N * K * 2;  // one digit of each operand
   static constexpr int AP = N + 1;                                 // padded row of the 64-bit sums
-  static constexpr size_t acc_bytes = (size_t)2 * 2 * N * AP * 8;
-  static constexpr size_t smem = (size_t)oz::S * (A_BYTES + B_BYTES) + acc_bytes;
-  static constexpr uint32_t TMEM_COLS = 256;  // >= S N, a power of 2
+  static constexpr size_t acc_elems = (size_t)2 * 2 * N * AP;      // [T_x / T_y][g][N][AP]
+  static constexpr size_t a_off = 0, b_off = (size_t)2 * oz::S * A_BYTES;  // two operand stages
+  static constexpr size_t acc_off = b_off + (size_t)oz::S * B_BYTES;
+  static constexpr size_t smem = acc_off + 2 * acc_elems * 8;      // two sums buffers
+  static constexpr uint32_t TMEM_COLS = 512;  // two stages of S N <= 256 columns
   // word offset of the core-matrix D2 table behind the mma.sync fragment table
   static constexpr size_t table_offset = (size_t)oz::S * (N / 8) * (N / 16) * 32 * 2;
 };
@@ -408,150 +438,197 @@ __device__ __forceinline__ int tc_off(int row, int k) {
 }
 
 template <int N>
-__global__ void __launch_bounds__(256, kPlanesTcBlocksPerSM) k_planes_tc(PlanesArgs a) {
+__global__ void __launch_bounds__(kWsThreads, 1) k_planes_tc(PlanesArgs a) {
   using P = TcPlanes<N>;
-  constexpr int NT = 256, NW = NT / 32, S = oz::S, AP = P::AP;
+  constexpr int S = oz::S, AP = P::AP;
+  constexpr int NP = 32 * kWsProducerWarps, NC = 32 * kWsConsumerWarps;  // producer, consumer threads
+  constexpr int BAR_P = 1, BAR_C = 2;                                      // their named barriers
   extern __shared__ __align__(128) unsigned char smem_raw[];  // (no-swizzle operands need 16 bytes)
-  unsigned char* sA = smem_raw;                    // [S][M rows][K], core-matrix layout
-  unsigned char* sB = smem_raw + S * P::A_BYTES;   // [S][N][K], core-matrix layout
-  long long* accx = reinterpret_cast<long long*>(sB + S * P::B_BYTES);  // [g][x][y (AP)]
-  long long* accy = accx + 2 * N * AP;                                   // [g][y][x (AP)]
-  __shared__ __align__(8) uint64_t mbar;
+  unsigned char* sA = smem_raw + P::a_off;  // [2 stages][S][M rows][K], core-matrix layout
+  unsigned char* sB = smem_raw + P::b_off;  // [S][N][K], core-matrix layout
+  long long* accbuf = reinterpret_cast<long long*>(smem_raw + P::acc_off);  // [2][T_x / T_y][g][N][AP]
+  __shared__ __align__(8) uint64_t full[2], mma_done[2], tmem_free[2];
   __shared__ uint32_t tslot;
-  __shared__ unsigned ered[NW][2];
-  __shared__ unsigned Eg[2];
+  __shared__ unsigned ered[2][kWsProducerWarps][2];  // per stage: each producer warp's exponent maxima
+  __shared__ unsigned Es[2][2];                      // per stage: the plane's exponent fields (re, im)
+  __shared__ volatile int stop;                      // a role gave up: the others stop waiting
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
 
   // the D2 digits, once per block (the table is stored in the core-matrix layout)
   const uint4* tb = reinterpret_cast<const uint4*>(a.ozb + P::table_offset);
-  for (int i = tid; i < S * P::B_BYTES / 16; i += NT) reinterpret_cast<uint4*>(sB)[i] = tb[i];
-  if (tid == 0) um::mbar_init(&mbar, 1);
+  for (int i = tid; i < S * P::B_BYTES / 16; i += kWsThreads) reinterpret_cast<uint4*>(sB)[i] = tb[i];
+  if (tid == 0) {
+    for (int s = 0; s < 2; ++s) {
+      um::mbar_init(&full[s], NP);
+      um::mbar_init(&mma_done[s], 1);
+      um::mbar_init(&tmem_free[s], 1);
+    }
+    stop = 0;
+  }
   if (w == 0) um::alloc(&tslot, P::TMEM_COLS);
   um::fence_proxy_async();
   um::fence_before();
   __syncthreads();
   um::fence_after();
   const uint32_t tmem = tslot;
-  uint32_t parity = 0;
-  bool failed = false;
-
-  // this thread's 2 x 2 block of the plane: an 8 x 8 tile per 16 lanes, two tiles per warp
-  // (lane bits: a = x pair, b = y pair, c = tile); digit stores then hit 32 distinct banks
-  const int la = lane & 3, lb = (lane >> 2) & 3, lc = lane >> 4;
-  const int x0 = 8 * (2 * (w & 1) + lc) + 2 * la, y0 = 8 * (w >> 1) + 2 * lb;
-  constexpr uint32_t idesc = um::idesc_bf16_f32(P::M, N);
-
-  const double2* src0 = a.xr ? reinterpret_cast<const double2*>(a.xr) : a.x;
-  // this thread's values of the block's next plane, loaded one pass ahead
-  double2 vn[2][2];
-  auto load_plane = [&](long pl) {
-#pragma unroll
-    for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-      for (int dx = 0; dx < 2; ++dx)
-        vn[dy][dx] = pl < a.n_planes ? src0[pl * N * N + (y0 + dy) * N + x0 + dx] : make_double2(0.0, 0.0);
-  };
-  load_plane(blockIdx.x);
-  // T_xy = T_x + T_y of a finished plane, one rounding; coalesced complex128 stores
-  auto final_pass = [&](long pp, int s0, int s1) {
-    double2* out = reinterpret_cast<double2*>(a.txy) + pp * N * N;
-    for (int i = tid; i < N * N; i += NT) {
-      const int y = i / N, x = i % N;
-      const long long re = accx[(0 * N + x) * AP + y] + accy[(0 * N + y) * AP + x];
-      const long long im = accx[(1 * N + x) * AP + y] + accy[(1 * N + y) * AP + x];
-      out[i] = make_double2(oz::to_double_hw(re, s0), oz::to_double_hw(im, s1));
+  const long limit = wait_limit(a.wait_polls);
+  const long n_local = (a.n_planes - blockIdx.x + gridDim.x - 1) / gridDim.x;  // this block's planes
+  auto give_up = [&]() {
+    if (!stop) {
+      stop = 1;
+      if (a.err) atomicOr(a.err, 4);
     }
   };
-  long prev = -1;  // the plane whose sums wait in accx/accy, and their output scales
-  int ps0 = 0, ps1 = 0;
-  for (long pl = blockIdx.x; pl < a.n_planes; pl += gridDim.x) {
-    double2 v[2][2];  // [dy][dx]
-    unsigned e0 = 0, e1 = 0;
+
+  if (w >= kWsConsumerWarps && w < kWsConsumerWarps + kWsProducerWarps) {
+    // ---------------------------------------------------------------- producers
+    const int pt = tid - NC, pw = pt >> 5;
+    // two 2 x 2 blocks per thread: the blocks of virtual threads vt = pt + NP j (j = 0, 1) of a
+    // 256-thread layout, an 8 x 8 tile per 16 lanes and two tiles per virtual warp (lane bits:
+    // a = x pair, b = y pair, c = tile), so that the digit stores hit 32 distinct banks
+    int bx0[2], by0[2], blc[2];
 #pragma unroll
-    for (int dy = 0; dy < 2; ++dy)
+    for (int j = 0; j < 2; ++j) {
+      const int vt = pt + NP * j, vw = vt >> 5, vl = vt & 31;
+      blc[j] = vl >> 4;
+      bx0[j] = 8 * (2 * (vw & 1) + blc[j]) + 2 * (vl & 3);
+      by0[j] = 8 * (vw >> 1) + 2 * ((vl >> 2) & 3);
+    }
+    const double2* src0 = a.xr ? reinterpret_cast<const double2*>(a.xr) : a.x;
+    double2 vn[2][2][2];  // [j][dy][dx], the next plane's values (loaded one plane ahead)
+    auto load_plane = [&](long pl) {
 #pragma unroll
-      for (int dx = 0; dx < 2; ++dx) {
-        v[dy][dx] = vn[dy][dx];
-        e0 = max(e0, oz::exp_field(v[dy][dx].x));
-        e1 = max(e1, oz::exp_field(v[dy][dx].y));
+      for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+          for (int dx = 0; dx < 2; ++dx)
+            vn[j][dy][dx] = pl < a.n_planes ? src0[pl * N * N + (by0[j] + dy) * N + bx0[j] + dx] : make_double2(0.0, 0.0);
+    };
+    load_plane(blockIdx.x);
+    for (long i = 0; i < n_local; ++i) {
+      const int s = (int)(i & 1);
+      const uint32_t u = (uint32_t)(i >> 1);
+      double2 v[2][2][2];
+      unsigned e0 = 0, e1 = 0;
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+          for (int dx = 0; dx < 2; ++dx) {
+            v[j][dy][dx] = vn[j][dy][dx];
+            e0 = max(e0, oz::exp_field(v[j][dy][dx].x));
+            e1 = max(e1, oz::exp_field(v[j][dy][dx].y));
+          }
+      load_plane(blockIdx.x + (i + 1) * gridDim.x);  // in flight through this plane's digit split
+      e0 = oz::warp_max(e0);
+      e1 = oz::warp_max(e1);
+      if (lane == 0) {
+        ered[s][pw][0] = e0;
+        ered[s][pw][1] = e1;
       }
-    load_plane(pl + gridDim.x);  // in flight through this pass's digit products
-    e0 = oz::warp_max(e0);
-    e1 = oz::warp_max(e1);
-    if (lane == 0) {
-      ered[w][0] = e0;
-      ered[w][1] = e1;
-    }
-    __syncthreads();
-    if (tid < 2) {
-      unsigned m = 0;
+      // stage s is free once the consumers have released it (two planes back)
+      bool ok = i < 2 || um::mbar_wait_or(&tmem_free[s], (u - 1) & 1u, limit, &stop);
+      if (!um::bar_and(BAR_P, NP, ok)) {  // (also makes every warp's ered visible)
+        give_up();
+        break;
+      }
+      unsigned Eg[2] = {0, 0};
 #pragma unroll
-      for (int k = 0; k < NW; ++k) m = max(m, ered[k][tid]);
-      Eg[tid] = m;
-    }
-    __syncthreads();
-    // digits into both row blocks (the lanes of one store cover one core matrix's 32 words:
-    // rows alternate with the tile bit so that the two tiles of a warp use different rows)
+      for (int k = 0; k < kWsProducerWarps; ++k) {
+        Eg[0] = max(Eg[0], ered[s][k][0]);
+        Eg[1] = max(Eg[1], ered[s][k][1]);
+      }
+      if (pt == 0) {
+        Es[s][0] = Eg[0];
+        Es[s][1] = Eg[1];
+      }
+      unsigned char* sAs = sA + (size_t)s * S * P::A_BYTES;
+      // digits into both row blocks (the lanes of one store cover one core matrix's 32 words:
+      // rows alternate with the tile bit so that the two tiles of a warp use different rows)
 #pragma unroll
-    for (int g = 0; g < 2; ++g) {
-      unsigned short d[2][2][S];
+      for (int j = 0; j < 2; ++j)
 #pragma unroll
-      for (int dy = 0; dy < 2; ++dy)
+        for (int g = 0; g < 2; ++g) {
+          unsigned short d[2][2][S];
 #pragma unroll
-        for (int dx = 0; dx < 2; ++dx) oz::split(g ? v[dy][dx].y : v[dy][dx].x, Eg[g], d[dy][dx]);
+          for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
-      for (int st = 0; st < 2; ++st) {
-        const int o = st ^ lc;  // which row (dy for T_x, dx for T_y) this store covers
-        const int ox = tc_off(g * N + y0 + o, x0);          // T_x row (g, y), k = x pair
-        const int oy = tc_off(2 * N + g * N + x0 + o, y0);  // T_y row (g, x), k = y pair
+            for (int dx = 0; dx < 2; ++dx) oz::split(g ? v[j][dy][dx].y : v[j][dy][dx].x, Eg[g], d[dy][dx]);
 #pragma unroll
-        for (int k = 0; k < S; ++k) {
-          const unsigned px0 = (unsigned)d[0][0][k] | ((unsigned)d[0][1][k] << 16);
-          const unsigned px1 = (unsigned)d[1][0][k] | ((unsigned)d[1][1][k] << 16);
-          const unsigned py0 = (unsigned)d[0][0][k] | ((unsigned)d[1][0][k] << 16);
-          const unsigned py1 = (unsigned)d[0][1][k] | ((unsigned)d[1][1][k] << 16);
-          *reinterpret_cast<unsigned*>(sA + k * P::A_BYTES + ox) = o ? px1 : px0;
-          *reinterpret_cast<unsigned*>(sA + k * P::A_BYTES + oy) = o ? py1 : py0;
+          for (int st = 0; st < 2; ++st) {
+            const int o = st ^ blc[j];  // which row (dy for T_x, dx for T_y) this store covers
+            const int ox = tc_off(g * N + by0[j] + o, bx0[j]);          // T_x row (g, y), k = x pair
+            const int oy = tc_off(2 * N + g * N + bx0[j] + o, by0[j]);  // T_y row (g, x), k = y pair
+#pragma unroll
+            for (int k = 0; k < S; ++k) {
+              const unsigned px0 = (unsigned)d[0][0][k] | ((unsigned)d[0][1][k] << 16);
+              const unsigned px1 = (unsigned)d[1][0][k] | ((unsigned)d[1][1][k] << 16);
+              const unsigned py0 = (unsigned)d[0][0][k] | ((unsigned)d[1][0][k] << 16);
+              const unsigned py1 = (unsigned)d[0][1][k] | ((unsigned)d[1][1][k] << 16);
+              *reinterpret_cast<unsigned*>(sAs + k * P::A_BYTES + ox) = o ? px1 : px0;
+              *reinterpret_cast<unsigned*>(sAs + k * P::A_BYTES + oy) = o ? py1 : py0;
+            }
+          }
         }
+      um::fence_proxy_async();  // the digits (generic proxy) before the tensor core reads them
+      um::mbar_arrive(&full[s]);
+    }
+  } else if (w == kWsConsumerWarps + kWsProducerWarps) {
+    // ---------------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      constexpr uint32_t idesc = um::idesc_bf16_f32(P::M, N);
+      long committed = 0;
+      for (long i = 0; i < n_local; ++i) {
+        const int s = (int)(i & 1);
+        if (!um::mbar_wait_or(&full[s], (uint32_t)(i >> 1) & 1u, limit, &stop)) {
+          give_up();
+          break;
+        }
+        um::fence_after();
+        const uint32_t a0 = um::su32(sA + (size_t)s * S * P::A_BYTES), b0 = um::su32(sB);
+        const uint32_t d0 = tmem + 256u * s;
+#pragma unroll
+        for (int L = 0; L < S; ++L)
+#pragma unroll
+          for (int k = 0; k <= L; ++k)
+#pragma unroll
+            for (int ks = 0; ks < P::K / 16; ++ks)
+              um::mma_bf16(d0 + L * N, um::sdesc(a0 + k * P::A_BYTES + ks * 2 * P::LBO, P::LBO, P::SBO),
+                           um::sdesc(b0 + (L - k) * P::B_BYTES + ks * 2 * P::LBO, P::LBO, P::SBO), idesc,
+                           (k > 0 || ks > 0) ? 1u : 0u);
+        um::commit(&mma_done[s]);
+        committed = i + 1;
       }
+      // the last MMAs complete before the tensor memory is freed (at once when the consumers
+      // have already waited for them), bounded
+      if (committed > 0)
+        um::mbar_wait(&mma_done[(committed - 1) & 1], (uint32_t)((committed - 1) >> 1) & 1u, kDrainPolls);
     }
-    um::fence_proxy_async();
-    um::fence_before();
-    __syncthreads();
-    if (tid == 0) {
+  } else if (w < kWsConsumerWarps) {
+    // ---------------------------------------------------------------- consumers
+    const int q = w & 3, c0 = 16 * (w >> 2);
+    const int g = q & 1, ax = q >> 1;  // N = 32: lane quadrant q = 2 ax + g
+    for (long i = 0; i < n_local; ++i) {
+      const int s = (int)(i & 1);
+      const uint32_t par = (uint32_t)(i >> 1) & 1u;
+      const long pl = blockIdx.x + i * gridDim.x;
+      // the MMAs are done; full[s] (already complete) orders the producers' scales before us
+      bool ok = um::mbar_wait_or(&mma_done[s], par, limit, &stop) && um::mbar_wait_or(&full[s], par, limit, &stop);
+      if (!um::bar_and(BAR_C, NC, ok)) {
+        give_up();
+        break;
+      }
       um::fence_after();
-      const uint32_t a0 = um::su32(sA), b0 = um::su32(sB);
-#pragma unroll
-      for (int L = 0; L < S; ++L)
-#pragma unroll
-        for (int k = 0; k <= L; ++k)
-#pragma unroll
-          for (int ks = 0; ks < P::K / 16; ++ks)
-            um::mma_bf16(tmem + L * N, um::sdesc(a0 + k * P::A_BYTES + ks * 2 * P::LBO, P::LBO, P::SBO),
-                         um::sdesc(b0 + (L - k) * P::B_BYTES + ks * 2 * P::LBO, P::LBO, P::SBO), idesc,
-                         (k > 0 || ks > 0) ? 1u : 0u);
-      um::commit(&mbar);
-    }
-    // the previous plane's T_xy while this plane's MMAs run
-    if (prev >= 0) final_pass(prev, ps0, ps1);
-    const bool ok = um::mbar_wait(&mbar, parity, wait_limit(a.wait_polls));
-    parity ^= 1u;
-    if (__syncthreads_or(!ok)) {  // (also: every thread is done with the sums of the previous plane)
-      failed = true;
-      break;
-    }
-    um::fence_after();
-    // read back: warp w reads tensor-memory lanes (rows) 32 (w % 4) + lane, columns
-    // 16 (w / 4) .. + 15; rows < 2N are T_x (g, y = row % N), the others T_y (g, x)
-    {
-      const int q = w & 3, c0 = 16 * (w >> 2);
-      const int g = (q & 1), ax = q >> 1;  // N = 32: quarter q = 2 ax + g
-      long long* dst = ax ? accy : accx;
+      const int ps0 = oz::out_scale(a.oz_sD, Es[s][0]), ps1 = oz::out_scale(a.oz_sD, Es[s][1]);
+      long long* acc = accbuf + (size_t)s * P::acc_elems;
+      long long* dst = acc + (size_t)ax * 2 * N * AP;
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         uint32_t r[S][8];
 #pragma unroll
-        for (int L = 0; L < S; ++L) um::ld8(r[L], tmem + ((uint32_t)(32 * q) << 16) + L * N + c0 + 8 * h);
+        for (int L = 0; L < S; ++L) um::ld8(r[L], tmem + ((uint32_t)(32 * q) << 16) + 256u * s + L * N + c0 + 8 * h);
         um::wait_ld_deps<S>(r);
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
@@ -561,19 +638,20 @@ __global__ void __launch_bounds__(256, kPlanesTcBlocksPerSM) k_planes_tc(PlanesA
           dst[(g * N + c0 + 8 * h + j) * AP + lane] = oz::combine_biased(lb);
         }
       }
+      um::fence_before();
+      um::bar_sync(BAR_C, NC);  // every consumer has read stage s and written its sums
+      if (tid == 0) um::mbar_arrive(&tmem_free[s]);
+      // T_xy = T_x + T_y of the plane, one rounding; coalesced complex128 stores
+      const long long* accx = acc;
+      const long long* accy = acc + 2 * N * AP;
+      double2* out = reinterpret_cast<double2*>(a.txy) + pl * N * N;
+      for (int idx = tid; idx < N * N; idx += NC) {
+        const int y = idx / N, x = idx % N;
+        const long long re = accx[(0 * N + x) * AP + y] + accy[(0 * N + y) * AP + x];
+        const long long im = accx[(1 * N + x) * AP + y] + accy[(1 * N + y) * AP + x];
+        out[idx] = make_double2(oz::to_double_hw(re, ps0), oz::to_double_hw(im, ps1));
+      }
     }
-    um::fence_before();  // (the next pass's first barrier orders these reads before its MMAs)
-    prev = pl;
-    ps0 = oz::out_scale(a.oz_sD, Eg[0]);
-    ps1 = oz::out_scale(a.oz_sD, Eg[1]);
-  }
-  if (!failed && prev >= 0) {
-    __syncthreads();
-    final_pass(prev, ps0, ps1);
-  }
-  if (failed) {
-    if (tid == 0 && a.err) atomicOr(a.err, 4);
-    um::mbar_wait(&mbar, parity ^ 1u, kDrainPolls);  // let the MMAs in flight finish, bounded
   }
   um::fence_before();
   __syncthreads();
@@ -667,8 +745,9 @@ __host__ __device__ constexpr int pencil_smem_bytes() {
 // ST (FP32 compute precision, corrector mode only): the strict split of LISE_MIXED_STRICT --
 // R and p - c in complex128 (units of h/48), y_{n+1} = Q + k1 m' and p - c = R - 17 m' in
 // FP64 from the exact FP64 value of m', densities of y_{n+1} from its FP64 values.
-template <typename R, int N, int TX, int QB, int MODE, bool ST = false>
-__global__ void __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N * TX == 256 ? 2 : ((sizeof(R) == 8 && N * TX == 128) ? 7 : ((sizeof(R) == 8 && N * TX == 192) ? 3 : 1))) k_pencils(const __grid_constant__ PencilArgs a) {
+// Block (bx of nbx) of group g of the evolution described by a.
+template <typename R, int N, int TX, int QB, int MODE, bool ST>
+__device__ __forceinline__ void pencils_body(const PencilArgs& a, const int g, const int bx, const int nbx) {
   using T = typename Cx<R>::T;
   constexpr int NT = N * TX;
   // one component block [z][x] in shared memory; for 8-byte elements the blocks are
@@ -696,11 +775,10 @@ __global__ void __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N
   }
   const long nxyz = (long)N * N * N;
   constexpr int TILES_X = N / TX;
-  const int y = blockIdx.x / TILES_X;
-  const int x0 = (blockIdx.x % TILES_X) * TX;
+  const int y = bx / TILES_X;
+  const int x0 = (bx % TILES_X) * TX;
   const int z = threadIdx.x / TX, xl = threadIdx.x % TX;
   const long site = ((long)z * N + y) * N + x0 + xl;
-  const int g = blockIdx.y;
   const int q_begin = g * a.qg;
   const int q_end = min(a.n_qp, q_begin + a.qg);
   double Wv = 0.0;
@@ -1008,7 +1086,7 @@ __global__ void __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N
       if ((int)threadIdx.x < QB && qb0 + (int)threadIdx.x < q_end) {
         double t = 0.0;
         for (int k = 0; k < NT; ++k) t += red[threadIdx.x][k];
-        a.eta_part[(long)(qb0 + threadIdx.x) * gridDim.x + blockIdx.x] = t;
+        a.eta_part[(long)(qb0 + threadIdx.x) * nbx + bx] = t;
       }
     }
     // the batch buffer is reused
@@ -1036,6 +1114,25 @@ __global__ void __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N
   }
 }
 
+#define LISE_PENCILS_BOUNDS                                                                                    \
+  __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N * TX == 256                                 \
+                                ? 2                                                                            \
+                                : ((sizeof(R) == 8 && N * TX == 128) ? 7 : ((sizeof(R) == 8 && N * TX == 192) ? 3 : 1)))
+
+template <typename R, int N, int TX, int QB, int MODE, bool ST = false>
+__global__ void LISE_PENCILS_BOUNDS k_pencils(const __grid_constant__ PencilArgs a) {
+  pencils_body<R, N, TX, QB, MODE, ST>(a, blockIdx.y, blockIdx.x, gridDim.x);
+}
+
+// Several evolutions of one lattice size in one launch: block row blockIdx.y is the item
+// (evolution, group) b.items[blockIdx.y], with that evolution's arguments b.evo[evolution]
+// (device memory, tensor maps included).
+template <typename R, int N, int TX, int QB, int MODE, bool ST = false>
+__global__ void LISE_PENCILS_BOUNDS k_pencils_batch(const __grid_constant__ PencilBatch b) {
+  const int2 it = b.items[blockIdx.y];
+  pencils_body<R, N, TX, QB, MODE, ST>(b.evo[it.x], it.y, blockIdx.x, gridDim.x);
+}
+
 // ------------------------------------------------------- reduce/potentials --
 __device__ __forceinline__ void neumaier(double& s, double& c, double x) {
   double t = s + x;
@@ -1046,8 +1143,7 @@ __device__ __forceinline__ void neumaier(double& s, double& c, double x) {
   s = t;
 }
 
-__global__ void k_reduce(ReduceArgs a) {
-  const long s = (long)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void reduce_body(const ReduceArgs& a, const long s) {
   if (s >= a.nxyz) return;
   double n = 0, cn = 0, r = 0, cr = 0, i = 0, ci = 0;
   for (int g = 0; g < a.n_groups; ++g) {
@@ -1080,6 +1176,15 @@ __global__ void k_reduce(ReduceArgs a) {
   a.D[s] = make_double2(-geff * r, -geff * i);                            // Delta = -g_eff nu
 }
 
+__global__ void k_reduce(ReduceArgs a) { reduce_body(a, (long)blockIdx.x * blockDim.x + threadIdx.x); }
+
+// Several evolutions in one launch: evolution k owns blocks [b.block0[k], b.block0[k + 1]).
+__global__ void k_reduce_batch(ReduceBatch b) {
+  int k = 0;
+  while (k + 1 < b.n && (long)blockIdx.x >= b.block0[k + 1]) ++k;
+  reduce_body(b.evo[k], ((long)blockIdx.x - b.block0[k]) * blockDim.x + threadIdx.x);
+}
+
 // --------------------------------------------------------------- pointwise --
 // Eq. p, Eq. m and the corrector's Q, R (see lise_kernels.cuh) from the history
 //   y0 = y_{k}, y1 = y_{k-1}, d0..d3 = y'_{k}..y'_{k-3}, pc = p_k - c_k,
@@ -1094,12 +1199,10 @@ __global__ void k_reduce(ReduceArgs a) {
 // units of h/48 (as in the FP64 path), P = hf + pt, Q = P - (161/170) R and
 // m = P - (161/170)(p - c) in FP64; m is rounded to FP32 only as the operand of the next
 // FP32 H psi, and its densities are taken from its FP64 value.
-template <typename R, bool ST = false>
-__global__ void k_predict(PointwiseArgs a) {
+template <typename R, bool ST>
+__device__ __forceinline__ void predict_body(const PointwiseArgs& a, const long s, const int g) {
   using T = typename Cx<R>::T;
-  const long s = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= a.nxyz) return;
-  const int g = blockIdx.y;
   const int q_begin = g * a.qg, q_end = min(a.n_qp, q_begin + a.qg);
   const R h48 = (R)(a.h / 48.0);
   const R c161 = (R)(161.0 / 170.0), c9 = (R)(9.0 / 170.0);
@@ -1127,61 +1230,70 @@ __global__ void k_predict(PointwiseArgs a) {
       }
       dens_acc(md[0], md[1], sn, sr, si);
     }
-    const long o = (long)g * a.nxyz + s;
-    a.part_n[o] = 2.0 * sn;
-    a.part_nr[o] = sr;
-    a.part_ni[o] = si;
-    return;
-  }
-  for (int q = q_begin; q < q_end; ++q) {
-    T mo[2];  // m in the compute precision, for its densities
+  } else {
+    for (int q = q_begin; q < q_end; ++q) {
+      T mo[2];  // m in the compute precision, for its densities
 #pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      const long i = (long)(2 * q + c) * a.nxyz + s;
-      const T e0 = reinterpret_cast<const T*>(a.d0)[i], e1 = reinterpret_cast<const T*>(a.d1)[i],
-              e2 = reinterpret_cast<const T*>(a.d2)[i], e3 = reinterpret_cast<const T*>(a.d3)[i];
-      const T pcv = reinterpret_cast<const T*>(a.pc)[i];
-      const T pt = T{h48 * (R(119) * e0.x - R(99) * e1.x + R(69) * e2.x - R(17) * e3.x),
-                     h48 * (R(119) * e0.y - R(99) * e1.y + R(69) * e2.y - R(17) * e3.y)};
-      const T ct = T{h48 * (R(51) * e0.x + R(3) * e1.x + e2.x), h48 * (R(51) * e0.y + R(3) * e1.y + e2.y)};
-      // FP64 keeps p - c and R in units of h/48 (as the FP64 pencils epilogues do)
-      const R cpc = sizeof(R) == 8 ? c161 * h48 : c161;
-      const T X = T{pt.x - cpc * pcv.x, pt.y - cpc * pcv.y};
-      const T Y = T{c161 * ct.x + c9 * pt.x, c161 * ct.y + c9 * pt.y};
-      const double2 y0 = a.y0[i], y1 = a.y1[i];
-      if constexpr (sizeof(R) == 4) {
-        // Q = (y0 + y1)/2 + Y in FP64 (two FMAs); m = Q + (X - Y) only needs FP32,
-        // the precision it is stored and used in
-        const double2 Yd = to_d(Y);
-        const double2 qv = make_double2(fma(0.5, y0.x, fma(0.5, y1.x, Yd.x)), fma(0.5, y0.y, fma(0.5, y1.y, Yd.y)));
-        a.q[i] = qv;
-        const T qr = to_r<R>(qv);
-        const T mr = T{qr.x + (X.x - Y.x), qr.y + (X.y - Y.y)};
-        reinterpret_cast<T*>(a.m)[i] = mr;
-        mo[c] = mr;
-      } else {
-        const double2 hf = dscale(dadd(y0, y1), 0.5);
-        const double2 mv = dadd(hf, to_d(X));
-        reinterpret_cast<T*>(a.m)[i] = to_r<R>(mv);
-        a.q[i] = dadd(hf, to_d(Y));
-        mo[c] = to_r<R>(mv);
+      for (int c = 0; c < 2; ++c) {
+        const long i = (long)(2 * q + c) * a.nxyz + s;
+        const T e0 = reinterpret_cast<const T*>(a.d0)[i], e1 = reinterpret_cast<const T*>(a.d1)[i],
+                e2 = reinterpret_cast<const T*>(a.d2)[i], e3 = reinterpret_cast<const T*>(a.d3)[i];
+        const T pcv = reinterpret_cast<const T*>(a.pc)[i];
+        const T pt = T{h48 * (R(119) * e0.x - R(99) * e1.x + R(69) * e2.x - R(17) * e3.x),
+                       h48 * (R(119) * e0.y - R(99) * e1.y + R(69) * e2.y - R(17) * e3.y)};
+        const T ct = T{h48 * (R(51) * e0.x + R(3) * e1.x + e2.x), h48 * (R(51) * e0.y + R(3) * e1.y + e2.y)};
+        // FP64 keeps p - c and R in units of h/48 (as the FP64 pencils epilogues do)
+        const R cpc = sizeof(R) == 8 ? c161 * h48 : c161;
+        const T X = T{pt.x - cpc * pcv.x, pt.y - cpc * pcv.y};
+        const T Y = T{c161 * ct.x + c9 * pt.x, c161 * ct.y + c9 * pt.y};
+        const double2 y0 = a.y0[i], y1 = a.y1[i];
+        if constexpr (sizeof(R) == 4) {
+          // Q = (y0 + y1)/2 + Y in FP64 (two FMAs); m = Q + (X - Y) only needs FP32,
+          // the precision it is stored and used in
+          const double2 Yd = to_d(Y);
+          const double2 qv = make_double2(fma(0.5, y0.x, fma(0.5, y1.x, Yd.x)), fma(0.5, y0.y, fma(0.5, y1.y, Yd.y)));
+          a.q[i] = qv;
+          const T qr = to_r<R>(qv);
+          const T mr = T{qr.x + (X.x - Y.x), qr.y + (X.y - Y.y)};
+          reinterpret_cast<T*>(a.m)[i] = mr;
+          mo[c] = mr;
+        } else {
+          const double2 hf = dscale(dadd(y0, y1), 0.5);
+          const double2 mv = dadd(hf, to_d(X));
+          reinterpret_cast<T*>(a.m)[i] = to_r<R>(mv);
+          a.q[i] = dadd(hf, to_d(Y));
+          mo[c] = to_r<R>(mv);
+        }
+        if constexpr (sizeof(R) == 8)
+          reinterpret_cast<T*>(a.r)[i] = T{R(68) * e0.x - R(102) * e1.x + R(68) * e2.x - R(17) * e3.x,
+                                           R(68) * e0.y - R(102) * e1.y + R(68) * e2.y - R(17) * e3.y};
+        else
+          reinterpret_cast<T*>(a.r)[i] = T{pt.x - ct.x, pt.y - ct.y};
       }
-      if constexpr (sizeof(R) == 8)
-        reinterpret_cast<T*>(a.r)[i] = T{R(68) * e0.x - R(102) * e1.x + R(68) * e2.x - R(17) * e3.x,
-                                         R(68) * e0.y - R(102) * e1.y + R(68) * e2.y - R(17) * e3.y};
+      if constexpr (sizeof(R) == 4)
+        dens_acc(mo[0], mo[1], dF);
       else
-        reinterpret_cast<T*>(a.r)[i] = T{pt.x - ct.x, pt.y - ct.y};
+        dens_acc(mo[0], mo[1], sn, sr, si);
     }
-    if constexpr (sizeof(R) == 4)
-      dens_acc(mo[0], mo[1], dF);
-    else
-      dens_acc(mo[0], mo[1], sn, sr, si);
+    if constexpr (sizeof(R) == 4) dens_fold(dF, sn, sr, si);
   }
-  if constexpr (sizeof(R) == 4) dens_fold(dF, sn, sr, si);
   const long o = (long)g * a.nxyz + s;
   a.part_n[o] = 2.0 * sn;
   a.part_nr[o] = sr;
   a.part_ni[o] = si;
+}
+
+template <typename R, bool ST = false>
+__global__ void k_predict(PointwiseArgs a) {
+  predict_body<R, ST>(a, (long)blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y);
+}
+
+// Several evolutions of one lattice size in one launch: block row blockIdx.y is the item
+// (evolution, group) b.items[blockIdx.y].
+template <typename R, bool ST = false>
+__global__ void k_predict_batch(PredictBatch b) {
+  const int2 it = b.items[blockIdx.y];
+  predict_body<R, ST>(b.evo[it.x], (long)blockIdx.x * blockDim.x + threadIdx.x, it.y);
 }
 
 __global__ void k_density(PointwiseArgs a) {
@@ -1403,7 +1515,7 @@ static int planes_oz_n(const PlanesArgs& a, cudaStream_t s) {
   return cudaGetLastError() == cudaSuccess ? 0 : 3;
 }
 
-// persistent: kPlanesTcBlocksPerSM blocks per SM, each walking the planes
+// persistent: one warp-specialised block per SM, each walking the planes
 template <int N>
 static int planes_tc_n(const PlanesArgs& a, cudaStream_t s) {
   using P = TcPlanes<N>;
@@ -1415,21 +1527,34 @@ static int planes_tc_n(const PlanesArgs& a, cudaStream_t s) {
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return 3;
-  const long blocks = std::min<long>(a.n_planes, (long)kPlanesTcBlocksPerSM * sms);
-  kern<<<(unsigned)blocks, 256, P::smem, s>>>(a);
+  const long blocks = std::min<long>(a.n_planes, (long)sms);
+  kern<<<(unsigned)blocks, kWsThreads, P::smem, s>>>(a);
   return cudaGetLastError() == cudaSuccess ? 0 : 3;
 }
 
-template <typename R, int N>
-static int planes_n(const PlanesArgs& a, cudaStream_t s) {
+// Planes per block of the FFT planes kernel: the variants compiled for a lattice (shared
+// memory within 227 KB, at most 32 values per thread in registers); the default is
+// PlanesPB<N>, a tuned value replaces it (lise_api.cu: tune_planes).  Every plane is
+// transformed on its own, so the choice does not change any result.
+template <typename R, int N, int PB>
+constexpr bool planes_pb_fits() {
   using T = typename Cx<R>::T;
-  if constexpr (pencil_oz<R, N>()) {
-    if constexpr (N == 32)
-      return planes_tc_n<N>(a, s);
-    else
-      return planes_oz_n<N>(a, s);
-  }
-  constexpr int PB = PlanesPB<N>::v;
+  return (size_t)PB * N * (N + 1) * sizeof(T) + N * sizeof(T) + N * sizeof(R) <= 227 * 1024 &&
+         (PB * N * N + 255) / 256 <= 32;
+}
+static std::atomic<int> g_pb_tuned[2][65];  // 0: not tuned
+
+int planes_pb_get(int N, int mixed) {
+  if (N < 0 || N > 64) return 0;
+  return g_pb_tuned[mixed ? 1 : 0][N].load(std::memory_order_relaxed);
+}
+void planes_pb_set(int N, int mixed, int pb) {
+  if (N >= 0 && N <= 64) g_pb_tuned[mixed ? 1 : 0][N].store(pb, std::memory_order_relaxed);
+}
+
+template <typename R, int N, int PB>
+static int planes_npb(const PlanesArgs& a, cudaStream_t s) {
+  using T = typename Cx<R>::T;
   constexpr int NT = 256;
   const size_t smem = (size_t)PB * N * (N + 1) * sizeof(T) + N * sizeof(T) + N * sizeof(R);
   auto kern = k_planes<R, N, PB, NT>;
@@ -1439,6 +1564,42 @@ static int planes_n(const PlanesArgs& a, cudaStream_t s) {
   if (blocks <= 0) return 0;
   kern<<<(unsigned)blocks, NT, smem, s>>>(a);
   return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}
+
+template <typename R, int N>
+static int planes_n(const PlanesArgs& a, cudaStream_t s, int pb) {
+  if constexpr (pencil_oz<R, N>()) {
+    if constexpr (N == 32)
+      return planes_tc_n<N>(a, s);
+    else
+      return planes_oz_n<N>(a, s);
+  } else {
+    if (pb == 0) pb = planes_pb_get(N, sizeof(R) == 4);
+    if constexpr (planes_pb_fits<R, N, 1>())
+      if (pb == 1) return planes_npb<R, N, 1>(a, s);
+    if constexpr (planes_pb_fits<R, N, 2>())
+      if (pb == 2) return planes_npb<R, N, 2>(a, s);
+    if constexpr (planes_pb_fits<R, N, 4>())
+      if (pb == 4) return planes_npb<R, N, 4>(a, s);
+    if constexpr (planes_pb_fits<R, N, 8>())
+      if (pb == 8) return planes_npb<R, N, 8>(a, s);
+    return planes_npb<R, N, PlanesPB<N>::v>(a, s);
+  }
+}
+
+template <typename R, int N>
+static bool planes_pb_valid_n(int pb) {
+  if constexpr (pencil_oz<R, N>()) {
+    return false;
+  } else {
+    switch (pb) {
+      case 1: return planes_pb_fits<R, N, 1>();
+      case 2: return planes_pb_fits<R, N, 2>();
+      case 4: return planes_pb_fits<R, N, 4>();
+      case 8: return planes_pb_fits<R, N, 8>();
+      default: return false;
+    }
+  }
 }
 
 // ----------------------------------------------------- pencil batch autotune --
@@ -1545,6 +1706,115 @@ static int pencils_nm(const PencilArgs& a, cudaStream_t s, int qb) {
   return pencils_nmq_st<R, N, MODE, qb_default<R, N>()>(a, s);
 }
 
+#define LISE_FOR_N(X) X(8) X(12) X(16) X(20) X(24) X(32) X(40) X(48) X(64)
+
+// ------------------------------------------------------------- batched launches --
+// The FP32 compute precision (the batched path serves the mixed splits).
+template <int N, int MODE, int QB, bool ST>
+static int pencils_batch_nmq(const PencilBatch& b, int n_items, cudaStream_t s) {
+  using T = float2;
+  constexpr int TX = N % 8 != 0 ? 4 : 8;  // = pencil_tx(N, 1)
+  const size_t smem = (size_t)pencil_smem_bytes<T, N, TX, QB>();
+  auto kern = k_pencils_batch<float, N, TX, QB, MODE, ST>;
+  static std::atomic<unsigned long long> attr_done{0};
+  if (smem_attr((const void*)kern, smem, attr_done)) return 3;
+  if (n_items <= 0) return 0;
+  kern<<<dim3((N / TX) * N, n_items), N * TX, smem, s>>>(b);
+  return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}
+
+template <int N, int MODE, bool ST>
+static int pencils_batch_nm(const PencilBatch& b, int n_items, int qb, cudaStream_t s) {
+  if constexpr (qb_fits<float, N, 2>())
+    if (qb == 2) return pencils_batch_nmq<N, MODE, 2, ST>(b, n_items, s);
+  if constexpr (qb_fits<float, N, 4>())
+    if (qb == 4) return pencils_batch_nmq<N, MODE, 4, ST>(b, n_items, s);
+  return 1;
+}
+
+template <int N>
+static int pencils_batch_n(int mode, int strict, const PencilBatch& b, int n_items, int qb, cudaStream_t s) {
+  if (mode == M_CORRECT)
+    return strict ? pencils_batch_nm<N, M_CORRECT, true>(b, n_items, qb, s)
+                  : pencils_batch_nm<N, M_CORRECT, false>(b, n_items, qb, s);
+  if (mode == M_RHS) return pencils_batch_nm<N, M_RHS, false>(b, n_items, qb, s);
+  return 1;
+}
+
+template <int N, int PB>
+static int planes_batch_npb(const PlanesBatch& b, long n_blocks, cudaStream_t s) {
+  constexpr int NT = 256;
+  const size_t smem = (size_t)PB * N * (N + 1) * sizeof(float2) + N * sizeof(float2) + N * sizeof(float);
+  auto kern = k_planes_batch<float, N, PB, NT>;
+  static std::atomic<unsigned long long> attr_done{0};
+  if (smem_attr((const void*)kern, smem, attr_done)) return 3;
+  if (n_blocks <= 0) return 0;
+  kern<<<(unsigned)n_blocks, NT, smem, s>>>(b);
+  return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}
+
+template <int N>
+static int planes_batch_n(const PlanesBatch& b, long n_blocks, int pb, cudaStream_t s) {
+  if constexpr (planes_pb_fits<float, N, 1>())
+    if (pb == 1) return planes_batch_npb<N, 1>(b, n_blocks, s);
+  if constexpr (planes_pb_fits<float, N, 2>())
+    if (pb == 2) return planes_batch_npb<N, 2>(b, n_blocks, s);
+  if constexpr (planes_pb_fits<float, N, 4>())
+    if (pb == 4) return planes_batch_npb<N, 4>(b, n_blocks, s);
+  if constexpr (planes_pb_fits<float, N, 8>())
+    if (pb == 8) return planes_batch_npb<N, 8>(b, n_blocks, s);
+  return 1;
+}
+
+int launch_pencils_batch(int N, int mode, int strict, const PencilBatch& b, int n_items, int qb, cudaStream_t s) {
+  switch (N) {
+#define CASE(n) \
+  case n: return pencils_batch_n<n>(mode, strict, b, n_items, qb, s);
+    LISE_FOR_N(CASE)
+#undef CASE
+    default: return 1;
+  }
+}
+
+int launch_planes_batch(int N, int pb, const PlanesBatch& b, long n_blocks, cudaStream_t s) {
+  switch (N) {
+#define CASE(n) \
+  case n: return planes_batch_n<n>(b, n_blocks, pb, s);
+    LISE_FOR_N(CASE)
+#undef CASE
+    default: return 1;
+  }
+}
+
+long planes_blocks(long n_planes, int pb) { return pb > 0 ? (n_planes + pb - 1) / pb : 0; }
+
+int launch_reduce_batch(const ReduceBatch& b, long n_blocks, cudaStream_t s) {
+  if (n_blocks <= 0) return 0;
+  k_reduce_batch<<<(unsigned)n_blocks, 256, 0, s>>>(b);
+  return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}
+
+int launch_predict_batch(int strict, const PredictBatch& b, long nxyz, int n_items, cudaStream_t s) {
+  if (n_items <= 0) return 0;
+  dim3 grid((unsigned)((nxyz + 255) / 256), (unsigned)n_items);
+  if (strict)
+    k_predict_batch<float, true><<<grid, 256, 0, s>>>(b);
+  else
+    k_predict_batch<float, false><<<grid, 256, 0, s>>>(b);
+  return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}
+
+bool pencils_batch_maps(int N, int mode, int strict, int qb, PencilArgs* a) {
+  const int TX = pencil_tx(N, 1);
+  bool ok = encode_stage_map(&a->tm_x, a->xr ? a->xr : (const void*)a->x, !a->xr, N, a->n_qp, TX, qb) &&
+            encode_stage_map(&a->tm_t, a->txy, false, N, a->n_qp, TX, qb);
+  if (ok && mode == M_CORRECT) {
+    ok = encode_stage_map(&a->tm_q, a->q, true, N, a->n_qp, TX, qb) &&
+         (strict || encode_stage_map(&a->tm_r, a->r, false, N, a->n_qp, TX, qb));
+  }
+  return ok;
+}
+
 template <typename R, int N>
 static int pencils_n(int mode, const PencilArgs& a, cudaStream_t s, int qb) {
   switch (mode) {
@@ -1567,12 +1837,10 @@ static bool qb_valid_n(int qb) {
   return false;
 }
 
-#define LISE_FOR_N(X) X(8) X(12) X(16) X(20) X(24) X(32) X(40) X(48) X(64)
-
-int launch_planes(int N, int mixed, const PlanesArgs& a, cudaStream_t s) {
+int launch_planes(int N, int mixed, const PlanesArgs& a, cudaStream_t s, int pb) {
   switch (N) {
 #define CASE(n) \
-  case n: return mixed ? planes_n<float, n>(a, s) : planes_n<double, n>(a, s);
+  case n: return mixed ? planes_n<float, n>(a, s, pb) : planes_n<double, n>(a, s, pb);
     LISE_FOR_N(CASE)
 #undef CASE
     default: return 1;
@@ -1586,6 +1854,28 @@ int launch_pencils(int N, int mixed, int mode, const PencilArgs& a, cudaStream_t
     LISE_FOR_N(CASE)
 #undef CASE
     default: return 1;
+  }
+}
+
+bool planes_pb_valid(int N, int mixed, int pb) {
+  switch (N) {
+#define CASE(n) \
+  case n: return mixed ? planes_pb_valid_n<float, n>(pb) : planes_pb_valid_n<double, n>(pb);
+    LISE_FOR_N(CASE)
+#undef CASE
+    default: return false;
+  }
+}
+
+int planes_pb(int N, int mixed) {
+  const int t = planes_pb_get(N, mixed);
+  if (t) return t;
+  switch (N) {
+#define CASE(n) \
+  case n: return PlanesPB<n>::v;
+    LISE_FOR_N(CASE)
+#undef CASE
+    default: return 0;
   }
 }
 

@@ -123,6 +123,23 @@ struct ReduceArgs {
   int* err;               // set bit 0 if a density is not finite
 };
 
+// Batched launches (lise_batch_*): the arguments of several evolutions in device memory and a
+// work table mapping each block (row) to an evolution.
+struct PencilBatch {
+  const PencilArgs* evo;   // per evolution (tensor maps of the staged FP32 path included)
+  const int2* items;       // block row -> (evolution, density group of that evolution)
+};
+struct PlanesBatch {
+  const PlanesArgs* seg;   // per evolution
+  const long* block0;      // first block of each segment, n_seg + 1 entries
+  int n_seg;
+};
+struct ReduceBatch {
+  const ReduceArgs* evo;   // per evolution
+  const long* block0;      // first block of each evolution, n + 1 entries
+  int n;
+};
+
 // Effective pairing coupling and its density derivative (Eqs. g0, geff_3D).
 __host__ __device__ inline void pairing_geff(double g, double alpha_n0, double c, double n, double* geff,
                                              double* dgeff) {
@@ -151,6 +168,11 @@ struct PointwiseArgs {
   long nxyz;
 };
 
+struct PredictBatch {
+  const PointwiseArgs* evo;  // per evolution
+  const int2* items;         // block row -> (evolution, density group)
+};
+
 // The corrector of Eq. c splits as c_{n+1} = cbase_{n+1} + (17 h/48) m'_{n+1} with
 //   cbase_{n+1} = (y_n + y_{n-1})/2 + h/48 (51 y'_n + 3 y'_{n-1} + y'_{n-2}),
 // which depends only on the history known at predictor time.  With
@@ -166,7 +188,14 @@ struct PointwiseArgs {
 // state value runs in FP64.
 
 // Host-side launchers (defined in lise_kernels.cu).
-int launch_planes(int N, int mixed, const PlanesArgs& a, cudaStream_t s);
+// pb: planes per block of the FFT planes kernel (0 = the tuned value, else the default)
+int launch_planes(int N, int mixed, const PlanesArgs& a, cudaStream_t s, int pb = 0);
+// Planes-per-block autotuning state of the FFT planes kernel (per process): tuned value per
+// (precision, N), 0 = none; the value in use; whether a variant is compiled.
+int planes_pb_get(int N, int mixed);
+void planes_pb_set(int N, int mixed, int pb);
+int planes_pb(int N, int mixed);
+bool planes_pb_valid(int N, int mixed, int pb);
 // qb: states per batch of the step modes (2 or 4 where compiled); 0 = the tuned value,
 // else the default for the lattice and precision
 int launch_pencils(int N, int mixed, int mode, const PencilArgs& a, cudaStream_t s, int qb = 0);
@@ -175,6 +204,17 @@ int pencil_qb_get(int N, int mixed);
 void pencil_qb_set(int N, int mixed, int qb);
 bool pencil_qb_valid(int N, int mixed, int qb);
 int launch_reduce(const ReduceArgs& a, cudaStream_t s);
+// Batched launches of the FP32 compute precision (lise_batch_*): one launch over several
+// evolutions of lattice N (items / segments / blocks as in the batch structs); qb: the
+// pencils batch size (2 or 4, the one the evolutions' tensor maps were encoded for).
+int launch_pencils_batch(int N, int mode, int strict, const PencilBatch& b, int n_items, int qb, cudaStream_t s);
+int launch_planes_batch(int N, int pb, const PlanesBatch& b, long n_blocks, cudaStream_t s);
+long planes_blocks(long n_planes, int pb);  // blocks of the FFT planes kernel: pb planes per block
+int launch_reduce_batch(const ReduceBatch& b, long n_blocks, cudaStream_t s);
+int launch_predict_batch(int strict, const PredictBatch& b, long nxyz, int n_items, cudaStream_t s);
+// Tensor maps of one evolution's staged pencils launch (FP32 compute precision) written
+// into a->tm_* from its array pointers; false if the encoding fails.
+bool pencils_batch_maps(int N, int mode, int strict, int qb, PencilArgs* a);
 int launch_predict(const PointwiseArgs& a, cudaStream_t s);
 int launch_density(const PointwiseArgs& a, cudaStream_t s);
 int launch_energy_sites(const double* part_ekin, int n_groups, const double* n, const double2* nu,

@@ -19,6 +19,12 @@
 // Work of different requests overlaps on the device through their streams;
 // every request runs the same deterministic kernels on its own buffers, so its
 // result does not depend on what else is in flight.
+// With batching on (lise_server_set_batching), the stepper steps the active requests of
+// each FP32 compute precision together through one lise_batch (shared launches over a
+// device work table), rebuilt whenever a request joins (its series start has finished
+// on the device) or leaves (its steps are done); the others are stepped one by one.
+// A batch's members advance by the same number of steps per turn, so every chunk is
+// bounded by the member with the fewest steps left.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -55,6 +61,8 @@ struct Request {
   cudaStream_t stream = nullptr;
   cudaEvent_t ev = nullptr;
   bool ev_pending = false;
+  cudaEvent_t ready_ev = nullptr;  // the series start has finished (batch membership)
+  bool batched = false;            // stepped through a batch
   int status = LISE_OK;
   enum State { QUEUED, ACTIVE, DONE } state = QUEUED;
   int skipped = 0;  // times a later request was admitted ahead of this one
@@ -63,8 +71,19 @@ struct Request {
 
 }  // namespace
 
+// Requests stepped together (one per batchable precision).
+struct BatchGroup {
+  int precision = 0;
+  std::vector<Request*> members;
+  lise_batch* batch = nullptr;
+  cudaEvent_t ev = nullptr;  // end of the last chunk
+  bool pending = false;
+};
+
 struct lise_server {
   int device = 0;
+  bool batching = false;
+  BatchGroup groups[2];  // LISE_MIXED, LISE_MIXED_STRICT
   size_t budget = 0;
   int max_active = 1;
   int steps_per_turn = 1;
@@ -89,6 +108,7 @@ struct lise_server {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
   void run_stepper();
+  void step_loop();
   void run_service();
 };
 
@@ -120,6 +140,8 @@ void finish(lise_server* s, Request* r) {
     r->ctx = nullptr;
   }
   if (r->ev) cudaEventDestroy(r->ev);
+  if (r->ready_ev) cudaEventDestroy(r->ready_ev);
+  r->ready_ev = nullptr;
   if (r->stream) cudaStreamDestroy(r->stream);
   r->ev = nullptr;
   r->stream = nullptr;
@@ -142,22 +164,147 @@ int admit(Request* r) {
     rc = lise_create(&r->p, &r->ctx);
   }
   if (rc == LISE_OK) rc = lise_set_state_enqueue(r->ctx, r->borrowed ? r->src : r->host, r->t0, r->dt);
+  if (rc == LISE_OK && cudaEventCreateWithFlags(&r->ready_ev, cudaEventDisableTiming) != cudaSuccess) rc = LISE_ECUDA;
+  if (rc == LISE_OK && cudaEventRecord(r->ready_ev, r->stream) != cudaSuccess) rc = LISE_ECUDA;
   return rc;
+}
+
+bool batchable(const Request* r) {
+  return (r->p.precision == LISE_MIXED || r->p.precision == LISE_MIXED_STRICT) && !r->p.remove_phase &&
+         !r->p.renormalize;
 }
 
 }  // namespace
 
 void lise_server::run_stepper() {
+  for (;;) {
+    try {
+      step_loop();  // returns when the server stops
+      return;
+    } catch (...) {
+      // host containers could not grow: fail the requests in flight (the service threads
+      // retire them) and carry on with the next ones rather than end the process
+      for (auto& G : groups) {
+        if (G.batch) lise_batch_destroy(G.batch);
+        G.batch = nullptr;
+        G.members.clear();
+        G.pending = false;
+      }
+      std::lock_guard<std::mutex> lk(mu);
+      for (Request* r : active) {
+        r->status = LISE_ENOMEM;
+        r->batched = false;
+        retire.push_back(r);
+      }
+      active.clear();
+      cv_service.notify_all();
+    }
+  }
+}
+
+void lise_server::step_loop() {
   cudaSetDevice(device);
   std::vector<Request*> act;
+  auto to_retire = [&](Request* r) {
+    std::lock_guard<std::mutex> lk(mu);
+    active.erase(std::find(active.begin(), active.end(), r));
+    retire.push_back(r);
+    cv_service.notify_one();
+  };
   for (;;) {
+    bool batching_now;
     {
       std::lock_guard<std::mutex> lk(mu);
-      if (stop && queue.empty() && in_flight == 0) return;
+      if (stop && queue.empty() && in_flight == 0) {
+        for (auto& G : groups) {
+          if (G.batch) lise_batch_destroy(G.batch);
+          if (G.ev) cudaEventDestroy(G.ev);
+          G.batch = nullptr;
+          G.ev = nullptr;
+        }
+        return;
+      }
       act = active;
+      batching_now = batching;
     }
     bool progressed = false;
+    // batched requests: one chunk at a time per group; membership changes between chunks
+    for (int gi = 0; gi < 2 && batching_now; ++gi) {
+      BatchGroup& G = groups[gi];
+      G.precision = gi == 0 ? LISE_MIXED : LISE_MIXED_STRICT;
+      if (G.pending) {
+        const cudaError_t q = cudaEventQuery(G.ev);
+        if (q == cudaErrorNotReady) continue;
+        G.pending = false;
+        if (q != cudaSuccess)
+          for (Request* r : G.members) r->status = LISE_ECUDA;
+      }
+      // leaving: finished or failed members; joining: requests whose series start is done.
+      // (A fresh snapshot: a request retired above may already be gone.)
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        act = active;
+      }
+      std::vector<Request*> keep, joined;
+      for (Request* r : G.members)
+        if (r->status == LISE_OK && r->done_steps < r->n_steps) keep.push_back(r);
+      for (Request* r : act)
+        if (!r->batched && batchable(r) && r->p.precision == G.precision && r->status == LISE_OK &&
+            r->done_steps < r->n_steps && !r->ev_pending && cudaEventQuery(r->ready_ev) == cudaSuccess)
+          joined.push_back(r);
+      const bool changed = keep.size() != G.members.size() || !joined.empty();
+      if (changed || (!G.batch && !keep.empty())) {
+        if (G.batch) lise_batch_destroy(G.batch);
+        G.batch = nullptr;
+        for (Request* r : G.members)
+          if (std::find(keep.begin(), keep.end(), r) == keep.end()) {
+            r->batched = false;
+            to_retire(r);
+          }
+        for (Request* r : joined) r->batched = true;
+        keep.insert(keep.end(), joined.begin(), joined.end());
+        G.members = keep;
+        progressed = true;
+        if (!G.members.empty()) {
+          std::vector<lise_ctx*> cs;
+          for (Request* r : G.members) cs.push_back(r->ctx);
+          const int rc = lise_batch_create(cs.data(), (int)cs.size(), &G.batch);
+          if (rc != LISE_OK) {
+            for (Request* r : G.members) r->status = rc;
+            continue;  // retired at the next turn
+          }
+          if (!G.ev && cudaEventCreateWithFlags(&G.ev, cudaEventDisableTiming) != cudaSuccess) G.ev = nullptr;
+        }
+      }
+      if (!G.batch || G.members.empty()) continue;
+      int k = steps_per_turn;
+      for (Request* r : G.members) k = std::min(k, r->n_steps - r->done_steps);
+      int rc = lise_batch_step(G.batch, k);
+      if (rc == LISE_OK && (!G.ev || cudaEventRecord(G.ev, (cudaStream_t)lise_batch_stream(G.batch)) != cudaSuccess))
+        rc = LISE_ECUDA;
+      if (rc != LISE_OK) {
+        for (Request* r : G.members) r->status = rc;
+      } else {
+        for (Request* r : G.members) r->done_steps += k;
+        G.pending = true;
+      }
+      progressed = true;
+    }
+    // requests stepped one by one (a fresh snapshot: the batch groups above may have retired
+    // some of the earlier one's requests, which must not be touched again)
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      act = active;
+    }
     for (Request* r : act) {
+      if (r->batched) continue;
+      if (batching_now && batchable(r) && r->status == LISE_OK && r->done_steps < r->n_steps && !r->ev_pending)
+        continue;  // waits for its series start, then joins its batch group
+      if (batching_now && batchable(r) && r->status != LISE_OK) {
+        to_retire(r);
+        progressed = true;
+        continue;
+      }
       if (r->ev_pending) {
         const cudaError_t q = cudaEventQuery(r->ev);
         if (q == cudaErrorNotReady) continue;
@@ -177,12 +324,7 @@ void lise_server::run_stepper() {
           r->ev_pending = true;
         }
       }
-      if (last) {
-        std::lock_guard<std::mutex> lk(mu);
-        active.erase(std::find(active.begin(), active.end(), r));
-        retire.push_back(r);
-        cv_service.notify_one();
-      }
+      if (last) to_retire(r);
       progressed = true;
     }
     if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(100));
@@ -368,6 +510,14 @@ int lise_server_set_admission(lise_server* s, int policy, int max_skips) {
     s->max_skips = max_skips;
   }
   s->cv_service.notify_one();
+  return LISE_OK;
+}
+
+int lise_server_set_batching(lise_server* s, int enable) {
+  if (!s) return LISE_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (s->next_id != 1) return LISE_ESTATE;  // only before the first submission
+  s->batching = enable != 0;
   return LISE_OK;
 }
 

@@ -63,6 +63,41 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, long 
   return done != 0;
 }
 
+// The same wait that also gives up once *stop becomes non-zero (another role of the block
+// gave up): returns false on timeout or stop.
+__device__ __forceinline__ bool mbar_wait_or(uint64_t* mbar, uint32_t parity, long limit, const volatile int* stop) {
+  uint32_t done = 0;
+  for (long it = 0; it < limit && !done; ++it) {
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(su32(mbar)), "r"(parity)
+        : "memory");
+    if (!done && *stop) return false;
+  }
+  return done != 0;
+}
+
+// Arrive on an mbarrier (release semantics at CTA scope).
+__device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(mbar)) : "memory");
+}
+
+// Named barrier `id` over `count` threads (a multiple of 32; whole warps), and the same with an
+// AND over the participating threads' predicates (every participant gets the same result).
+__device__ __forceinline__ void bar_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool bar_and(int id, int count, bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n.reg .pred pi, po;\nsetp.ne.u32 pi, %1, 0;\nbar.red.and.pred po, %2, %3, pi;\nselp.u32 %0, 1, 0, po;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v), "r"(id), "r"(count)
+      : "memory");
+  return r != 0;
+}
+
 // Tensor-memory allocation (one full warp): ncols columns (a power of 2, >= 32); the base
 // address is written to shared memory.
 __device__ __forceinline__ void alloc(uint32_t* slot, uint32_t ncols) {

@@ -61,6 +61,8 @@ SIGNATURES = {
     "lise_currents": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lise_pencil_batch": (C.c_int, [C.c_int, C.c_int]),
     "lise_set_pencil_batch": (C.c_int, [C.c_int, C.c_int, C.c_int]),
+    "lise_planes_per_block": (C.c_int, [C.c_int, C.c_int]),
+    "lise_set_planes_per_block": (C.c_int, [C.c_int, C.c_int, C.c_int]),
     "lise_step": (C.c_int, [C.c_void_p, C.c_int, C.c_double]),
     "lise_get_state": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lise_get_state_device": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -81,6 +83,10 @@ SIGNATURES = {
     "lise_checkpoint_bytes": (C.c_size_t, [C.c_void_p]),
     "lise_checkpoint_save": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "lise_checkpoint_load": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "lise_batch_create": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "lise_batch_step": (C.c_int, [C.c_void_p, C.c_int]),
+    "lise_batch_sync": (C.c_int, [C.c_void_p]),
+    "lise_batch_destroy": (None, [C.c_void_p]),
     "lise_server_create": (C.c_int, [C.c_int, C.c_size_t, C.c_int, C.c_int, C.c_void_p]),
     "lise_server_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_int,
                                      C.POINTER(C.c_long)]),
@@ -90,6 +96,7 @@ SIGNATURES = {
     "lise_server_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t), C.POINTER(C.c_int)]),
     "lise_server_poll": (C.c_int, [C.c_void_p, C.c_long, C.POINTER(C.c_int)]),
     "lise_server_set_admission": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "lise_server_set_batching": (C.c_int, [C.c_void_p, C.c_int]),
     "lise_server_destroy": (None, [C.c_void_p]),
 }
 
@@ -153,6 +160,16 @@ def measure_fp64_peak(device=0) -> float:
     t = C.c_double()
     _check(load().lise_measure_fp64_peak(int(device), C.byref(t)), "lise_measure_fp64_peak")
     return t.value
+
+
+def planes_per_block(N, precision="mixed") -> int:
+    """Planes per block of the FFT planes kernel for this lattice and precision (0: tensor-core kernel)."""
+    return int(load().lise_planes_per_block(int(N), PRECISIONS[precision]))
+
+
+def set_planes_per_block(N, precision="mixed", pb=0):
+    """Force the FFT planes kernel's planes per block (1, 2, 4, 8 where compiled), or 0 to re-tune."""
+    _check(load().lise_set_planes_per_block(int(N), PRECISIONS[precision], int(pb)), "lise_set_planes_per_block")
 
 
 def footprint_bytes(N, n_qp, precision="fp64", **kw) -> int:
@@ -337,6 +354,38 @@ class Context:
         _check(load().lise_set_wait_limit(self._h, int(polls)), "lise_set_wait_limit")
 
 
+class Batch:
+    """Several contexts (FP32 compute precision, after set_state) stepped together in shared
+    launches (lise_batch_*).  Use the contexts only through the batch until sync() or close()."""
+
+    def __init__(self, contexts):
+        self._ctxs = list(contexts)
+        arr = (C.c_void_p * len(self._ctxs))(*[c._h.value for c in self._ctxs])
+        h = C.c_void_p()
+        _check(load().lise_batch_create(arr, len(self._ctxs), C.byref(h)), "lise_batch_create")
+        self._h = h
+
+    def step(self, n_steps):
+        _check(load().lise_batch_step(self._h, int(n_steps)), "lise_batch_step")
+
+    def sync(self):
+        _check(load().lise_batch_sync(self._h), "lise_batch_sync")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().lise_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
 class RequestInfo(C.Structure):
     _fields_ = [("status", C.c_int), ("submit_s", C.c_double), ("admit_s", C.c_double),
                 ("done_s", C.c_double), ("t", C.c_double), ("E", C.c_double), ("N", C.c_double)]
@@ -414,6 +463,10 @@ class Server:
         """'fifo' (arrival order) or 'first_fit' (a request may be passed over at most max_skips times)."""
         code = {"fifo": ADMIT_FIFO, "first_fit": ADMIT_FIRST_FIT}[policy]
         _check(load().lise_server_set_admission(self._h, code, int(max_skips)), "lise_server_set_admission")
+
+    def set_batching(self, enable=True):
+        """Step the active mixed-precision requests together in shared launches (before submitting)."""
+        _check(load().lise_server_set_batching(self._h, int(bool(enable))), "lise_server_set_batching")
 
     def stats(self):
         u, a = C.c_size_t(), C.c_int()

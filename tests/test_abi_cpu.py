@@ -126,3 +126,17 @@ def test_pencil_batch_controls_host_only():
     with pytest.raises(L.LiseError) as e:
         L.set_pencil_batch(24, "fp64", 1)                # 24 % 16 != 0: FFT kernels
     assert e.value.status == L.EINVAL
+
+
+def test_planes_per_block_controls_host_only():
+    assert L.planes_per_block(32, "fp64") == 0          # tensor-core planes kernel
+    assert L.planes_per_block(48, "mixed") in (1, 2, 4, 8)
+    with pytest.raises(L.LiseError) as e:
+        L.set_planes_per_block(32, "fp64", 2)           # no FFT planes kernel there
+    assert e.value.status == L.EINVAL
+    with pytest.raises(L.LiseError) as e:
+        L.set_planes_per_block(64, "mixed", 8)          # 8 planes of 64^2 do not fit
+    assert e.value.status == L.EINVAL
+    L.set_planes_per_block(16, "mixed", 8)
+    assert L.planes_per_block(16, "mixed") == 8
+    L.set_planes_per_block(16, "mixed", 0)

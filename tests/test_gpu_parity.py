@@ -536,6 +536,31 @@ def test_pencil_batch_choice_is_bitwise_neutral(N, precision):
         assert np.array_equal(x, tuned)
 
 
+@pytest.mark.parametrize("N,precision", [(24, "mixed"), (48, "mixed"), (12, "fp64")])
+def test_planes_per_block_choice_is_bitwise_neutral(N, precision):
+    w = W.ufg_plane_waves(N, 13, noise_eps=0.05)
+
+    def run():
+        with L.Context.from_workload(w, precision=precision) as ctx:
+            ctx.set_state(w.initial_state(), 0.0, w.dt)
+            ctx.step(5)
+            return ctx.state()
+
+    outs = {}
+    for pb in (1, 2, 4, 8):
+        try:
+            L.set_planes_per_block(N, precision, pb)
+        except L.LiseError:
+            continue  # variant not compiled for this lattice
+        outs[pb] = run()
+    L.set_planes_per_block(N, precision, 0)   # the next set_state tunes
+    tuned = run()
+    assert len(outs) >= 2
+    assert L.planes_per_block(N, precision) in outs
+    for x in outs.values():
+        assert np.array_equal(x, tuned)
+
+
 # ------------------------------------------------------------ large lattices ----
 
 def test_fp64_run_64_cubed():

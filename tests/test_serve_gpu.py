@@ -18,7 +18,10 @@ def alone(w, steps, precision):
         return ctx.state(), ctx.energy()
 
 
-def test_results_identical_alone_and_in_the_mix():
+@pytest.mark.parametrize("batching", [False, True])
+def test_results_identical_alone_and_in_the_mix(batching):
+    # with batching, the mixed-precision requests are stepped together in shared launches
+    # (joining and leaving the batch as they start and finish); the FP64 ones alone
     reqs = [
         (W.ufg_plane_waves(16, 40, noise_eps=0.05), 12, "fp64"),
         (W.trap_vortex(16, 24), 9, "mixed"),
@@ -31,6 +34,8 @@ def test_results_identical_alone_and_in_the_mix():
     fps = [L.footprint_bytes(w.nx, w.n_qp, precision=prec) for w, _, prec in reqs]
     budget = int(2.2 * max(fps))  # forces queueing: at most a few requests fit at once
     with L.Server(budget, max_active=4, steps_per_turn=3) as srv:
+        if batching:
+            srv.set_batching(True)
         ids = [srv.submit_workload(w, n_steps=k, precision=prec) for w, k, prec in reqs]
         outs = [srv.wait(i) for i in ids]
         st = srv.stats()
@@ -121,3 +126,24 @@ def test_borrowed_submission_matches_copied():
         assert np.array_equal(o, ref_psi)
         assert info["E"] == E and info["N"] == N
     assert psi_none is None and info_none["status"] == L.OK and info_none["E"] == refs[0][1][0]
+
+
+def test_batched_serving_of_mixed_requests():
+    # only mixed requests, all admitted at once, uneven step counts: members leave the batch
+    # as they finish and the batch is rebuilt for the rest; every result as if alone
+    reqs = [(W.driven(16, 30, A=0.03, noise_eps=0.05), 6), (W.ufg_plane_waves(24, 20, noise_eps=0.05), 11),
+            (W.driven(16, 12, A=0.01, noise_eps=0.05), 9), (W.trap_vortex(12, 16), 14)]
+    for w, _ in reqs:
+        w.precision = "mixed"
+    refs = [alone(w, k, "mixed") for w, k in reqs]
+    with L.Server(1 << 34, max_active=8, steps_per_turn=4) as srv:
+        srv.set_batching(True)
+        ids = [srv.submit_workload(w, n_steps=k) for w, k in reqs]
+        outs = [srv.wait(i) for i in ids]
+        with pytest.raises(L.LiseError) as e:   # only before the first submission
+            srv.set_batching(False)
+        assert e.value.status == L.ESTATE
+    for (psi, info), (ref_psi, (E, N)) in zip(outs, refs):
+        assert info["status"] == L.OK
+        assert np.array_equal(psi, ref_psi)
+        assert info["E"] == E

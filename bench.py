@@ -406,7 +406,7 @@ def run_batch(args):
         base[n] = (w, w.initial_state())
     budget = int(args.batch_budget_gb * 1e9)
     fps = [L.footprint_bytes(int(l), int(nq), precision="mixed") for l, nq in zip(lattices, nqps)]
-    with L.Server(budget, max_active=args.batch_max_active, steps_per_turn=args.serve_turn) as srv:
+    with L.Server(budget, max_active=args.batch_max_active, steps_per_turn=args.batch_turn) as srv:
         srv.set_admission("first_fit", max_skips=args.batch_max_skips)
         if not args.batch_separate:
             srv.set_batching(True)
@@ -439,7 +439,7 @@ def run_batch(args):
             "stepping": "separate contexts" if args.batch_separate else "shared launches (lise_batch)",
             "hbm_budget_gb": args.batch_budget_gb, "max_active": args.batch_max_active,
             "admission": "first fit, max %d skips" % args.batch_max_skips,
-            "steps_per_turn": args.serve_turn, "sum_footprint_gb": round(sum(fps) / 1e9, 1),
+            "steps_per_turn": args.batch_turn, "sum_footprint_gb": round(sum(fps) / 1e9, 1),
             "throughput": units / makespan, "unit": UNIT, "makespan_s": makespan, "wall_s": wall,
             "peak_used_gb": st["peak_used_bytes"] / 1e9, "peak_active": st["peak_active"],
             "all_ok": all(inf["status"] == 0 for inf in infos),
@@ -645,6 +645,7 @@ def main():
     ap.add_argument("--batch-budget-gb", type=float, default=200.0)
     ap.add_argument("--batch-max-active", type=int, default=8)
     ap.add_argument("--batch-max-skips", type=int, default=8)
+    ap.add_argument("--batch-turn", type=int, default=8, help="steps per turn of the batched evolutions")
     ap.add_argument("--batch-separate", action="store_true",
                     help="step every evolution on its own (no shared launches)")
     ap.add_argument("--pencil-batch", type=int, default=0,

@@ -109,7 +109,7 @@ struct lise_ctx {
   // parity x position of the derivative ring), replayed by lise_step
   cudaGraphExec_t graph[2][4] = {};
   double* drive_dev = nullptr;  // drive amplitudes of the reductions of one replay
-  double drive_host_t[16] = {};  // offsets (t - t_start) of those reductions, recorded at capture
+  int drive_red = 0;  // reductions per captured ABM step (2); checked at capture
   int capturing = 0;            // > 0 while capturing: index of the next reduction
   void* D_base[4] = {nullptr, nullptr, nullptr, nullptr};  // the ring's allocations in ring order
   // per-launch timing (lise_profile)
@@ -316,7 +316,6 @@ int run_reduce(lise_ctx* c, int dslot, const double* avg_n, const double2* avg_n
   r.drive = drive_at(c, t);
   if (c->capturing) {  // inside a graph: the amplitude is refreshed before every replay
     if (c->p.drive_A != 0.0) r.drive_ptr = c->drive_dev + (c->capturing - 1);
-    c->drive_host_t[c->capturing - 1] = t;
     ++c->capturing;
   }
   return timed(c, LISE_KC_REDUCE, [&] { return launch_reduce(r, c->stream) ? LISE_ECUDA : LISE_OK; });
@@ -561,12 +560,13 @@ int capture_graph(lise_ctx* c, cudaGraphExec_t* out) {
   c->capturing = 1;
   int rc = LISE_OK;
   for (int k = 0; k < kGraphSteps && rc == LISE_OK; ++k) rc = abm_step(c);
-  for (int k = 0; k < c->capturing - 1; ++k) c->drive_host_t[k] -= t0;
+  c->drive_red = c->capturing - 1;  // reductions captured (2 per ABM step)
   c->capturing = 0;
   cudaError_t e = cudaStreamEndCapture(c->stream, &g);
   c->t = t0;
   c->y0_slot = slot0;
   for (int k = 0; k < 4; ++k) c->D[k] = d0[k];
+  if (rc == LISE_OK && c->drive_red != 2 * kGraphSteps) rc = LISE_ECUDA;  // (the replay's drive table)
   if (rc != LISE_OK) {
     if (g) cudaGraphDestroy(g);
     return rc;
@@ -585,7 +585,15 @@ int graph_steps(lise_ctx* c) {
   if (!g) TRY(capture_graph(c, &g));
   if (c->p.drive_A != 0.0) {
     double amp[2 * kGraphSteps];
-    for (int k = 0; k < 2 * kGraphSteps; ++k) amp[k] = drive_at(c, c->t + c->drive_host_t[k]);
+    // the times of a step's two reductions, t_{n+1} = t_n + dt and t_{n+1} + dt, accumulated
+    // exactly as abm_step does, so that a replay is bitwise the plain launches
+    double t = c->t;
+    for (int j = 0; j < kGraphSteps; ++j) {
+      const double t1 = t + c->dt;
+      amp[2 * j] = drive_at(c, t1);
+      amp[2 * j + 1] = drive_at(c, t1 + c->dt);
+      t = t1;
+    }
     TRY(cu(cudaMemcpyAsync(c->drive_dev, amp, sizeof(amp), cudaMemcpyHostToDevice, c->stream)));
   }
   TRY(cu(cudaGraphLaunch(g, c->stream)));
@@ -1423,11 +1431,14 @@ struct lise_batch {
     PointwiseArgs* pred[4] = {};
     int2* items = nullptr;
     long* pl_block0 = nullptr;
+    ReduceArgs* red[4][2] = {};       // the reductions of these evolutions
+    long* red_block0 = nullptr;
+    long red_blocks = 0;
+    cudaStream_t stream = nullptr;    // this size's launches (forked from and joined to the batch stream)
+    cudaEvent_t done = nullptr;       // end of this size's launches of a chunk
   };
+  cudaEvent_t fork = nullptr;
   std::vector<Size> sizes;
-  ReduceArgs* red[4][2] = {};
-  long* red_block0 = nullptr;
-  long red_blocks = 0;
   double* drive_dev = nullptr;        // [4 phases][2 reductions][evolutions]
   std::vector<double> drive_host;
   void* tables = nullptr;
@@ -1441,31 +1452,51 @@ void free_batch(lise_batch* b) {
   for (auto& g : b->graph)
     if (g) cudaGraphExecDestroy(g);
   if (b->stream) cudaStreamSynchronize(b->stream);
+  for (auto& z : b->sizes) {
+    if (z.stream) cudaStreamDestroy(z.stream);
+    if (z.done) cudaEventDestroy(z.done);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
   if (b->tables) cudaFree(b->tables);
   if (b->stream) cudaStreamDestroy(b->stream);
 }
 
-// Launches of one ABM step in history phase k.
-int batch_launch_step(lise_batch* b, int k) {
-  const int E = (int)b->ctx.size();
+// The launches made by f(size, stream) for every lattice size, each size on its own stream
+// (the sizes run independently on the device), forked from and joined back to the batch stream.
+template <typename F>
+int batch_per_size(lise_batch* b, F f) {
+  if (b->sizes.size() == 1) return f(b->sizes[0], b->stream);
+  if (cudaEventRecord(b->fork, b->stream) != cudaSuccess) return LISE_ECUDA;
+  for (auto& z : b->sizes) {
+    if (cudaStreamWaitEvent(z.stream, b->fork, 0) != cudaSuccess) return LISE_ECUDA;
+    TRY(f(z, z.stream));
+    if (cudaEventRecord(z.done, z.stream) != cudaSuccess) return LISE_ECUDA;
+  }
   for (auto& z : b->sizes)
-    if (launch_planes_batch(z.N, z.pb, PlanesBatch{z.pl_m[k], z.pl_block0, (int)z.evo.size()}, z.pl_blocks, b->stream))
-      return LISE_ECUDA;
-  for (auto& z : b->sizes)
-    if (launch_pencils_batch(z.N, M_CORRECT, b->strict, PencilBatch{z.corr[k], z.items}, z.n_items, z.qb, b->stream))
-      return LISE_ECUDA;
-  if (launch_reduce_batch(ReduceBatch{b->red[k][0], b->red_block0, E}, b->red_blocks, b->stream)) return LISE_ECUDA;
-  for (auto& z : b->sizes)
-    if (launch_planes_batch(z.N, z.pb, PlanesBatch{z.pl_y[k], z.pl_block0, (int)z.evo.size()}, z.pl_blocks, b->stream))
-      return LISE_ECUDA;
-  for (auto& z : b->sizes)
-    if (launch_pencils_batch(z.N, M_RHS, 0, PencilBatch{z.deriv[k], z.items}, z.n_items, z.qb, b->stream))
-      return LISE_ECUDA;
-  for (auto& z : b->sizes)
-    if (launch_predict_batch(b->strict, PredictBatch{z.pred[k], z.items}, z.nxyz, z.n_items, b->stream))
-      return LISE_ECUDA;
-  if (launch_reduce_batch(ReduceBatch{b->red[k][1], b->red_block0, E}, b->red_blocks, b->stream)) return LISE_ECUDA;
+    if (cudaStreamWaitEvent(b->stream, z.done, 0) != cudaSuccess) return LISE_ECUDA;
   return LISE_OK;
+}
+
+// The launches of one ABM step in history phase k of the evolutions of one lattice size.
+int batch_size_step(lise_batch* b, lise_batch::Size& z, int k, cudaStream_t st) {
+  const int ne = (int)z.evo.size();
+  if (launch_planes_batch(z.N, z.pb, PlanesBatch{z.pl_m[k], z.pl_block0, ne}, z.pl_blocks, st) ||
+      launch_pencils_batch(z.N, M_CORRECT, b->strict, PencilBatch{z.corr[k], z.items}, z.n_items, z.qb, st) ||
+      launch_reduce_batch(ReduceBatch{z.red[k][0], z.red_block0, ne}, z.red_blocks, st) ||
+      launch_planes_batch(z.N, z.pb, PlanesBatch{z.pl_y[k], z.pl_block0, ne}, z.pl_blocks, st) ||
+      launch_pencils_batch(z.N, M_RHS, 0, PencilBatch{z.deriv[k], z.items}, z.n_items, z.qb, st) ||
+      launch_predict_batch(b->strict, PredictBatch{z.pred[k], z.items}, z.nxyz, z.n_items, st) ||
+      launch_reduce_batch(ReduceBatch{z.red[k][1], z.red_block0, ne}, z.red_blocks, st))
+    return LISE_ECUDA;
+  return LISE_OK;
+}
+
+// m ABM steps from history phase k0.
+int batch_launch_steps(lise_batch* b, int k0, int m) {
+  return batch_per_size(b, [&](lise_batch::Size& z, cudaStream_t st) {
+    for (int j = 0; j < m; ++j) TRY(batch_size_step(b, z, (k0 + j) % 4, st));
+    return LISE_OK;
+  });
 }
 
 // Drive amplitudes of the reductions of the next m steps (phases step .. step + m - 1).
@@ -1476,11 +1507,13 @@ int batch_refresh_drive(lise_batch* b, int m) {
     lise_ctx* c = b->ctx[e];
     if (c->p.drive_A == 0.0) continue;
     any = true;
+    double t = c->t;  // accumulated as abm_step does (bitwise the same times)
     for (int j = 0; j < m; ++j) {
       const int k = (int)((b->step + j) % 4);
-      const double t1 = c->t + (j + 1) * c->dt;
+      const double t1 = t + c->dt;
       b->drive_host[(size_t)(2 * k) * E + e] = drive_at(c, t1);
       b->drive_host[(size_t)(2 * k + 1) * E + e] = drive_at(c, t1 + c->dt);
+      t = t1;
     }
   }
   if (!any) return LISE_OK;
@@ -1532,6 +1565,7 @@ static int batch_create(lise_ctx* const* ctxs, int n, lise_batch** out) {
     b->D0.push_back({c->D[0], c->D[1], c->D[2], c->D[3]});
   }
   if (rc == LISE_OK && cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) rc = LISE_ECUDA;
+  if (rc == LISE_OK && cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) rc = LISE_ECUDA;
   // lattice sizes in order of first appearance
   for (int e = 0; e < n && rc == LISE_OK; ++e) {
     lise_ctx* c = ctxs[e];
@@ -1547,6 +1581,10 @@ static int batch_create(lise_ctx* const* ctxs, int n, lise_batch** out) {
     }
     it->evo.push_back(e);
   }
+  for (auto& z : b->sizes) {
+    if (rc == LISE_OK && cudaStreamCreateWithFlags(&z.stream, cudaStreamNonBlocking) != cudaSuccess) rc = LISE_ECUDA;
+    if (rc == LISE_OK && cudaEventCreateWithFlags(&z.done, cudaEventDisableTiming) != cudaSuccess) rc = LISE_ECUDA;
+  }
   // host image of every table, then one device copy
   std::vector<unsigned char> img;
   auto place = [&](size_t bytes) {
@@ -1555,7 +1593,7 @@ static int batch_create(lise_ctx* const* ctxs, int n, lise_batch** out) {
     return off;
   };
   struct Off {
-    size_t corr[4], deriv[4], pl_m[4], pl_y[4], pred[4], items, pl_block0;
+    size_t corr[4], deriv[4], pl_m[4], pl_y[4], pred[4], red[4][2], items, pl_block0, red_block0;
   };
   std::vector<Off> off(b->sizes.size());
   for (size_t zi = 0; zi < b->sizes.size(); ++zi) {
@@ -1567,16 +1605,14 @@ static int batch_create(lise_ctx* const* ctxs, int n, lise_batch** out) {
       off[zi].pl_m[k] = place(ne * sizeof(PlanesArgs));
       off[zi].pl_y[k] = place(ne * sizeof(PlanesArgs));
       off[zi].pred[k] = place(ne * sizeof(PointwiseArgs));
+      for (int r = 0; r < 2; ++r) off[zi].red[k][r] = place(ne * sizeof(ReduceArgs));
     }
+    off[zi].red_block0 = place((ne + 1) * sizeof(long));
     z.n_items = 0;
     for (int e : z.evo) z.n_items += b->ctx[e]->n_groups;
     off[zi].items = place((size_t)z.n_items * sizeof(int2));
     off[zi].pl_block0 = place((ne + 1) * sizeof(long));
   }
-  size_t red_off[4][2];
-  for (int k = 0; k < 4; ++k)
-    for (int r = 0; r < 2; ++r) red_off[k][r] = place((size_t)n * sizeof(ReduceArgs));
-  const size_t red_block0_off = place((size_t)(n + 1) * sizeof(long));
   const size_t drive_off = place((size_t)8 * n * sizeof(double));
   if (rc == LISE_OK && cudaMalloc(&b->tables, img.size()) != cudaSuccess) {
     cudaGetLastError();
@@ -1623,7 +1659,7 @@ static int batch_create(lise_ctx* const* ctxs, int n, lise_batch** out) {
           ReduceArgs ra = a.red[r];
           if (c->p.drive_A != 0.0)
             ra.drive_ptr = reinterpret_cast<const double*>(dev + drive_off) + (size_t)(2 * k + r) * n + e;
-          reinterpret_cast<ReduceArgs*>(img.data() + red_off[k][r])[e] = ra;
+          reinterpret_cast<ReduceArgs*>(img.data() + off[zi].red[k][r])[j] = ra;
         }
       }
       z.corr[k] = reinterpret_cast<PencilArgs*>(dev + off[zi].corr[k]);
@@ -1631,18 +1667,17 @@ static int batch_create(lise_ctx* const* ctxs, int n, lise_batch** out) {
       z.pl_m[k] = reinterpret_cast<PlanesArgs*>(dev + off[zi].pl_m[k]);
       z.pl_y[k] = reinterpret_cast<PlanesArgs*>(dev + off[zi].pl_y[k]);
       z.pred[k] = reinterpret_cast<PointwiseArgs*>(dev + off[zi].pred[k]);
+      for (int r = 0; r < 2; ++r) z.red[k][r] = reinterpret_cast<ReduceArgs*>(dev + off[zi].red[k][r]);
     }
+    long* rb0 = reinterpret_cast<long*>(img.data() + off[zi].red_block0);
+    rb0[0] = 0;
+    for (size_t j = 0; j < z.evo.size(); ++j) rb0[j + 1] = rb0[j] + (b->ctx[z.evo[j]]->nxyz + 255) / 256;
+    z.red_blocks = rb0[z.evo.size()];
+    z.red_block0 = reinterpret_cast<long*>(dev + off[zi].red_block0);
     z.items = reinterpret_cast<int2*>(dev + off[zi].items);
     z.pl_block0 = reinterpret_cast<long*>(dev + off[zi].pl_block0);
   }
   if (rc == LISE_OK) {
-    long* rb0 = reinterpret_cast<long*>(img.data() + red_block0_off);
-    rb0[0] = 0;
-    for (int e = 0; e < n; ++e) rb0[e + 1] = rb0[e] + (b->ctx[e]->nxyz + 255) / 256;
-    b->red_blocks = rb0[n];
-    b->red_block0 = reinterpret_cast<long*>(dev + red_block0_off);
-    for (int k = 0; k < 4; ++k)
-      for (int r = 0; r < 2; ++r) b->red[k][r] = reinterpret_cast<ReduceArgs*>(dev + red_off[k][r]);
     b->drive_dev = reinterpret_cast<double*>(dev + drive_off);
     b->drive_host.assign((size_t)8 * n, 0.0);
     rc = cu(cudaMemcpyAsync(b->tables, img.data(), img.size(), cudaMemcpyHostToDevice, b->stream));
@@ -1679,8 +1714,7 @@ int lise_batch_step(lise_batch* b, int n_steps) {
       if (!g) {
         cudaGraph_t graph = nullptr;
         if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return LISE_ECUDA;
-        int rc = LISE_OK;
-        for (int j = 0; j < 4 && rc == LISE_OK; ++j) rc = batch_launch_step(b, (phase + j) % 4);
+        int rc = batch_launch_steps(b, phase, 4);
         const cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
         if (rc == LISE_OK && (e != cudaSuccess || !graph)) rc = LISE_ECUDA;
         if (rc == LISE_OK && cudaGraphInstantiate(&g, graph, 0) != cudaSuccess) rc = LISE_ECUDA;
@@ -1689,7 +1723,7 @@ int lise_batch_step(lise_batch* b, int n_steps) {
       }
       TRY(cu(cudaGraphLaunch(g, b->stream)));
     } else {
-      TRY(batch_launch_step(b, phase));
+      TRY(batch_launch_steps(b, phase, 1));
     }
     for (lise_ctx* c : b->ctx)
       for (int j = 0; j < m; ++j) rotate_history(c, c->t + c->dt);

@@ -405,17 +405,28 @@ __global__ void __launch_bounds__(256) k_planes_oz(PlanesArgs a) {
 //
 // Warp-specialised and persistent, one block per SM holding all 512 tensor-memory columns, so
 // that the digit split, the MMAs and the read-back of different planes overlap:
-//   producers (warps 8-11): load a plane (one plane ahead), find its exponent groups, write its
-//     digits into operand stage s = i % 2 (i: the block's plane counter) and arrive on full[s];
-//   issuer (warp 12, one thread): waits for full[s], issues the plane's 56 MMAs into the
-//     columns [256 s, 256 s + 224) and commits to mma_done[s];
-//   consumers (warps 0-7): wait for mma_done[s], read the levels back (warp w: lanes
-//     32 (w % 4) .., columns 16 (w / 4) ..), write the 64-bit sums into buffer acc[s], release
-//     the stage (tmem_free[s]), then form T_x + T_y of the plane and store it.
+//   consumers (the first kWsConsumerWarps warps): wait for mma_done[s], read the levels back
+//     (warp w: lanes 32 (w % 4) .., its share of the columns), write the 64-bit sums into buffer
+//     acc[s], release the stage (tmem_free[s]), then form T_x + T_y of the plane and store it;
+//   producers (the next kWsProducerWarps warps): load a plane (one plane ahead), find its
+//     exponent groups, write its digits into operand stage s = i % 2 (i: the block's plane
+//     counter) and arrive on full[s];
+//   issuer (the last warp, one thread): waits for full[s], issues the plane's 56 MMAs into the
+//     columns [256 s, 256 s + 224) and commits to mma_done[s].
 // A producer refills stage s (operand, scales) only after tmem_free[s].  Every wait is bounded
 // (and gives up early once another role has given up): the block then records bit 4 in the
 // error word, the issuer waits (bounded) for its last MMAs, and the tensor memory is freed.
-constexpr int kWsConsumerWarps = 8, kWsProducerWarps = 4;
+#ifndef LISE_WS_PRODUCER_WARPS
+#define LISE_WS_PRODUCER_WARPS 4
+#endif
+#ifndef LISE_WS_CONSUMER_WARPS
+#define LISE_WS_CONSUMER_WARPS 8
+#endif
+// (measured on 32^3 x 2048: 4 producer + 8 consumer warps 2.15 ms per launch, 8 + 4 2.50 ms)
+constexpr int kWsProducerWarps = LISE_WS_PRODUCER_WARPS;  // 4 or 8
+constexpr int kWsConsumerWarps = LISE_WS_CONSUMER_WARPS;  // 4 or 8 (whole lane quadrants)
+static_assert((kWsProducerWarps == 4 || kWsProducerWarps == 8) && (kWsConsumerWarps == 4 || kWsConsumerWarps == 8),
+              "role split");
 constexpr int kWsThreads = 32 * (kWsConsumerWarps + kWsProducerWarps + 1);
 template <int N>
 struct TcPlanes {
@@ -439,6 +450,7 @@ __device__ __forceinline__ int tc_off(int row, int k) {
 
 template <int N>
 __global__ void __launch_bounds__(kWsThreads, 1) k_planes_tc(PlanesArgs a) {
+  static_assert(kWsThreads <= 1024, "block size");
   using P = TcPlanes<N>;
   constexpr int S = oz::S, AP = P::AP;
   constexpr int NP = 32 * kWsProducerWarps, NC = 32 * kWsConsumerWarps;  // producer, consumer threads
@@ -483,22 +495,23 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_planes_tc(PlanesArgs a) {
   if (w >= kWsConsumerWarps && w < kWsConsumerWarps + kWsProducerWarps) {
     // ---------------------------------------------------------------- producers
     const int pt = tid - NC, pw = pt >> 5;
-    // two 2 x 2 blocks per thread: the blocks of virtual threads vt = pt + NP j (j = 0, 1) of a
+    // VB = 256 / NP 2 x 2 blocks per thread: the blocks of virtual threads vt = pt + NP j of a
     // 256-thread layout, an 8 x 8 tile per 16 lanes and two tiles per virtual warp (lane bits:
     // a = x pair, b = y pair, c = tile), so that the digit stores hit 32 distinct banks
-    int bx0[2], by0[2], blc[2];
+    constexpr int VB = 256 / NP;
+    int bx0[VB], by0[VB], blc[VB];
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
+    for (int j = 0; j < VB; ++j) {
       const int vt = pt + NP * j, vw = vt >> 5, vl = vt & 31;
       blc[j] = vl >> 4;
       bx0[j] = 8 * (2 * (vw & 1) + blc[j]) + 2 * (vl & 3);
       by0[j] = 8 * (vw >> 1) + 2 * ((vl >> 2) & 3);
     }
     const double2* src0 = a.xr ? reinterpret_cast<const double2*>(a.xr) : a.x;
-    double2 vn[2][2][2];  // [j][dy][dx], the next plane's values (loaded one plane ahead)
+    double2 vn[VB][2][2];  // [j][dy][dx], the next plane's values (loaded one plane ahead)
     auto load_plane = [&](long pl) {
 #pragma unroll
-      for (int j = 0; j < 2; ++j)
+      for (int j = 0; j < VB; ++j)
 #pragma unroll
         for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
@@ -509,10 +522,10 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_planes_tc(PlanesArgs a) {
     for (long i = 0; i < n_local; ++i) {
       const int s = (int)(i & 1);
       const uint32_t u = (uint32_t)(i >> 1);
-      double2 v[2][2][2];
+      double2 v[VB][2][2];
       unsigned e0 = 0, e1 = 0;
 #pragma unroll
-      for (int j = 0; j < 2; ++j)
+      for (int j = 0; j < VB; ++j)
 #pragma unroll
         for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
@@ -548,7 +561,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_planes_tc(PlanesArgs a) {
       // digits into both row blocks (the lanes of one store cover one core matrix's 32 words:
       // rows alternate with the tile bit so that the two tiles of a warp use different rows)
 #pragma unroll
-      for (int j = 0; j < 2; ++j)
+      for (int j = 0; j < VB; ++j)
 #pragma unroll
         for (int g = 0; g < 2; ++g) {
           unsigned short d[2][2][S];
@@ -608,8 +621,10 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_planes_tc(PlanesArgs a) {
     }
   } else if (w < kWsConsumerWarps) {
     // ---------------------------------------------------------------- consumers
-    const int q = w & 3, c0 = 16 * (w >> 2);
-    const int g = q & 1, ax = q >> 1;  // N = 32: lane quadrant q = 2 ax + g
+    // warp w reads lane quadrant q = w % 4 (N = 32: q = 2 ax + g) and CW columns from c0
+    constexpr int CW = N / (kWsConsumerWarps / 4);
+    const int q = w & 3, c0 = CW * (w >> 2);
+    const int g = q & 1, ax = q >> 1;
     for (long i = 0; i < n_local; ++i) {
       const int s = (int)(i & 1);
       const uint32_t par = (uint32_t)(i >> 1) & 1u;
@@ -625,7 +640,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_planes_tc(PlanesArgs a) {
       long long* acc = accbuf + (size_t)s * P::acc_elems;
       long long* dst = acc + (size_t)ax * 2 * N * AP;
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
+      for (int h = 0; h < CW / 8; ++h) {
         uint32_t r[S][8];
 #pragma unroll
         for (int L = 0; L < S; ++L) um::ld8(r[L], tmem + ((uint32_t)(32 * q) << 16) + 256u * s + L * N + c0 + 8 * h);

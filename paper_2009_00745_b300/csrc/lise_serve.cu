@@ -71,13 +71,15 @@ struct Request {
 
 }  // namespace
 
-// Requests stepped together (one per batchable precision).
+// Requests stepped together (one per batchable precision).  Up to two chunks of steps are
+// queued on the batch's stream, so that the device never waits for the stepper between
+// chunks; membership changes once the queue has drained.
 struct BatchGroup {
   int precision = 0;
   std::vector<Request*> members;
   lise_batch* batch = nullptr;
-  cudaEvent_t ev = nullptr;  // end of the last chunk
-  bool pending = false;
+  cudaEvent_t ev[2] = {nullptr, nullptr};  // end of each queued chunk (a ring)
+  int head = 0, queued = 0;                // next event slot, chunks not yet seen complete
 };
 
 struct lise_server {
@@ -188,7 +190,7 @@ void lise_server::run_stepper() {
         if (G.batch) lise_batch_destroy(G.batch);
         G.batch = nullptr;
         G.members.clear();
-        G.pending = false;
+        G.queued = 0;
       }
       std::lock_guard<std::mutex> lk(mu);
       for (Request* r : active) {
@@ -218,9 +220,11 @@ void lise_server::step_loop() {
       if (stop && queue.empty() && in_flight == 0) {
         for (auto& G : groups) {
           if (G.batch) lise_batch_destroy(G.batch);
-          if (G.ev) cudaEventDestroy(G.ev);
+          for (auto& e : G.ev) {
+            if (e) cudaEventDestroy(e);
+            e = nullptr;
+          }
           G.batch = nullptr;
-          G.ev = nullptr;
         }
         return;
       }
@@ -228,19 +232,20 @@ void lise_server::step_loop() {
       batching_now = batching;
     }
     bool progressed = false;
-    // batched requests: one chunk at a time per group; membership changes between chunks
+    // batched requests: up to two chunks queued per group; membership changes between chunks
     for (int gi = 0; gi < 2 && batching_now; ++gi) {
       BatchGroup& G = groups[gi];
       G.precision = gi == 0 ? LISE_MIXED : LISE_MIXED_STRICT;
-      if (G.pending) {
-        const cudaError_t q = cudaEventQuery(G.ev);
-        if (q == cudaErrorNotReady) continue;
-        G.pending = false;
+      while (G.queued > 0) {  // chunks that have finished, oldest first
+        const int tail = (G.head - G.queued + 2) % 2;
+        const cudaError_t q = cudaEventQuery(G.ev[tail]);
+        if (q == cudaErrorNotReady) break;
+        --G.queued;
         if (q != cudaSuccess)
           for (Request* r : G.members) r->status = LISE_ECUDA;
       }
-      // leaving: finished or failed members; joining: requests whose series start is done.
-      // (A fresh snapshot: a request retired above may already be gone.)
+      // leaving: finished (all steps enqueued) or failed members; joining: requests whose
+      // series start is done.  (A fresh snapshot: a request retired above may already be gone.)
       {
         std::lock_guard<std::mutex> lk(mu);
         act = active;
@@ -254,6 +259,7 @@ void lise_server::step_loop() {
           joined.push_back(r);
       const bool changed = keep.size() != G.members.size() || !joined.empty();
       if (changed || (!G.batch && !keep.empty())) {
+        if (G.queued > 0) continue;  // the queued chunks finish first
         if (G.batch) lise_batch_destroy(G.batch);
         G.batch = nullptr;
         for (Request* r : G.members)
@@ -273,20 +279,22 @@ void lise_server::step_loop() {
             for (Request* r : G.members) r->status = rc;
             continue;  // retired at the next turn
           }
-          if (!G.ev && cudaEventCreateWithFlags(&G.ev, cudaEventDisableTiming) != cudaSuccess) G.ev = nullptr;
+          for (auto& e : G.ev)
+            if (!e && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) e = nullptr;
         }
       }
-      if (!G.batch || G.members.empty()) continue;
+      if (!G.batch || G.members.empty() || G.queued >= 2 || !G.ev[G.head]) continue;
       int k = steps_per_turn;
       for (Request* r : G.members) k = std::min(k, r->n_steps - r->done_steps);
       int rc = lise_batch_step(G.batch, k);
-      if (rc == LISE_OK && (!G.ev || cudaEventRecord(G.ev, (cudaStream_t)lise_batch_stream(G.batch)) != cudaSuccess))
+      if (rc == LISE_OK && cudaEventRecord(G.ev[G.head], (cudaStream_t)lise_batch_stream(G.batch)) != cudaSuccess)
         rc = LISE_ECUDA;
       if (rc != LISE_OK) {
         for (Request* r : G.members) r->status = rc;
       } else {
         for (Request* r : G.members) r->done_steps += k;
-        G.pending = true;
+        G.head ^= 1;
+        ++G.queued;
       }
       progressed = true;
     }

@@ -103,6 +103,15 @@ typedef struct {
   int renormalize;          /* 1: at the end of every ABM step each state is scaled to unit norm,
                                a^3 sum_r (|u|^2 + |v|^2) = 1, before its y' is formed (the optional
                                renormalisation the paper describes after Eq. sp_en); 0: off */
+  double pair_ec;           /* > 0: the spherical momentum cutoff of Eq. geff at energy E_c = pair_ec,
+                               1/g_eff(r) = 1/g0(r) - meff k_c/(2 pi^2) (1 - (k_F/2k_c) ln[(k_c+k_F)/(k_c-k_F)])
+                               for k_F^2 >= 0 and (1 + (|k_F|/k_c) arctan(|k_F|/k_c)) for k_F^2 < 0, with
+                               meff = 1/alpha, k_F^2 = 2 meff (mu - U_loc), k_c^2 = 2 meff (E_c + mu - U_loc),
+                               U_loc(r) = U(n(r)) + V_ext(r, t); g_eff = g0 where k_c^2 <= 0.  U gains
+                               (d g_eff/dn) |nu|^2 (through g0 and U(n)).  Requires alpha > 0,
+                               pair_lattice = 0 and pair_ec <= alpha pi^2 / (2 dx^2) (the paper's bound:
+                               Eq. geff does not apply above the natural cutoff of one axis); else
+                               LISE_EINVAL.  0: off */
 } lise_params;
 
 /* Device bytes lise_create would allocate for these parameters (0 if invalid). */

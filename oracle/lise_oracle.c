@@ -18,6 +18,10 @@
  *     averaged densities n_cor = (n_pre + n(t))/2, nu_cor likewise, and
  *     V_ext(t + dt/2).
  *   - The Nyquist mode is kept in k^2 (zeroing applies to odd derivatives only).
+ *   - Eq. geff (spherical cutoff): m* = 1/alpha everywhere in it; U is the local
+ *     potential U(n) + V_ext without the pairing term; g_eff = g0 where
+ *     k_c^2 <= 0; E_pair = g_eff(n, r) |nu|^2, so d g_eff/dn includes the path
+ *     through U(n).
  */
 #include "lise_oracle.h"
 #include <math.h>
@@ -206,18 +210,57 @@ double or_vext(const or_params *p, int ix, int iy, int iz, double t) {
   return v;
 }
 
-void or_geff(const or_params *p, double n, double *geff, double *dgeff_dn) {
+/* Spherical-cutoff term of Eq. geff, c = m* k_c / (2 pi^2 hbar^2) (1 -/+ ...), and dc/dU, at a
+ * site whose local potential is U.  hbar = 1 and the dispersion of the Hamiltonian's kinetic
+ * term, alpha k^2 / 2, i.e. m* = 1/alpha in the prefactor and in the relations for E_c and mu.
+ * Where E_c + mu - U <= 0 no momenta lie below the cutoff and c = 0 (a reading). */
+static void geff_cutoff(const or_params *p, double U, double *c, double *dc_dU) {
+  const double m = 1.0 / p->alpha;
+  const double kc2 = 2.0 * m * (p->pair_ec + p->mu - U); /* E_c = k_c^2 / 2m* + U - mu */
+  const double kf2 = 2.0 * m * (p->mu - U);              /* mu = k_F^2 / 2m* + U */
+  *c = 0.0;
+  *dc_dU = 0.0;
+  if (!(kc2 > 0.0)) return;
+  const double kc = sqrt(kc2), pre = m * kc / (2.0 * OR_PI * OR_PI);
+  const double dkc = -m / kc; /* dk_c/dU */
+  if (kf2 > 0.0) {
+    /* first branch: 1 - (k_F / 2k_c) ln[(k_c + k_F)/(k_c - k_F)] */
+    const double kf = sqrt(kf2), dkf = -m / kf;
+    const double lg = log1p(2.0 * kf / (kc - kf));
+    *c = pre * (1.0 - kf / (2.0 * kc) * lg);
+    /* d/dU of m* / (2 pi^2) [k_c - (k_F/2) lg], d lg = (dk_c + dk_F)/(k_c + k_F) - (dk_c - dk_F)/(k_c - k_F) */
+    const double dlg = (dkc + dkf) / (kc + kf) - (dkc - dkf) / (kc - kf);
+    *dc_dU = m / (2.0 * OR_PI * OR_PI) * (dkc - 0.5 * dkf * lg - 0.5 * kf * dlg);
+  } else if (kf2 < 0.0) {
+    /* second branch: 1 + (|k_F| / k_c) arctan(|k_F| / k_c) */
+    const double q = sqrt(-kf2), dq = m / q; /* d|k_F|/dU */
+    *c = pre * (1.0 + q / kc * atan(q / kc));
+    /* d/dU of m* / (2 pi^2) [k_c + q arctan(q/k_c)] */
+    const double y = q / kc, dy = dq / kc - q * dkc / kc2;
+    *dc_dU = m / (2.0 * OR_PI * OR_PI) * (dkc + dq * atan(y) + q * dy / (1.0 + y * y));
+  } else {
+    /* k_F = 0: both branches give m* k_c / (2 pi^2); the derivative is their common limit */
+    *c = pre;
+    *dc_dU = m * m / (2.0 * OR_PI * OR_PI * kc);
+  }
+}
+
+void or_geff(const or_params *p, double n, double u_loc, double *geff, double *dgeff_dn) {
   double g0 = p->g, dg0 = 0.0;
   if (p->pair_alpha != 0.0) { /* Eq. g0 */
     g0 = p->g * (1.0 - p->pair_alpha * n / p->pair_n0);
     dg0 = -p->g * p->pair_alpha / p->pair_n0;
   }
-  double c = 0.0;
+  double c = 0.0, dc_dU = 0.0;
   if (p->pair_lattice) /* Eq. geff_3D with hbar = 1, m* = 1/alpha, dx = a */
     c = (1.0 / p->alpha) / (4.0 * OR_PI * OR_PI) * (OR_PI / p->a) * OR_GEFF_K;
+  else if (p->pair_ec > 0.0) /* Eq. geff */
+    geff_cutoff(p, u_loc, &c, &dc_dU);
   double den = 1.0 - c * g0;
   *geff = g0 / den;
-  *dgeff_dn = dg0 / (den * den);
+  /* dU/dn of U = beta (3 pi^2 n)^(2/3) / 2 (taken as 0 at n = 0, where nu vanishes too) */
+  double dU = n > 0.0 ? p->beta / 3.0 * pow(3.0 * OR_PI * OR_PI, 2.0 / 3.0) * pow(n, -1.0 / 3.0) : 0.0;
+  *dgeff_dn = dg0 / (den * den) + (*geff) * (*geff) * dc_dU * dU;
 }
 
 void or_potentials(const or_params *p, const double *n, const double complex *nu,
@@ -228,10 +271,11 @@ void or_potentials(const or_params *p, const double *n, const double complex *nu
       for (int x = 0; x < nx; ++x) {
         long r = ((long)z * ny + y) * nx + x;
         double U = 0.5 * p->beta * pow(3.0 * OR_PI * OR_PI * n[r], 2.0 / 3.0);
+        double vext = or_vext(p, x, y, z, t);
         double geff, dgeff;
-        or_geff(p, n[r], &geff, &dgeff);
+        or_geff(p, n[r], U + vext, &geff, &dgeff);
         double nu2 = creal(nu[r]) * creal(nu[r]) + cimag(nu[r]) * cimag(nu[r]);
-        W[r] = U + dgeff * nu2 - p->mu + or_vext(p, x, y, z, t);
+        W[r] = U + dgeff * nu2 - p->mu + vext;
         Delta[r] = -geff * nu[r];
       }
 }
@@ -622,10 +666,11 @@ void or_energy_of(const or_params *p, const double complex *psi, double t,
         long r = ((long)z * p->ny + y) * p->nx + x;
         double nr = n[r];
         /* Eq. pairing: E_pair = +g_eff |nu|^2 (with Delta = -g_eff nu, Eq. pairingfield) */
+        double vext = or_vext(p, x, y, z, t);
         double geff, dgeff;
-        or_geff(p, nr, &geff, &dgeff);
+        or_geff(p, nr, 0.5 * p->beta * pow(3.0 * OR_PI * OR_PI * nr, 2.0 / 3.0) + vext, &geff, &dgeff);
         double e = cint * pow(nr, 5.0 / 3.0) + geff * (creal(nu[r]) * creal(nu[r]) + cimag(nu[r]) * cimag(nu[r])) +
-                   or_vext(p, x, y, z, t) * nr;
+                   vext * nr;
         neumaier_add(&es, &ec, a3 * e);
         neumaier_add(&ns_, &nc, a3 * nr);
       }

@@ -51,15 +51,21 @@ typedef struct {
   int pair_lattice;        /* 1: Eq. geff_3D, 1/g_eff = 1/g0(r) - meff (pi/a) K / (4 pi^2 hbar^2), meff = 1/alpha */
   int renormalize;         /* 1: at the end of every ABM step each state is scaled to a^3 sum(|u|^2+|v|^2) = 1
                               (the renormalisation remark that follows Eq. sp_en), before its y' is formed */
+  double pair_ec;          /* > 0: Eq. geff, the spherical momentum cutoff at energy E_c (exclusive with
+                              pair_lattice; 0 < E_c <= pi^2 / (2 meff a^2)); 0 = off */
 } or_params;
 
 /* K of Eq. geff_3D (the value printed with it). */
 #define OR_GEFF_K 2.442749607806335
 
-/* Effective coupling and its density derivative at density n:
- * g_eff = g0 / (1 - c g0) (the same as 1/g_eff = 1/g0 - c), c = K / (4 pi a alpha)
- * with the lattice renormalisation, else 0; dgeff_dn = (dg0/dn) / (1 - c g0)^2. */
-void or_geff(const or_params *p, double n, double *geff, double *dgeff_dn);
+/* Effective coupling and its total density derivative at a site of density n whose local
+ * potential (U(n) + V_ext, without -mu and without the pairing term) is u_loc:
+ * g_eff = g0 / (1 - c g0) (the same as 1/g_eff = 1/g0 - c) with
+ *   c = K / (4 pi a alpha)                       (pair_lattice, Eq. geff_3D),
+ *   c = the spherical-cutoff term of Eq. geff    (pair_ec > 0; depends on u_loc),
+ *   c = 0                                        (neither);
+ * dgeff_dn = (dg0/dn) / (1 - c g0)^2 + g_eff^2 (dc/dU) (dU/dn), U(n) = beta (3 pi^2 n)^(2/3) / 2. */
+void or_geff(const or_params *p, double n, double u_loc, double *geff, double *dgeff_dn);
 
 /* 1D DFT of length n (any n >= 1), out-of-place, unnormalised.
  * sign = -1: sum_j x_j exp(-2 pi i j k / n); sign = +1: exp(+...). */

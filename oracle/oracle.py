@@ -62,7 +62,7 @@ def lib():
         L.or_abm_corrector.argtypes = [C.c_long, d, vp, vp, vp, vp, vp, vp, vp]
         L.or_abm_final.argtypes = [C.c_long, vp, vp, vp, vp]
         L.or_eta.argtypes = [vp, vp, vp, vp]
-        L.or_geff.argtypes = [vp, d, P(d), P(d)]
+        L.or_geff.argtypes = [vp, d, d, P(d), P(d)]
         _lib = L
     return _lib
 
@@ -73,7 +73,7 @@ class _Params(C.Structure):
                 ("mu", C.c_double), ("g", C.c_double), ("v_static", C.c_void_p),
                 ("drive_A", C.c_double), ("drive_Omega", C.c_double), ("remove_phase", C.c_int),
                 ("pair_alpha", C.c_double), ("pair_n0", C.c_double), ("pair_lattice", C.c_int),
-                ("renormalize", C.c_int)]
+                ("renormalize", C.c_int), ("pair_ec", C.c_double)]
 
 
 class Params:
@@ -81,7 +81,7 @@ class Params:
 
     def __init__(self, nx, ny, nz, a=1.0, n_qp=1, alpha=1.0, beta=0.0, mu=0.0, g=0.0,
                  v_static=None, drive_A=0.0, drive_Omega=0.0, remove_phase=False, pair_alpha=0.0,
-                 pair_n0=1.0, pair_lattice=False, renormalize=False):
+                 pair_n0=1.0, pair_lattice=False, renormalize=False, pair_ec=0.0):
         self.nx, self.ny, self.nz, self.a, self.n_qp = int(nx), int(ny), int(nz), float(a), int(n_qp)
         self.alpha, self.beta, self.mu, self.g = float(alpha), float(beta), float(mu), float(g)
         self.v_static = None if v_static is None else np.ascontiguousarray(v_static, dtype=np.float64).reshape(nz, ny, nx)
@@ -89,13 +89,14 @@ class Params:
         self.remove_phase = bool(remove_phase)
         self.pair_alpha, self.pair_n0, self.pair_lattice = float(pair_alpha), float(pair_n0), bool(pair_lattice)
         self.renormalize = bool(renormalize)
+        self.pair_ec = float(pair_ec)
 
     def with_(self, **kw):
         d = dict(nx=self.nx, ny=self.ny, nz=self.nz, a=self.a, n_qp=self.n_qp, alpha=self.alpha,
                  beta=self.beta, mu=self.mu, g=self.g, v_static=self.v_static,
                  drive_A=self.drive_A, drive_Omega=self.drive_Omega, remove_phase=self.remove_phase,
                  pair_alpha=self.pair_alpha, pair_n0=self.pair_n0, pair_lattice=self.pair_lattice,
-                 renormalize=self.renormalize)
+                 renormalize=self.renormalize, pair_ec=self.pair_ec)
         d.update(kw)
         return Params(**d)
 
@@ -103,7 +104,7 @@ class Params:
         s = _Params(self.nx, self.ny, self.nz, self.a, self.n_qp, self.alpha, self.beta, self.mu,
                     self.g, None if self.v_static is None else self.v_static.ctypes.data,
                     self.drive_A, self.drive_Omega, int(self.remove_phase), self.pair_alpha,
-                    self.pair_n0, int(self.pair_lattice), int(self.renormalize))
+                    self.pair_n0, int(self.pair_lattice), int(self.renormalize), self.pair_ec)
         return s
 
     @property
@@ -230,11 +231,11 @@ def kick(p: Params, psi, chi):
     return out
 
 
-def geff(p: Params, n):
-    """(g_eff, d g_eff / dn) at density n."""
+def geff(p: Params, n, u_loc=0.0):
+    """(g_eff, d g_eff / dn) at density n and local potential u_loc = U(n) + V_ext."""
     g, dg = C.c_double(), C.c_double()
     ps = p._c()
-    lib().or_geff(C.byref(ps), float(n), C.byref(g), C.byref(dg))
+    lib().or_geff(C.byref(ps), float(n), float(u_loc), C.byref(g), C.byref(dg))
     return g.value, dg.value
 
 

@@ -47,7 +47,27 @@ int check_params(const lise_params* p) {
   if (p->pair_lattice && !(p->alpha > 0.0)) return LISE_EINVAL;
   if (p->pair_alpha != 0.0 && !(std::isfinite(p->pair_alpha) && p->pair_n0 > 0.0 && std::isfinite(p->pair_n0)))
     return LISE_EINVAL;
+  // Eq. geff: E_c > 0, at most the one-axis natural cutoff pi^2 / (2 m* a^2) of the lattice, and
+  // not together with the lattice form of Eq. geff_3D
+  if (!(p->pair_ec >= 0.0) || !std::isfinite(p->pair_ec)) return LISE_EINVAL;
+  if (p->pair_ec > 0.0) {
+    const double PI = 3.14159265358979323846;
+    if (p->pair_lattice || !(p->alpha > 0.0) || p->pair_ec > p->alpha * PI * PI / (2.0 * p->dx * p->dx))
+      return LISE_EINVAL;
+  }
   return LISE_OK;
+}
+
+Pairing make_pairing(const lise_params* p) {
+  Pairing r;
+  r.g = p->g;
+  r.alpha_n0 = p->pair_alpha != 0.0 ? p->pair_alpha / p->pair_n0 : 0.0;
+  r.c = p->pair_lattice ? pairing_lattice_c(p->dx, p->alpha) : 0.0;
+  r.ec = p->pair_ec;
+  r.m = p->pair_ec > 0.0 ? 1.0 / p->alpha : 0.0;
+  r.mu = p->mu;
+  r.beta = p->beta;
+  return r;
 }
 
 }  // namespace lise
@@ -299,9 +319,7 @@ ReduceArgs reduce_args(const lise_ctx* c, int dslot, const double* avg_n, const 
   r.drive_ptr = nullptr;
   r.beta = c->p.beta;
   r.mu = c->p.mu;
-  r.g = c->p.g;
-  r.pair_alpha_n0 = c->p.pair_alpha != 0.0 ? c->p.pair_alpha / c->p.pair_n0 : 0.0;
-  r.pair_c = c->p.pair_lattice ? pairing_lattice_c(c->p.dx, c->p.alpha) : 0.0;
+  r.pair = make_pairing(&c->p);
   r.err = c->err;
   return r;
 }
@@ -1114,10 +1132,8 @@ int lise_energy(lise_ctx* c, double* E, double* Nout) {
   a.dens = 1;
   TRY(run_pencils(c, M_ENERGY, a));
   TRY(exchange_parts(c));  // the other shards' kinetic partials
-  TRY(launch_energy_sites(c->parts, c->n_groups_all, c->dn[0], c->dnu[0], c->v_static, drive_at(c, c->t), c->p.beta,
-                          c->p.g, c->p.pair_alpha != 0.0 ? c->p.pair_alpha / c->p.pair_n0 : 0.0,
-                          c->p.pair_lattice ? pairing_lattice_c(c->p.dx, c->p.alpha) : 0.0, c->N, c->p.dx,
-                          c->e_site, c->stream)
+  TRY(launch_energy_sites(c->parts, c->n_groups_all, c->dn[0], c->dnu[0], c->v_static, drive_at(c, c->t),
+                          make_pairing(&c->p), c->N, c->p.dx, c->e_site, c->stream)
           ? LISE_ECUDA
           : LISE_OK);
   TRY(cu(cudaMemcpyAsync(c->host_e, c->e_site, 2 * c->nxyz * sizeof(double), cudaMemcpyDeviceToHost, c->stream)));

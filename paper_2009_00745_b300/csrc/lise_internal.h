@@ -15,6 +15,9 @@ namespace lise {
 // (lattice, spacing, state count, precision, finiteness of every physical parameter, the
 // pairing options).
 int check_params(const lise_params* p);
+// The pairing coupling's kernel arguments (lise_kernels.cuh) for valid parameters.
+struct Pairing;
+Pairing make_pairing(const lise_params* p);
 }  // namespace lise
 
 // The stream a batch (lise_batch_*) enqueues its work on.

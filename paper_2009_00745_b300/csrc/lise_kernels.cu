@@ -1185,9 +1185,10 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs& a, const long s) {
   const int iz = (int)(s / ((long)a.N * a.N));
   double v = a.v_static ? a.v_static[s] : 0.0;
   v += (a.drive_ptr ? *a.drive_ptr : a.drive) * ((iz - a.N / 2) * a.a);
+  const double U = 0.5 * a.beta * cb * cb;
   double geff, dgeff;
-  pairing_geff(a.g, a.pair_alpha_n0, a.pair_c, n, &geff, &dgeff);
-  a.W[s] = 0.5 * a.beta * cb * cb + dgeff * (r * r + i * i) - a.mu + v;  // U(n) + dE_pair/dn - mu + V_ext
+  pairing_geff(a.pair, n, cb * cb, U + v, &geff, &dgeff);
+  a.W[s] = U + dgeff * (r * r + i * i) - a.mu + v;  // U(n) + dE_pair/dn - mu + V_ext
   a.D[s] = make_double2(-geff * r, -geff * i);                            // Delta = -g_eff nu
 }
 
@@ -1331,8 +1332,7 @@ __global__ void k_density(PointwiseArgs a) {
 // E = a^3 sum_r [(alpha/2) tau + (3/10) beta (3 pi^2)^(2/3) n^(5/3) + g |nu|^2 + V n]
 // (Eq. pairing has + g_eff |kappa|^2); part holds sum_k 2 Re(v_k^* T v_k).
 __global__ void k_energy_sites(const double* part, int n_groups, const double* nd, const double2* nu,
-                               const double* v_static, double drive, double beta, double g, double pair_alpha_n0,
-                               double pair_c, int N, double a, double* out) {
+                               const double* v_static, double drive, Pairing pair, int N, double a, double* out) {
   const long nxyz = (long)N * N * N;
   const long s = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= nxyz) return;
@@ -1348,9 +1348,10 @@ __global__ void k_energy_sites(const double* part, int n_groups, const double* n
   v += drive * ((iz - N / 2) * a);
   const double2 w = nu[s];
   const double a3 = a * a * a;
+  const double cb2 = cb * cb * cn * cn;  // (3 pi^2 n)^(2/3)
   double geff, dgeff;
-  pairing_geff(g, pair_alpha_n0, pair_c, n, &geff, &dgeff);
-  out[s] = a3 * (ek + 0.3 * beta * cb * cb * n * cn * cn + geff * (w.x * w.x + w.y * w.y) + v * n);
+  pairing_geff(pair, n, cb2, 0.5 * pair.beta * cb2 + v, &geff, &dgeff);
+  out[s] = a3 * (ek + 0.3 * pair.beta * cb * cb * n * cn * cn + geff * (w.x * w.x + w.y * w.y) + v * n);
   out[nxyz + s] = a3 * n;
 }
 
@@ -2061,12 +2062,12 @@ double pairing_lattice_c(double a, double alpha) {
 }
 
 int launch_energy_sites(const double* part_ekin, int n_groups, const double* n, const double2* nu,
-                        const double* v_static, double drive, double beta, double g, double pair_alpha_n0,
-                        double pair_c, int N, double a, double* e_site, cudaStream_t s) {
+                        const double* v_static, double drive, const Pairing& pair, int N, double a,
+                        double* e_site, cudaStream_t s) {
   const int nt = 256;
   const long nxyz = (long)N * N * N;
-  k_energy_sites<<<(unsigned)((nxyz + nt - 1) / nt), nt, 0, s>>>(part_ekin, n_groups, n, nu, v_static, drive, beta, g,
-                                                                  pair_alpha_n0, pair_c, N, a, e_site);
+  k_energy_sites<<<(unsigned)((nxyz + nt - 1) / nt), nt, 0, s>>>(part_ekin, n_groups, n, nu, v_static, drive, pair,
+                                                                  N, a, e_site);
   return cudaGetLastError() == cudaSuccess ? 0 : 3;
 }
 

@@ -100,6 +100,17 @@ struct PlanesArgs {
   long wait_polls;        // as in PencilArgs
 };
 
+// Pairing coupling of Eqs. g0, geff_3D and geff (hbar = 1), built once from the parameters.
+struct Pairing {
+  double g;         // bare coupling: Delta = -g_eff nu
+  double alpha_n0;  // Eq. g0: g0 = g (1 - alpha_n0 n), alpha_n0 = pair_alpha / pair_n0
+  double c;         // Eq. geff_3D: 1/g_eff = 1/g0 - c; 0 without the lattice form
+  double ec;        // Eq. geff: spherical momentum cutoff at energy E_c > 0; 0 = off
+  double m;         // m* = 1/alpha (dispersion alpha k^2 / 2), for Eq. geff
+  double mu;        // chemical potential, for Eq. geff
+  double beta;      // U(n) = beta (3 pi^2 n)^(2/3) / 2, whose n-dependence enters d g_eff / dn
+};
+
 struct ReduceArgs {
   const double* part_n;
   const double* part_nr;
@@ -117,9 +128,8 @@ struct ReduceArgs {
   const double* v_static; // may be null
   double drive;           // A sin(Omega t)
   const double* drive_ptr;  // if non-null, the drive amplitude is read from here (graph replays)
-  double beta, mu, g;
-  double pair_alpha_n0;   // Eq. g0: g0 = g (1 - pair_alpha_n0 * n), pair_alpha_n0 = alpha_p / n0
-  double pair_c;          // Eq. geff_3D: g_eff = g0 / (1 - pair_c g0); 0 without renormalisation
+  double beta, mu;
+  Pairing pair;
   int* err;               // set bit 0 if a density is not finite
 };
 
@@ -140,13 +150,42 @@ struct ReduceBatch {
   int n;
 };
 
-// Effective pairing coupling and its density derivative (Eqs. g0, geff_3D).
-__host__ __device__ inline void pairing_geff(double g, double alpha_n0, double c, double n, double* geff,
+// Effective pairing coupling g_eff and its total density derivative at a site of density n,
+// cb2 = (3 pi^2 n)^(2/3), local potential u_loc = U(n) + V_ext (Eqs. g0, geff_3D, geff):
+// 1/g_eff = 1/g0 - c.  The spherical-cutoff term of Eq. geff, with s = k_F^2 = 2 m* (mu - u_loc)
+// and k_c^2 = s + 2 m* E_c, is the single analytic function
+//   c = m* k_c / (2 pi^2) (1 - z A(z)),  z = s / k_c^2 < 1,
+//   A(z) = artanh(sqrt z) / sqrt z (z > 0),  arctan(sqrt -z) / sqrt -z (z < 0),  1 (z = 0),
+// which is the equation's logarithmic form for k_F^2 > 0 and its arctan form for k_F^2 < 0; its
+// derivative is dc/du_loc = m*^2 A(z) / (2 pi^2 k_c).  c = 0 where k_c^2 <= 0 (no momenta below
+// the cutoff).  d g_eff/dn = (dg0/dn) / (1 - c g0)^2 + g_eff^2 (dc/du_loc) dU/dn,
+// dU/dn = beta cb2 / (3 n) (0 at n = 0).
+__host__ __device__ inline void pairing_geff(const Pairing& P, double n, double cb2, double u_loc, double* geff,
                                              double* dgeff) {
-  const double g0 = g * (1.0 - alpha_n0 * n);
+  const double g0 = P.g * (1.0 - P.alpha_n0 * n);
+  double c = P.c, dc = 0.0;
+  if (P.ec > 0.0) {
+    const double s = 2.0 * P.m * (P.mu - u_loc), kc2 = s + 2.0 * P.m * P.ec;
+    c = 0.0;
+    if (kc2 > 0.0) {
+      const double kc = sqrt(kc2), z = s / kc2;
+      double A = 1.0;
+      if (z > 0.0) {
+        const double r = sqrt(z);
+        A = atanh(r) / r;
+      } else if (z < 0.0) {
+        const double r = sqrt(-z);
+        A = atan(r) / r;
+      }
+      const double k2pi2 = 1.0 / (2.0 * 3.14159265358979323846 * 3.14159265358979323846);
+      c = P.m * kc * k2pi2 * (1.0 - z * A);
+      dc = P.m * P.m * A * k2pi2 / kc;
+    }
+  }
   const double den = 1.0 - c * g0;
-  *geff = g0 / den;
-  *dgeff = (-g * alpha_n0) / (den * den);
+  const double ge = g0 / den;
+  *geff = ge;
+  *dgeff = (-P.g * P.alpha_n0) / (den * den) + (n > 0.0 ? ge * ge * dc * (P.beta * cb2 / (3.0 * n)) : 0.0);
 }
 
 struct PointwiseArgs {
@@ -218,8 +257,8 @@ bool pencils_batch_maps(int N, int mode, int strict, int qb, PencilArgs* a);
 int launch_predict(const PointwiseArgs& a, cudaStream_t s);
 int launch_density(const PointwiseArgs& a, cudaStream_t s);
 int launch_energy_sites(const double* part_ekin, int n_groups, const double* n, const double2* nu,
-                        const double* v_static, double drive, double beta, double g, double pair_alpha_n0,
-                        double pair_c, int N, double a, double* e_site, cudaStream_t s);
+                        const double* v_static, double drive, const Pairing& pair, int N, double a,
+                        double* e_site, cudaStream_t s);
 // pair_c of Eq. geff_3D for lattice constant a and kinetic coefficient alpha (meff = 1/alpha).
 double pairing_lattice_c(double a, double alpha);
 int launch_finite_check(const double2* x, long count, int* err, cudaStream_t s);

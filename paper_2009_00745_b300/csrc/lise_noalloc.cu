@@ -147,9 +147,7 @@ extern "C" int lise_rhs_noalloc(const lise_params* p, const double* psi_dev, dou
   r.drive = p->drive_A == 0.0 ? 0.0 : p->drive_A * std::sin(p->drive_Omega * t);
   r.beta = p->beta;
   r.mu = p->mu;
-  r.g = p->g;
-  r.pair_alpha_n0 = p->pair_alpha != 0.0 ? p->pair_alpha / p->pair_n0 : 0.0;
-  r.pair_c = p->pair_lattice ? pairing_lattice_c(p->dx, p->alpha) : 0.0;
+  r.pair = make_pairing(p);
   r.err = err;
   if (launch_reduce(r, s)) return LISE_ECUDA;
 

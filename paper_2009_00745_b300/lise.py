@@ -38,7 +38,7 @@ class _Params(C.Structure):
                 ("drive_A", C.c_double), ("drive_Omega", C.c_double), ("precision", C.c_int),
                 ("device", C.c_int), ("hbm_budget_bytes", C.c_size_t), ("stream", C.c_void_p),
                 ("remove_phase", C.c_int), ("pair_alpha", C.c_double), ("pair_n0", C.c_double),
-                ("pair_lattice", C.c_int), ("renormalize", C.c_int)]
+                ("pair_lattice", C.c_int), ("renormalize", C.c_int), ("pair_ec", C.c_double)]
 
 
 # lise_exchange_fn and lise_shard (sharded densities)
@@ -129,7 +129,7 @@ def _check(rc, where):
 
 def _params(N, n_qp, a, alpha, beta, mu, g, v_static, drive_A, drive_Omega, precision, device,
             hbm_budget_bytes, stream, remove_phase=False, pair_alpha=0.0, pair_n0=1.0, pair_lattice=False,
-            renormalize=False):
+            renormalize=False, pair_ec=0.0):
     prec = PRECISIONS.get(precision, precision)
     vs = None
     if v_static is not None:
@@ -139,7 +139,8 @@ def _params(N, n_qp, a, alpha, beta, mu, g, v_static, drive_A, drive_Omega, prec
     p = _Params(N, N, N, float(a), int(n_qp), float(alpha), float(beta), float(mu), float(g),
                 None if vs is None else vs.ctypes.data, float(drive_A), float(drive_Omega),
                 int(prec), int(device), int(hbm_budget_bytes), stream, int(bool(remove_phase)),
-                float(pair_alpha), float(pair_n0), int(bool(pair_lattice)), int(bool(renormalize)))
+                float(pair_alpha), float(pair_n0), int(bool(pair_lattice)), int(bool(renormalize)),
+                float(pair_ec))
     return p, vs
 
 
@@ -202,11 +203,11 @@ class Context:
     def __init__(self, N, n_qp, *, a=1.0, alpha=1.0, beta=0.0, mu=0.0, g=0.0, v_static=None,
                  drive_A=0.0, drive_Omega=0.0, precision="fp64", device=0, hbm_budget_bytes=0,
                  stream=None, remove_phase=False, pair_alpha=0.0, pair_n0=1.0, pair_lattice=False,
-                 renormalize=False):
+                 renormalize=False, pair_ec=0.0):
         self.N, self.n_qp = int(N), int(n_qp)
         self._p, self._vs = _params(N, n_qp, a, alpha, beta, mu, g, v_static, drive_A, drive_Omega,
                                     precision, device, hbm_budget_bytes, stream, remove_phase, pair_alpha,
-                                    pair_n0, pair_lattice, renormalize)
+                                    pair_n0, pair_lattice, renormalize, pair_ec)
         h = C.c_void_p()
         _check(load().lise_create(C.byref(self._p), C.byref(h)), "lise_create")
         self._h = h

@@ -4,6 +4,7 @@ import ctypes as C
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_2009_00745_b300 import build as B
@@ -104,6 +105,22 @@ def test_noalloc_validates_parameters_before_any_device_call(lib, field):
     p.alpha = p.beta = p.mu = p.g = p.drive_A = p.drive_Omega = 0.0
     p.pair_alpha, p.pair_n0 = 0.5, 0.0   # Eq. g0 needs n0 > 0
     assert lib.lise_rhs_noalloc(C.byref(p), fake, 0.0, fake) == L.EINVAL
+
+
+@pytest.mark.parametrize("ec,lattice,alpha,ok", [
+    (0.0, 0, 1.0, True), (2.0, 0, 1.0, True), (np.pi ** 2 / 2, 0, 1.0, True),
+    (np.pi ** 2 / 2 * 1.0001, 0, 1.0, False),   # above the natural cutoff of one axis
+    (2.0, 1, 1.0, False),                       # not with the lattice form of Eq. geff_3D
+    (-0.1, 0, 1.0, False), (float("nan"), 0, 1.0, False), (float("inf"), 0, 1.0, False),
+    (1.0, 0, 0.0, False)])
+def test_spherical_cutoff_parameters(lib, ec, lattice, alpha, ok):
+    # Eq. geff: 0 < E_c <= alpha pi^2 / (2 dx^2); lise_footprint_bytes is 0 for invalid parameters
+    p, _ = L._params(16, 4, 1.0, alpha, -0.5, 0.2, -0.7, None, 0.0, 0.0, "fp64", 0, 0, None,
+                     pair_lattice=bool(lattice), pair_ec=ec)
+    assert (lib.lise_footprint_bytes(C.byref(p)) > 0) == ok
+    if not ok:
+        fake = C.c_void_p(4096)
+        assert lib.lise_rhs_noalloc(C.byref(p), fake, 0.0, fake) == L.EINVAL
 
 
 def test_pencil_batch_controls_host_only():

@@ -427,6 +427,53 @@ def test_run_density_dependent_renormalised_pairing():
     assert E == pytest.approx(Eo, rel=1e-11)
 
 
+# ------------------------------------- pairing coupling (Eq. geff, spherical cutoff) ----
+
+def _u_loc(p, psi):
+    nn, _ = O.densities(p, psi)
+    u = 0.5 * p.beta * (3 * np.pi ** 2 * nn) ** (2.0 / 3.0)
+    return u + (p.v_static if p.v_static is not None else 0.0)
+
+
+def test_rhs_spherical_cutoff_pairing():
+    # sites on both branches of Eq. geff (k_F^2 of either sign), a density-dependent g0
+    N, n_qp = 16, 6
+    psi = random_state(N, n_qp, seed=43, kmax=5)
+    vs = np.random.default_rng(3).uniform(-1, 1, (N, N, N))
+    kw = dict(alpha=1.1, beta=-0.5, mu=0.25, g=-1.2, pair_alpha=0.5, pair_n0=0.02, pair_ec=2.0)
+    p = O.Params(N, N, N, n_qp=n_qp, v_static=vs, drive_A=0.02, drive_Omega=0.3, **kw)
+    u = _u_loc(p, psi)
+    assert (u < p.mu).sum() > 100 and (u > p.mu).sum() > 100
+    with L.Context(N, n_qp, v_static=vs, drive_A=0.02, drive_Omega=0.3, **kw) as ctx:
+        got = ctx.rhs(psi, 0.7)
+    ref = O.rhs(p, psi, 0.7)
+    assert rel(got, ref) < TOL_FP64_RHS
+    assert maxabs_rel(got, ref) < TOL_FP64_ELEM
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL_FP64_RUN), ("mixed", 5e-6)])
+def test_run_spherical_cutoff_pairing(precision, tol):
+    # the driven workload in a trap: k_F^2 > 0, k_F^2 < 0 and empty-sphere (k_c^2 < 0) sites,
+    # with the drive moving U_loc in time (graph replays read the drive from device memory)
+    w = W.driven(12, 10, A=0.05, Omega=0.3, noise_eps=0.2, g=-0.9, steps=6)
+    w.v_static = W.harmonic_trap(12, 0.15)
+    kw = dict(pair_alpha=0.4, pair_n0=0.01, pair_ec=0.5)
+    p = oracle_params(w, **kw)
+    u = _u_loc(p, w.initial_state())
+    assert (u < p.mu).sum() > 100 and (u > p.mu + 0.5).sum() > 100
+    with L.Context.from_workload(w, precision=precision, **kw) as ctx:
+        ctx.set_state(w.initial_state(), 0.0, w.dt)
+        ctx.step(w.steps)
+        got = ctx.state()
+        E, _ = ctx.energy()
+    s = O.Solver(p)
+    s.set_state(w.initial_state(), 0.0, w.dt)
+    s.step(w.steps)
+    assert rel(got, s.state()) < tol
+    Eo, _ = s.energy()
+    assert E == pytest.approx(Eo, rel=1e-11 if precision == "fp64" else 1e-6)
+
+
 # ------------------------------------------------------------ CUDA graphs ----
 
 @pytest.mark.parametrize("workload", ["ufg", "drive"])

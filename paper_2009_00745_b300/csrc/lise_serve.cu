@@ -20,11 +20,13 @@
 // every request runs the same deterministic kernels on its own buffers, so its
 // result does not depend on what else is in flight.
 // With batching on (lise_server_set_batching), the stepper steps the active requests of
-// each FP32 compute precision together through one lise_batch (shared launches over a
-// device work table), rebuilt whenever a request joins (its series start has finished
-// on the device) or leaves (its steps are done); the others are stepped one by one.
-// A batch's members advance by the same number of steps per turn, so every chunk is
-// bounded by the member with the fewest steps left.
+// each FP32 compute precision and lattice size together through one lise_batch (shared
+// launches over a device work table), rebuilt whenever a request joins (its series start
+// has finished on the device) or leaves (its steps are done); the others are stepped one
+// by one.  Groups of different lattice sizes advance independently (their own streams and
+// chunk queues), so that a rebuild of one group does not hold up the others.  A batch's
+// members advance by the same number of steps per turn, so every chunk is bounded by the
+// member with the fewest steps left.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -71,11 +73,11 @@ struct Request {
 
 }  // namespace
 
-// Requests stepped together (one per batchable precision).  Up to two chunks of steps are
-// queued on the batch's stream, so that the device never waits for the stepper between
-// chunks; membership changes once the queue has drained.
+// Requests stepped together (one group per batchable precision and lattice size).  Up to two
+// chunks of steps are queued on the batch's stream, so that the device never waits for the
+// stepper between chunks; membership changes once the queue has drained.
 struct BatchGroup {
-  int precision = 0;
+  int precision = 0, N = 0;
   std::vector<Request*> members;
   lise_batch* batch = nullptr;
   cudaEvent_t ev[2] = {nullptr, nullptr};  // end of each queued chunk (a ring)
@@ -85,7 +87,7 @@ struct BatchGroup {
 struct lise_server {
   int device = 0;
   bool batching = false;
-  BatchGroup groups[2];  // LISE_MIXED, LISE_MIXED_STRICT
+  std::vector<BatchGroup> groups;  // by (precision, lattice size), created on first use
   size_t budget = 0;
   int max_active = 1;
   int steps_per_turn = 1;
@@ -232,10 +234,19 @@ void lise_server::step_loop() {
       batching_now = batching;
     }
     bool progressed = false;
+    // a group for every (precision, lattice size) of a batchable active request
+    if (batching_now)
+      for (Request* r : act)
+        if (batchable(r) &&
+            std::none_of(groups.begin(), groups.end(),
+                         [&](const BatchGroup& G) { return G.precision == r->p.precision && G.N == r->p.nx; })) {
+          groups.emplace_back();
+          groups.back().precision = r->p.precision;
+          groups.back().N = r->p.nx;
+        }
     // batched requests: up to two chunks queued per group; membership changes between chunks
-    for (int gi = 0; gi < 2 && batching_now; ++gi) {
+    for (size_t gi = 0; gi < groups.size() && batching_now; ++gi) {
       BatchGroup& G = groups[gi];
-      G.precision = gi == 0 ? LISE_MIXED : LISE_MIXED_STRICT;
       while (G.queued > 0) {  // chunks that have finished, oldest first
         const int tail = (G.head - G.queued + 2) % 2;
         const cudaError_t q = cudaEventQuery(G.ev[tail]);
@@ -254,7 +265,7 @@ void lise_server::step_loop() {
       for (Request* r : G.members)
         if (r->status == LISE_OK && r->done_steps < r->n_steps) keep.push_back(r);
       for (Request* r : act)
-        if (!r->batched && batchable(r) && r->p.precision == G.precision && r->status == LISE_OK &&
+        if (!r->batched && batchable(r) && r->p.precision == G.precision && r->p.nx == G.N && r->status == LISE_OK &&
             r->done_steps < r->n_steps && !r->ev_pending && cudaEventQuery(r->ready_ev) == cudaSuccess)
           joined.push_back(r);
       const bool changed = keep.size() != G.members.size() || !joined.empty();

@@ -330,9 +330,8 @@ class Context:
         exchange(parts, on_device, stream, nxyz, first_group, n_local, n_groups_all) fills the
         other shards' groups of the partial-sum block at address `parts` (see shard.py); an
         exception in it fails the library call with EEXCHANGE.  Call before set_state."""
-        n_local = -(-self.n_qp // int(group_size))
-        if n_groups_all is None:
-            n_groups_all = first_group + n_local
+        if n_groups_all is None:  # (a group size < 1 is left to the library to reject)
+            n_groups_all = first_group + (-(-self.n_qp // int(group_size)) if int(group_size) > 0 else 0)
         if exchange is None:
             cb = EXCHANGE_FN()
         else:

@@ -417,15 +417,17 @@ __global__ void __launch_bounds__(256) k_planes_oz(PlanesArgs a) {
 // (and gives up early once another role has given up): the block then records bit 4 in the
 // error word, the issuer waits (bounded) for its last MMAs, and the tensor memory is freed.
 #ifndef LISE_WS_PRODUCER_WARPS
-#define LISE_WS_PRODUCER_WARPS 4
+#define LISE_WS_PRODUCER_WARPS 8
 #endif
 #ifndef LISE_WS_CONSUMER_WARPS
 #define LISE_WS_CONSUMER_WARPS 8
 #endif
-// (measured on 32^3 x 2048: 4 producer + 8 consumer warps 2.15 ms per launch, 8 + 4 2.50 ms)
+// (measured on 32^3 x 2048, ms per launch: 8 producer + 8 consumer warps 2.02, 4 + 8 2.14, 8 + 4 2.50,
+// 8 + 16 2.53)
 constexpr int kWsProducerWarps = LISE_WS_PRODUCER_WARPS;  // 4 or 8
-constexpr int kWsConsumerWarps = LISE_WS_CONSUMER_WARPS;  // 4 or 8 (whole lane quadrants)
-static_assert((kWsProducerWarps == 4 || kWsProducerWarps == 8) && (kWsConsumerWarps == 4 || kWsConsumerWarps == 8),
+constexpr int kWsConsumerWarps = LISE_WS_CONSUMER_WARPS;  // 4, 8 or 16 (whole lane quadrants)
+static_assert((kWsProducerWarps == 4 || kWsProducerWarps == 8) &&
+                  (kWsConsumerWarps == 4 || kWsConsumerWarps == 8 || kWsConsumerWarps == 16),
               "role split");
 constexpr int kWsThreads = 32 * (kWsConsumerWarps + kWsProducerWarps + 1);
 template <int N>

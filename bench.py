@@ -539,10 +539,12 @@ def measure(L, w, psi_dev, args, local, stream, drift_steps=0, drift_every=25, c
     ctx.profile(True)
     import torch
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed_steps")  # (lets a profiler select exactly these launches)
     e0.record(stream)
     ctx.step(args.steps)
     e1.record(stream)
     e1.synchronize()
+    torch.cuda.nvtx.range_pop()
     torch_sync()
     if barrier:
         barrier()

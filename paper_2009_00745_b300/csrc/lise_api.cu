@@ -1441,12 +1441,17 @@ struct lise_batch {
     long nxyz = 0;
     std::vector<int> evo;             // their batch indices
     int n_items = 0;                  // (evolution, group) items of the pencils and predictor launches
-    long pl_blocks = 0;               // planes blocks over all of them
-    PencilArgs *corr[4] = {}, *deriv[4] = {};
-    PlanesArgs *pl_m[4] = {}, *pl_y[4] = {};
+    // pencils and planes arguments (host copies: the launches carry them in their parameters), per
+    // history phase and evolution; the evolutions in chunks of at most kBatchInline, one launch each
+    std::vector<PencilArgs> corr[4], deriv[4];
+    std::vector<PlanesArgs> pl_m[4], pl_y[4];
+    std::vector<int> chunk0;          // first evolution (index into evo) of each chunk, and the end
+    std::vector<int> chunk_item0;     // first item of each chunk, and the end
+    std::vector<long> pl_block0;      // first planes block of each evolution within its chunk
+    std::vector<long> chunk_blocks;   // planes blocks of each chunk
     PointwiseArgs* pred[4] = {};
-    int2* items = nullptr;
-    long* pl_block0 = nullptr;
+    int2* items = nullptr;            // items (evolution relative to its chunk, group), by chunk
+    int2* items_abs = nullptr;        // the same items with the evolution's index in evo (predictor)
     ReduceArgs* red[4][2] = {};       // the reductions of these evolutions
     long* red_block0 = nullptr;
     long red_blocks = 0;
@@ -1493,15 +1498,44 @@ int batch_per_size(lise_batch* b, F f) {
   return LISE_OK;
 }
 
+// One planes launch per chunk of the evolutions of one lattice size (arguments a[e]).
+int batch_planes(const lise_batch::Size& z, const std::vector<PlanesArgs>& a, cudaStream_t st) {
+  PlanesBatch pb;
+  for (size_t c = 0; c + 1 < z.chunk0.size(); ++c) {
+    const int e0 = z.chunk0[c], ne = z.chunk0[c + 1] - e0;
+    for (int j = 0; j < ne; ++j) {
+      pb.seg[j] = a[e0 + j];
+      pb.block0[j] = z.pl_block0[e0 + j];
+    }
+    pb.block0[ne] = z.chunk_blocks[c];
+    pb.n_seg = ne;
+    if (launch_planes_batch(z.N, z.pb, pb, z.chunk_blocks[c], st)) return LISE_ECUDA;
+  }
+  return LISE_OK;
+}
+
+// The same for a pencils launch in the given mode.
+int batch_pencils(const lise_batch::Size& z, int mode, int strict, const std::vector<PencilArgs>& a, cudaStream_t st) {
+  PencilBatch pb;
+  for (size_t c = 0; c + 1 < z.chunk0.size(); ++c) {
+    const int e0 = z.chunk0[c], ne = z.chunk0[c + 1] - e0;
+    for (int j = 0; j < ne; ++j) pb.evo[j] = a[e0 + j];
+    pb.items = z.items + z.chunk_item0[c];
+    if (launch_pencils_batch(z.N, mode, strict, pb, z.chunk_item0[c + 1] - z.chunk_item0[c], z.qb, st))
+      return LISE_ECUDA;
+  }
+  return LISE_OK;
+}
+
 // The launches of one ABM step in history phase k of the evolutions of one lattice size.
 int batch_size_step(lise_batch* b, lise_batch::Size& z, int k, cudaStream_t st) {
   const int ne = (int)z.evo.size();
-  if (launch_planes_batch(z.N, z.pb, PlanesBatch{z.pl_m[k], z.pl_block0, ne}, z.pl_blocks, st) ||
-      launch_pencils_batch(z.N, M_CORRECT, b->strict, PencilBatch{z.corr[k], z.items}, z.n_items, z.qb, st) ||
-      launch_reduce_batch(ReduceBatch{z.red[k][0], z.red_block0, ne}, z.red_blocks, st) ||
-      launch_planes_batch(z.N, z.pb, PlanesBatch{z.pl_y[k], z.pl_block0, ne}, z.pl_blocks, st) ||
-      launch_pencils_batch(z.N, M_RHS, 0, PencilBatch{z.deriv[k], z.items}, z.n_items, z.qb, st) ||
-      launch_predict_batch(b->strict, PredictBatch{z.pred[k], z.items}, z.nxyz, z.n_items, st) ||
+  TRY(batch_planes(z, z.pl_m[k], st));
+  TRY(batch_pencils(z, M_CORRECT, b->strict, z.corr[k], st));
+  if (launch_reduce_batch(ReduceBatch{z.red[k][0], z.red_block0, ne}, z.red_blocks, st)) return LISE_ECUDA;
+  TRY(batch_planes(z, z.pl_y[k], st));
+  TRY(batch_pencils(z, M_RHS, 0, z.deriv[k], st));
+  if (launch_predict_batch(b->strict, PredictBatch{z.pred[k], z.items_abs}, z.nxyz, z.n_items, st) ||
       launch_reduce_batch(ReduceBatch{z.red[k][1], z.red_block0, ne}, z.red_blocks, st))
     return LISE_ECUDA;
   return LISE_OK;
@@ -1609,17 +1643,13 @@ static int batch_create(lise_ctx* const* ctxs, int n, lise_batch** out) {
     return off;
   };
   struct Off {
-    size_t corr[4], deriv[4], pl_m[4], pl_y[4], pred[4], red[4][2], items, pl_block0, red_block0;
+    size_t pred[4], red[4][2], items, items_abs, red_block0;
   };
   std::vector<Off> off(b->sizes.size());
   for (size_t zi = 0; zi < b->sizes.size(); ++zi) {
     auto& z = b->sizes[zi];
     const size_t ne = z.evo.size();
     for (int k = 0; k < 4; ++k) {
-      off[zi].corr[k] = place(ne * sizeof(PencilArgs));
-      off[zi].deriv[k] = place(ne * sizeof(PencilArgs));
-      off[zi].pl_m[k] = place(ne * sizeof(PlanesArgs));
-      off[zi].pl_y[k] = place(ne * sizeof(PlanesArgs));
       off[zi].pred[k] = place(ne * sizeof(PointwiseArgs));
       for (int r = 0; r < 2; ++r) off[zi].red[k][r] = place(ne * sizeof(ReduceArgs));
     }
@@ -1627,7 +1657,7 @@ static int batch_create(lise_ctx* const* ctxs, int n, lise_batch** out) {
     z.n_items = 0;
     for (int e : z.evo) z.n_items += b->ctx[e]->n_groups;
     off[zi].items = place((size_t)z.n_items * sizeof(int2));
-    off[zi].pl_block0 = place((ne + 1) * sizeof(long));
+    off[zi].items_abs = place((size_t)z.n_items * sizeof(int2));
   }
   const size_t drive_off = place((size_t)8 * n * sizeof(double));
   if (rc == LISE_OK && cudaMalloc(&b->tables, img.size()) != cudaSuccess) {
@@ -1638,21 +1668,40 @@ static int batch_create(lise_ctx* const* ctxs, int n, lise_batch** out) {
   // fill the image
   for (size_t zi = 0; zi < b->sizes.size() && rc == LISE_OK; ++zi) {
     auto& z = b->sizes[zi];
+    const int ne = (int)z.evo.size();
     int2* items = reinterpret_cast<int2*>(img.data() + off[zi].items);
-    long* pb0 = reinterpret_cast<long*>(img.data() + off[zi].pl_block0);
+    int2* items_abs = reinterpret_cast<int2*>(img.data() + off[zi].items_abs);
+    // chunks of at most kBatchInline evolutions: items and planes blocks counted per chunk
+    z.chunk0.clear();
+    z.chunk_item0.clear();
+    z.chunk_blocks.clear();
+    z.pl_block0.assign(ne, 0);
     int it = 0;
-    pb0[0] = 0;
-    for (size_t j = 0; j < z.evo.size(); ++j) {
+    for (int j = 0; j < ne; ++j) {
+      if (j % kBatchInline == 0) {
+        z.chunk0.push_back(j);
+        z.chunk_item0.push_back(it);
+        z.chunk_blocks.push_back(0);
+      }
       lise_ctx* c = b->ctx[z.evo[j]];
-      for (int g = 0; g < c->n_groups; ++g) items[it++] = make_int2((int)j, g);
-      pb0[j + 1] = pb0[j] + planes_blocks((long)c->p.n_qp * 2 * c->N, z.pb);
+      for (int g = 0; g < c->n_groups; ++g) {
+        items[it] = make_int2(j % kBatchInline, g);
+        items_abs[it++] = make_int2(j, g);
+      }
+      z.pl_block0[j] = z.chunk_blocks.back();
+      z.chunk_blocks.back() += planes_blocks((long)c->p.n_qp * 2 * c->N, z.pb);
     }
-    z.pl_blocks = pb0[z.evo.size()];
+    z.chunk0.push_back(ne);
+    z.chunk_item0.push_back(it);
     for (int k = 0; k < 4 && rc == LISE_OK; ++k) {
-      PencilArgs* corr = reinterpret_cast<PencilArgs*>(img.data() + off[zi].corr[k]);
-      PencilArgs* deriv = reinterpret_cast<PencilArgs*>(img.data() + off[zi].deriv[k]);
-      PlanesArgs* plm = reinterpret_cast<PlanesArgs*>(img.data() + off[zi].pl_m[k]);
-      PlanesArgs* ply = reinterpret_cast<PlanesArgs*>(img.data() + off[zi].pl_y[k]);
+      z.corr[k].resize(ne);
+      z.deriv[k].resize(ne);
+      z.pl_m[k].resize(ne);
+      z.pl_y[k].resize(ne);
+      std::vector<PencilArgs>& corr = z.corr[k];
+      std::vector<PencilArgs>& deriv = z.deriv[k];
+      std::vector<PlanesArgs>& plm = z.pl_m[k];
+      std::vector<PlanesArgs>& ply = z.pl_y[k];
       PointwiseArgs* pred = reinterpret_cast<PointwiseArgs*>(img.data() + off[zi].pred[k]);
       for (size_t j = 0; j < z.evo.size(); ++j) {
         const int e = z.evo[j];
@@ -1678,10 +1727,6 @@ static int batch_create(lise_ctx* const* ctxs, int n, lise_batch** out) {
           reinterpret_cast<ReduceArgs*>(img.data() + off[zi].red[k][r])[j] = ra;
         }
       }
-      z.corr[k] = reinterpret_cast<PencilArgs*>(dev + off[zi].corr[k]);
-      z.deriv[k] = reinterpret_cast<PencilArgs*>(dev + off[zi].deriv[k]);
-      z.pl_m[k] = reinterpret_cast<PlanesArgs*>(dev + off[zi].pl_m[k]);
-      z.pl_y[k] = reinterpret_cast<PlanesArgs*>(dev + off[zi].pl_y[k]);
       z.pred[k] = reinterpret_cast<PointwiseArgs*>(dev + off[zi].pred[k]);
       for (int r = 0; r < 2; ++r) z.red[k][r] = reinterpret_cast<ReduceArgs*>(dev + off[zi].red[k][r]);
     }
@@ -1691,7 +1736,7 @@ static int batch_create(lise_ctx* const* ctxs, int n, lise_batch** out) {
     z.red_blocks = rb0[z.evo.size()];
     z.red_block0 = reinterpret_cast<long*>(dev + off[zi].red_block0);
     z.items = reinterpret_cast<int2*>(dev + off[zi].items);
-    z.pl_block0 = reinterpret_cast<long*>(dev + off[zi].pl_block0);
+    z.items_abs = reinterpret_cast<int2*>(dev + off[zi].items_abs);
   }
   if (rc == LISE_OK) {
     b->drive_dev = reinterpret_cast<double*>(dev + drive_off);

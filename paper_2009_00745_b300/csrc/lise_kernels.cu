@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(NT) k_planes(PlanesArgs a) {
 // Several evolutions' planes in one launch: segment k covers blocks
 // [b.block0[k], b.block0[k + 1]) with the arguments b.seg[k] (one evolution's operand).
 template <typename R, int N, int PB, int NT>
-__global__ void __launch_bounds__(NT) k_planes_batch(PlanesBatch b) {
+__global__ void __launch_bounds__(NT) k_planes_batch(const __grid_constant__ PlanesBatch b) {
   int k = 0;
   while (k + 1 < b.n_seg && (long)blockIdx.x >= b.block0[k + 1]) ++k;
   planes_body<R, N, PB, NT>(b.seg[k], (long)blockIdx.x - b.block0[k]);

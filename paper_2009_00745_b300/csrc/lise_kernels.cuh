@@ -133,15 +133,19 @@ struct ReduceArgs {
   int* err;               // set bit 0 if a density is not finite
 };
 
-// Batched launches (lise_batch_*): the arguments of several evolutions in device memory and a
-// work table mapping each block (row) to an evolution.
+// Batched launches (lise_batch_*): the arguments of several evolutions and a work table mapping
+// each block (row) to an evolution.  The pencils and planes launches carry up to kBatchInline
+// evolutions' arguments in their kernel parameters (constant-bank reads, and the pencils
+// kernel's tensor maps in parameter space, as in the per-context launches; larger groups take
+// several launches); the reduction and predictor launches read theirs from device memory.
+constexpr int kBatchInline = 16;
 struct PencilBatch {
-  const PencilArgs* evo;   // per evolution (tensor maps of the staged FP32 path included)
-  const int2* items;       // block row -> (evolution, density group of that evolution)
+  PencilArgs evo[kBatchInline];  // per evolution (tensor maps of the staged FP32 path included)
+  const int2* items;             // block row -> (index into evo, density group of that evolution)
 };
 struct PlanesBatch {
-  const PlanesArgs* seg;   // per evolution
-  const long* block0;      // first block of each segment, n_seg + 1 entries
+  PlanesArgs seg[kBatchInline];  // per evolution
+  long block0[kBatchInline + 1]; // first block of each segment, n_seg + 1 entries
   int n_seg;
 };
 struct ReduceBatch {

@@ -598,7 +598,8 @@ def run_pair(L, args, local, stream, fp64_peak):
         out[prec] = {"value": r["units"] / (r["ms"] / 1e3), "ms_per_step": r["ms"] / args.steps,
                      "roofline": roofline(w, r["prof"], r["ms"] / args.steps, fp64_peak), "clocks": r["clocks"],
                      "gpu_launches": int(sum(v[0] for v in r["prof"].values())),
-                     "tuned": {"pencils_states_per_batch": L.pencil_batch(w.nx, prec)}}
+                     "tuned": {"pencils_states_per_batch": L.pencil_batch(w.nx, prec),
+                               "planes_per_block": L.planes_per_block(w.nx, prec)}}
         torch.cuda.empty_cache()
     del psi_dev
     torch.cuda.empty_cache()
@@ -739,7 +740,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if not mixed else "f64+c64",
             "data": "synthetic", "config": config_of(w, args), "roofline": roof, "cpu_baseline": cpu,
-            "tuned": {"pencils_states_per_batch": L.pencil_batch(w.nx, w.precision)},
+            "tuned": {"pencils_states_per_batch": L.pencil_batch(w.nx, w.precision),
+                      "planes_per_block": L.planes_per_block(w.nx, w.precision)},
             "e2e": e2e, "clocks": r["clocks"], "gpu_launches": gpu_launches,
             "energy_after_timed_steps": r["E_end"], "particle_number": r["N_end"],
             "fp64_fma_peak_tflops": fp64_peak, "pair": pair,

@@ -145,11 +145,14 @@ int lise_pencil_batch(int N, int precision);
 int lise_set_pencil_batch(int N, int precision, int qb);
 /* The same for the planes per block of the FFT planes kernel (the in-plane part T_xy on
  * lattices that do not use the tensor-core planes kernels: the mixed path, and FP64 with N
- * not a multiple of 16): candidates 1, 2, 4, 8 where the variant fits in shared memory and
- * registers, tuned on the first lise_set_state of each lattice and precision; results do
- * not depend on it (every plane is transformed on its own).  lise_planes_per_block returns
- * the value in use (0 for the tensor-core lattices or an unsupported N); the setter forces
- * pb or clears it with pb = 0 (LISE_EINVAL for a variant that does not exist). */
+ * not a multiple of 16): candidates 1, 2, 4, 8 (line FFTs through shared memory) and, in the
+ * FP32 compute precision with N <= 48, -1, -2, -4, -8 (the same transforms with each thread
+ * holding whole lines in registers, -pb planes per block), where the variant fits in shared
+ * memory and registers, tuned on the first lise_set_state of each lattice and precision;
+ * results do not depend on it (the same operations in the same order for every plane).
+ * lise_planes_per_block returns the value in use (0 for the tensor-core lattices or an
+ * unsupported N); the setter forces pb or clears it with pb = 0 (LISE_EINVAL for a variant
+ * that does not exist). */
 int lise_planes_per_block(int N, int precision);
 int lise_set_planes_per_block(int N, int precision, int pb);
 

@@ -784,8 +784,8 @@ static int tune_planes(lise_ctx* c) {
   if (ozaki_path(c->N, c->mixed) || planes_pb_get(c->N, c->mixed)) return LISE_OK;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   if (planes_pb_get(c->N, c->mixed)) return LISE_OK;
-  int cands[4], n_valid = 0;
-  for (int pb : {1, 2, 4, 8})
+  int cands[8], n_valid = 0;
+  for (int pb : {1, 2, 4, 8, -1, -2, -4, -8})
     if (planes_pb_valid(c->N, c->mixed, pb)) cands[n_valid++] = pb;
   if (n_valid < 2) {
     if (n_valid == 1) planes_pb_set(c->N, c->mixed, cands[0]);

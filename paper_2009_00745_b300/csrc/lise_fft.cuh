@@ -238,7 +238,47 @@ __device__ __forceinline__ void fft_phase2(typename Cx<R>::T* buf, Base base, in
 
 struct Identity {
   template <typename T> __device__ __forceinline__ T operator()(int, int, T v) const { return v; }
+  template <typename T> __device__ __forceinline__ T operator()(int, T v) const { return v; }
 };
+
+// The same four-step transform of one line held by one thread in registers (x in natural
+// order in and out; post(k, value) as in fft_phase2): the same butterflies, twiddles and
+// operation order as fft_phase1 and fft_phase2, so the values are those of the
+// shared-memory version.  Every index is a compile-time constant (fully unrolled).
+template <int N, int S, typename R, typename Post>
+__device__ __forceinline__ void line_fft(typename Cx<R>::T (&x)[N], const typename Cx<R>::T* tw, Post post) {
+  using T = typename Cx<R>::T;
+  constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2;
+#pragma unroll
+  for (int j2 = 0; j2 < N2; ++j2) {
+    T a[N1];
+#pragma unroll
+    for (int j1 = 0; j1 < N1; ++j1) a[j1] = x[j2 + N2 * j1];
+    Dft<N1, S, R>::run(a);
+    if (j2 != 0) {
+#pragma unroll
+      for (int k1 = 1; k1 < N1; ++k1) {
+        T w = tw[j2 * N1 + k1];
+        if (S > 0) w.y = -w.y;
+        a[k1] = cmul(a[k1], w);
+      }
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) x[j2 + N2 * k1] = a[k1];
+  }
+  T y[N];
+#pragma unroll
+  for (int k1 = 0; k1 < N1; ++k1) {
+    T b[N2];
+#pragma unroll
+    for (int j2 = 0; j2 < N2; ++j2) b[j2] = x[k1 * N2 + j2];
+    Dft<N2, S, R>::run(b);
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) y[k1 + N1 * k2] = post(k1 + N1 * k2, b[k2]);
+  }
+#pragma unroll
+  for (int k = 0; k < N; ++k) x[k] = y[k];
+}
 
 // Full line transform (both phases), with barriers after each phase.
 template <int N, int S, typename R, int NL, int NT, typename Base, typename Post>

@@ -164,15 +164,21 @@ __device__ __forceinline__ void dens_fold(const DensF& d, double& sn, double& sr
 template <int N> struct PlanesPB { static constexpr int v = N <= 8 ? 8 : (N <= 16 ? 4 : (N <= 32 ? 2 : 1)); };
 
 // ------------------------------------------------------------------ planes --
+// The kinetic factor's multiply, rounded on its own (never fused with the additions of the
+// transform that follows: in the register-line kernel the product stays in registers, and the
+// two planes kernels must round identically).
+__device__ __forceinline__ float2 kin_mul(float2 v, float f) { return make_float2(__fmul_rn(v.x, f), __fmul_rn(v.y, f)); }
+__device__ __forceinline__ double2 kin_mul(double2 v, double f) { return make_double2(__dmul_rn(v.x, f), __dmul_rn(v.y, f)); }
+
+// The block's PB planes of the operand into shared memory (rows padded to N + 1 elements, so
+// that row and column lines are both conflict-free), with the twiddles and kinetic factors;
+// returns the number of planes the block holds (NT threads).
 template <typename R, int N, int PB, int NT>
-__device__ __forceinline__ void planes_body(const PlanesArgs& a, const long block) {
+__device__ __forceinline__ int planes_load(const PlanesArgs& a, const long block, typename Cx<R>::T* buf,
+                                           typename Cx<R>::T* tw, R* hk) {
   using T = typename Cx<R>::T;
   constexpr int NP = N + 1;   // padded row stride (conflict-free row and column lines)
   constexpr int PS = N * NP;  // plane stride
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  T* buf = reinterpret_cast<T*>(smem_raw);
-  T* tw = buf + PB * PS;
-  R* hk = reinterpret_cast<R*>(tw + N);
   const T* twg = reinterpret_cast<const T*>(a.tw);
   const R* hg = reinterpret_cast<const R*>(a.hxy);
   for (int i = threadIdx.x; i < N; i += NT) {
@@ -201,22 +207,105 @@ __device__ __forceinline__ void planes_body(const PlanesArgs& a, const long bloc
     const int pl = i / (N * N), r = i % (N * N);
     if (i < PB * N * N) buf[pl * PS + (r / N) * NP + (r % N)] = v[e];
   }
+  return np;
+}
+
+// The block's np planes of T_xy x from shared memory, coalesced.
+template <typename R, int N, int PB, int NT>
+__device__ __forceinline__ void planes_store(const PlanesArgs& a, const long block, const int np,
+                                            const typename Cx<R>::T* buf) {
+  using T = typename Cx<R>::T;
+  constexpr int NP = N + 1, PS = N * NP;
+  T* dst = reinterpret_cast<T*>(a.txy) + block * PB * N * N;
+  for (int i = threadIdx.x; i < np * N * N; i += NT) {
+    int pl = i / (N * N), r = i % (N * N);
+    dst[i] = buf[pl * PS + (r / N) * NP + (r % N)];
+  }
+}
+
+template <typename R, int N, int PB, int NT>
+__device__ __forceinline__ void planes_body(const PlanesArgs& a, const long block) {
+  using T = typename Cx<R>::T;
+  constexpr int NP = N + 1;   // padded row stride (conflict-free row and column lines)
+  constexpr int PS = N * NP;  // plane stride
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  T* buf = reinterpret_cast<T*>(smem_raw);
+  T* tw = buf + PB * PS;
+  R* hk = reinterpret_cast<R*>(tw + N);
+  const int np = planes_load<R, N, PB, NT>(a, block, buf, tw, hk);
   __syncthreads();
   auto rows = [](int l) { return (l / N) * PS + (l % N) * NP; };
   auto cols = [](int l) { return (l / N) * PS + (l % N); };
   fft_lines<N, -1, R, PB * N, NT>(buf, rows, 1, tw, Identity());
   // forward along y; on store multiply by (alpha/2)(kx^2 + ky^2)/N^2 (line l has kx = l % N)
-  fft_lines<N, -1, R, PB * N, NT>(buf, cols, NP, tw, [&](int l, int k, T v) {
-    R f = hk[l % N] + hk[k];
-    return T{v.x * f, v.y * f};
-  });
+  fft_lines<N, -1, R, PB * N, NT>(buf, cols, NP, tw, [&](int l, int k, T v) { return kin_mul(v, hk[l % N] + hk[k]); });
   fft_lines<N, +1, R, PB * N, NT>(buf, cols, NP, tw, Identity());
   fft_lines<N, +1, R, PB * N, NT>(buf, rows, 1, tw, Identity());
-  T* dst = reinterpret_cast<T*>(a.txy) + plane0 * N * N;
-  for (int i = threadIdx.x; i < np * N * N; i += NT) {
-    int pl = i / (N * N), r = i % (N * N);
-    dst[i] = buf[pl * PS + (r / N) * NP + (r % N)];
-  }
+  planes_store<R, N, PB, NT>(a, block, np, buf);
+}
+
+// The same transform with whole lines in registers (FP32 compute precision): one thread per
+// line (PB N threads), the plane in shared memory only between the row, column and row passes
+// (8 shared-memory accesses per element instead of 18: this kernel is bound by shared-memory
+// bandwidth).  The line transforms are line_fft, the same operations in the same order as the
+// shared-memory passes: the result is bitwise that of planes_body.
+template <int N, int PB>
+__device__ __forceinline__ void planes_line_body(const PlanesArgs& a, const long block) {
+  using R = float;
+  using T = float2;
+  constexpr int NT = PB * N, NP = N + 1, PS = N * NP;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  T* buf = reinterpret_cast<T*>(smem_raw);
+  T* tw = buf + PB * PS;
+  R* hk = reinterpret_cast<R*>(tw + N);
+  const int np = planes_load<R, N, PB, NT>(a, block, buf, tw, hk);
+  __syncthreads();
+  const int ln = threadIdx.x % N;  // this thread's row y, then column x, of plane threadIdx.x / N
+  T* row = buf + (threadIdx.x / N) * PS + ln * NP;
+  T* col = buf + (threadIdx.x / N) * PS + ln;
+  T x[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) x[i] = row[i];
+  line_fft<N, -1, R>(x, tw, Identity());
+#pragma unroll
+  for (int i = 0; i < N; ++i) row[i] = x[i];
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < N; ++i) x[i] = col[i * NP];
+  // forward along y, times (alpha/2)(kx^2 + ky^2)/N^2 (kx = ln), then the inverse along y
+  line_fft<N, -1, R>(x, tw, [&](int k, T v) { return kin_mul(v, hk[ln] + hk[k]); });
+  line_fft<N, +1, R>(x, tw, Identity());
+#pragma unroll
+  for (int i = 0; i < N; ++i) col[i * NP] = x[i];
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < N; ++i) x[i] = row[i];
+  line_fft<N, +1, R>(x, tw, Identity());
+#pragma unroll
+  for (int i = 0; i < N; ++i) row[i] = x[i];
+  __syncthreads();
+  planes_store<R, N, PB, NT>(a, block, np, buf);
+}
+
+// resident blocks of the line kernel: a register budget of about 168 per thread for lines of
+// 40 or 48 points (a line of N complex values takes 2N), 128 for shorter lines
+template <int N, int NT>
+constexpr int line_min_blocks() {
+  constexpr int regs = N >= 40 ? 168 : 128, w = (NT + 31) / 32 * 32;
+  return 65536 / (w * regs) < 1 ? 1 : 65536 / (w * regs);
+}
+
+template <int N, int PB>
+__global__ void __launch_bounds__(PB * N, line_min_blocks<N, PB * N>()) k_planes_line(PlanesArgs a) {
+  planes_line_body<N, PB>(a, blockIdx.x);
+}
+
+template <int N, int PB>
+__global__ void __launch_bounds__(PB * N, line_min_blocks<N, PB * N>())
+    k_planes_line_batch(const __grid_constant__ PlanesBatch b) {
+  int k = 0;
+  while (k + 1 < b.n_seg && (long)blockIdx.x >= b.block0[k + 1]) ++k;
+  planes_line_body<N, PB>(b.seg[k], (long)blockIdx.x - b.block0[k]);
 }
 
 template <typename R, int N, int PB, int NT>
@@ -1570,6 +1659,29 @@ void planes_pb_set(int N, int mixed, int pb) {
   if (N >= 0 && N <= 64) g_pb_tuned[mixed ? 1 : 0][N].store(pb, std::memory_order_relaxed);
 }
 
+// The register-line variant (planes_line_body), FP32 compute precision only: a whole line in
+// registers (N <= 48), PB N threads per block, shared memory within 227 KB.
+template <typename R, int N, int PB>
+constexpr bool planes_line_fits() {
+  return sizeof(R) == 4 && N <= 48 && PB * N <= 1024 &&
+         (size_t)PB * N * (N + 1) * sizeof(float2) + N * sizeof(float2) + N * sizeof(float) <= 227 * 1024;
+}
+template <int N, int PB>
+constexpr size_t planes_line_smem() {
+  return (size_t)PB * N * (N + 1) * sizeof(float2) + N * sizeof(float2) + N * sizeof(float);
+}
+
+template <int N, int PB>
+static int planes_line_npb(const PlanesArgs& a, cudaStream_t s) {
+  auto kern = k_planes_line<N, PB>;
+  static std::atomic<unsigned long long> attr_done{0};
+  if (smem_attr((const void*)kern, planes_line_smem<N, PB>(), attr_done)) return 3;
+  const long blocks = (a.n_planes + PB - 1) / PB;
+  if (blocks <= 0) return 0;
+  kern<<<(unsigned)blocks, PB * N, planes_line_smem<N, PB>(), s>>>(a);
+  return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}
+
 template <typename R, int N, int PB>
 static int planes_npb(const PlanesArgs& a, cudaStream_t s) {
   using T = typename Cx<R>::T;
@@ -1593,6 +1705,14 @@ static int planes_n(const PlanesArgs& a, cudaStream_t s, int pb) {
       return planes_oz_n<N>(a, s);
   } else {
     if (pb == 0) pb = planes_pb_get(N, sizeof(R) == 4);
+    if constexpr (planes_line_fits<R, N, 1>())
+      if (pb == -1) return planes_line_npb<N, 1>(a, s);
+    if constexpr (planes_line_fits<R, N, 2>())
+      if (pb == -2) return planes_line_npb<N, 2>(a, s);
+    if constexpr (planes_line_fits<R, N, 4>())
+      if (pb == -4) return planes_line_npb<N, 4>(a, s);
+    if constexpr (planes_line_fits<R, N, 8>())
+      if (pb == -8) return planes_line_npb<N, 8>(a, s);
     if constexpr (planes_pb_fits<R, N, 1>())
       if (pb == 1) return planes_npb<R, N, 1>(a, s);
     if constexpr (planes_pb_fits<R, N, 2>())
@@ -1615,6 +1735,10 @@ static bool planes_pb_valid_n(int pb) {
       case 2: return planes_pb_fits<R, N, 2>();
       case 4: return planes_pb_fits<R, N, 4>();
       case 8: return planes_pb_fits<R, N, 8>();
+      case -1: return planes_line_fits<R, N, 1>();
+      case -2: return planes_line_fits<R, N, 2>();
+      case -4: return planes_line_fits<R, N, 4>();
+      case -8: return planes_line_fits<R, N, 8>();
       default: return false;
     }
   }
@@ -1771,8 +1895,26 @@ static int planes_batch_npb(const PlanesBatch& b, long n_blocks, cudaStream_t s)
   return cudaGetLastError() == cudaSuccess ? 0 : 3;
 }
 
+template <int N, int PB>
+static int planes_line_batch_npb(const PlanesBatch& b, long n_blocks, cudaStream_t s) {
+  auto kern = k_planes_line_batch<N, PB>;
+  static std::atomic<unsigned long long> attr_done{0};
+  if (smem_attr((const void*)kern, planes_line_smem<N, PB>(), attr_done)) return 3;
+  if (n_blocks <= 0) return 0;
+  kern<<<(unsigned)n_blocks, PB * N, planes_line_smem<N, PB>(), s>>>(b);
+  return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}
+
 template <int N>
 static int planes_batch_n(const PlanesBatch& b, long n_blocks, int pb, cudaStream_t s) {
+  if constexpr (planes_line_fits<float, N, 1>())
+    if (pb == -1) return planes_line_batch_npb<N, 1>(b, n_blocks, s);
+  if constexpr (planes_line_fits<float, N, 2>())
+    if (pb == -2) return planes_line_batch_npb<N, 2>(b, n_blocks, s);
+  if constexpr (planes_line_fits<float, N, 4>())
+    if (pb == -4) return planes_line_batch_npb<N, 4>(b, n_blocks, s);
+  if constexpr (planes_line_fits<float, N, 8>())
+    if (pb == -8) return planes_line_batch_npb<N, 8>(b, n_blocks, s);
   if constexpr (planes_pb_fits<float, N, 1>())
     if (pb == 1) return planes_batch_npb<N, 1>(b, n_blocks, s);
   if constexpr (planes_pb_fits<float, N, 2>())
@@ -1804,7 +1946,10 @@ int launch_planes_batch(int N, int pb, const PlanesBatch& b, long n_blocks, cuda
   }
 }
 
-long planes_blocks(long n_planes, int pb) { return pb > 0 ? (n_planes + pb - 1) / pb : 0; }
+long planes_blocks(long n_planes, int pb) {
+  const int p = pb < 0 ? -pb : pb;  // (negative: the register-line variant with -pb planes per block)
+  return p > 0 ? (n_planes + p - 1) / p : 0;
+}
 
 int launch_reduce_batch(const ReduceBatch& b, long n_blocks, cudaStream_t s) {
   if (n_blocks <= 0) return 0;

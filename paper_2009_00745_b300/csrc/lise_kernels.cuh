@@ -234,7 +234,9 @@ struct PredictBatch {
 // pb: planes per block of the FFT planes kernel (0 = the tuned value, else the default)
 int launch_planes(int N, int mixed, const PlanesArgs& a, cudaStream_t s, int pb = 0);
 // Planes-per-block autotuning state of the FFT planes kernel (per process): tuned value per
-// (precision, N), 0 = none; the value in use; whether a variant is compiled.
+// (precision, N), 0 = none; the value in use; whether a variant is compiled.  pb > 0: the
+// shared-memory line FFTs with pb planes per block; pb < 0: the register-line variant with
+// -pb planes per block (FP32 compute precision, N <= 48).  All give bitwise the same result.
 int planes_pb_get(int N, int mixed);
 void planes_pb_set(int N, int mixed, int pb);
 int planes_pb(int N, int mixed);
@@ -252,7 +254,7 @@ int launch_reduce(const ReduceArgs& a, cudaStream_t s);
 // pencils batch size (2 or 4, the one the evolutions' tensor maps were encoded for).
 int launch_pencils_batch(int N, int mode, int strict, const PencilBatch& b, int n_items, int qb, cudaStream_t s);
 int launch_planes_batch(int N, int pb, const PlanesBatch& b, long n_blocks, cudaStream_t s);
-long planes_blocks(long n_planes, int pb);  // blocks of the FFT planes kernel: pb planes per block
+long planes_blocks(long n_planes, int pb);  // blocks of the FFT planes kernel: |pb| planes per block
 int launch_reduce_batch(const ReduceBatch& b, long n_blocks, cudaStream_t s);
 int launch_predict_batch(int strict, const PredictBatch& b, long nxyz, int n_items, cudaStream_t s);
 // Tensor maps of one evolution's staged pencils launch (FP32 compute precision) written

@@ -147,7 +147,7 @@ def test_pencil_batch_controls_host_only():
 
 def test_planes_per_block_controls_host_only():
     assert L.planes_per_block(32, "fp64") == 0          # tensor-core planes kernel
-    assert L.planes_per_block(48, "mixed") in (1, 2, 4, 8)
+    assert L.planes_per_block(48, "mixed") in (1, 2, 4, 8, -1, -2, -4, -8)
     with pytest.raises(L.LiseError) as e:
         L.set_planes_per_block(32, "fp64", 2)           # no FFT planes kernel there
     assert e.value.status == L.EINVAL
@@ -156,4 +156,10 @@ def test_planes_per_block_controls_host_only():
     assert e.value.status == L.EINVAL
     L.set_planes_per_block(16, "mixed", 8)
     assert L.planes_per_block(16, "mixed") == 8
+    L.set_planes_per_block(16, "mixed", -4)             # whole lines in registers
+    assert L.planes_per_block(16, "mixed") == -4
+    for N, prec, pb in ((64, "mixed", -1), (12, "fp64", -2), (16, "mixed", -3)):
+        with pytest.raises(L.LiseError) as e:           # no register-line variant there
+            L.set_planes_per_block(N, prec, pb)
+        assert e.value.status == L.EINVAL
     L.set_planes_per_block(16, "mixed", 0)

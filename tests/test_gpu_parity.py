@@ -583,7 +583,7 @@ def test_pencil_batch_choice_is_bitwise_neutral(N, precision):
         assert np.array_equal(x, tuned)
 
 
-@pytest.mark.parametrize("N,precision", [(24, "mixed"), (48, "mixed"), (12, "fp64")])
+@pytest.mark.parametrize("N,precision", [(16, "mixed"), (24, "mixed"), (32, "mixed"), (48, "mixed"), (12, "fp64")])
 def test_planes_per_block_choice_is_bitwise_neutral(N, precision):
     w = W.ufg_plane_waves(N, 13, noise_eps=0.05)
 
@@ -594,7 +594,7 @@ def test_planes_per_block_choice_is_bitwise_neutral(N, precision):
             return ctx.state()
 
     outs = {}
-    for pb in (1, 2, 4, 8):
+    for pb in (1, 2, 4, 8, -1, -2, -4, -8):   # negative: whole lines in registers (FP32 path)
         try:
             L.set_planes_per_block(N, precision, pb)
         except L.LiseError:

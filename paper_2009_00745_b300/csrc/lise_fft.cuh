@@ -290,4 +290,54 @@ __device__ __forceinline__ void fft_lines(typename Cx<R>::T* buf, Base base, int
   __syncthreads();
 }
 
+// The same transform of one line shared by two threads (N1 and N2 even): thread s holds the
+// line positions p = 2 m + s in L[m], m < N/2, on input and on output.  Phase 1: the thread's
+// N1-point DFTs are those of j2 = 2 jj + s; phase 2 needs, for k1 = 2 kk + s, the phase-1
+// values of every j2: the ones of the other parity come from the partner thread (lane ^ 16,
+// one shuffle per real word).  The butterflies, twiddles and operation order are those of
+// fft_phase1 and fft_phase2 (the shuffles and selects only move values), so the values are
+// those of the shared-memory version.  Every register index is a compile-time constant.
+template <int N, int S, typename Post>
+__device__ __forceinline__ void half_line_fft(float2 (&L)[N / 2], const float2* tw, int s, Post post) {
+  constexpr int N1 = Plan<N>::N1, N2 = Plan<N>::N2, H1 = N1 / 2, H2 = N2 / 2;
+  static_assert(N1 % 2 == 0 && N2 % 2 == 0, "half lines need even factors");
+  float2 P[H2][N1];  // phase-1 output of j2 = 2 jj + s at k1
+#pragma unroll
+  for (int jj = 0; jj < H2; ++jj) {
+    const int j2 = 2 * jj + s;
+    float2 a[N1];
+#pragma unroll
+    for (int j1 = 0; j1 < N1; ++j1) a[j1] = L[jj + H2 * j1];  // position j2 + N2 j1
+    Dft<N1, S, float>::run(a);
+    if (j2 != 0) {
+#pragma unroll
+      for (int k1 = 1; k1 < N1; ++k1) {
+        float2 w = tw[j2 * N1 + k1];
+        if (S > 0) w.y = -w.y;
+        a[k1] = cmul(a[k1], w);
+      }
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) P[jj][k1] = a[k1];
+  }
+#pragma unroll
+  for (int kk = 0; kk < H1; ++kk) {
+    // k1 = 2 kk + s: own values at j2 = 2 jj + s, the partner's at j2 = 2 jj + 1 - s
+    float2 b[N2];
+#pragma unroll
+    for (int jj = 0; jj < H2; ++jj) {
+      const float2 keep = s ? P[jj][2 * kk + 1] : P[jj][2 * kk];
+      const float2 send = s ? P[jj][2 * kk] : P[jj][2 * kk + 1];
+      float2 recv;
+      recv.x = __shfl_xor_sync(0xFFFFFFFFu, send.x, 16);
+      recv.y = __shfl_xor_sync(0xFFFFFFFFu, send.y, 16);
+      b[2 * jj] = s ? recv : keep;
+      b[2 * jj + 1] = s ? keep : recv;
+    }
+    Dft<N2, S, float>::run(b);
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) L[kk + H1 * k2] = post(2 * kk + s + N1 * k2, b[k2]);  // position k1 + N1 k2
+  }
+}
+
 }  // namespace lise

@@ -287,25 +287,81 @@ __device__ __forceinline__ void planes_line_body(const PlanesArgs& a, const long
   planes_store<R, N, PB, NT>(a, block, np, buf);
 }
 
-// resident blocks of the line kernel: a register budget of about 168 per thread for lines of
-// 40 or 48 points (a line of N complex values takes 2N), 128 for shorter lines
+// The same with each line shared by two threads (lattices of 48 and 64 points, whose whole
+// lines do not fit in one thread's registers): 2 PB N threads, half_line_fft.  Warp lanes
+// 0-15 hold the even positions of 16 lines, lanes 16-31 the odd positions of the same lines
+// (conflict-free shared-memory rows and columns).  Bitwise the result of planes_body.
+template <int N, int PB>
+__device__ __forceinline__ void planes_half_body(const PlanesArgs& a, const long block) {
+  using R = float;
+  using T = float2;
+  constexpr int NT = 2 * PB * N, NP = N + 1, PS = N * NP, H = N / 2;
+  static_assert(PB * N % 16 == 0, "whole warps of lines");
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  T* buf = reinterpret_cast<T*>(smem_raw);
+  T* tw = buf + PB * PS;
+  R* hk = reinterpret_cast<R*>(tw + N);
+  const int np = planes_load<R, N, PB, NT>(a, block, buf, tw, hk);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, s = lane >> 4;
+  const int line = 16 * (threadIdx.x >> 5) + (lane & 15);  // of the block's PB N lines
+  const int ln = line % N;                                  // row y, then column x
+  T* row = buf + (line / N) * PS + ln * NP;
+  T* col = buf + (line / N) * PS + ln;
+  T L[H];
+#pragma unroll
+  for (int m = 0; m < H; ++m) L[m] = row[2 * m + s];
+  half_line_fft<N, -1>(L, tw, s, Identity());
+#pragma unroll
+  for (int m = 0; m < H; ++m) row[2 * m + s] = L[m];
+  __syncthreads();
+#pragma unroll
+  for (int m = 0; m < H; ++m) L[m] = col[(2 * m + s) * NP];
+  half_line_fft<N, -1>(L, tw, s, [&](int k, T v) { return kin_mul(v, hk[ln] + hk[k]); });
+  half_line_fft<N, +1>(L, tw, s, Identity());
+#pragma unroll
+  for (int m = 0; m < H; ++m) col[(2 * m + s) * NP] = L[m];
+  __syncthreads();
+#pragma unroll
+  for (int m = 0; m < H; ++m) L[m] = row[2 * m + s];
+  half_line_fft<N, +1>(L, tw, s, Identity());
+#pragma unroll
+  for (int m = 0; m < H; ++m) row[2 * m + s] = L[m];
+  __syncthreads();
+  planes_store<R, N, PB, NT>(a, block, np, buf);
+}
+
+// The register-line kernels: one thread per line up to 40 points, two from 48 (LineTpl).
+template <int N> struct LineTpl { static constexpr int v = N >= 48 ? 2 : 1; };
+
+// resident blocks of the line kernels: a register budget of about 168 per thread for whole
+// lines of 40 points (a line of N complex values takes 2N registers), 128 otherwise
 template <int N, int NT>
 constexpr int line_min_blocks() {
-  constexpr int regs = N >= 40 ? 168 : 128, w = (NT + 31) / 32 * 32;
+  constexpr int regs = (N >= 40 && LineTpl<N>::v == 1) ? 168 : 128, w = (NT + 31) / 32 * 32;
   return 65536 / (w * regs) < 1 ? 1 : 65536 / (w * regs);
 }
 
 template <int N, int PB>
-__global__ void __launch_bounds__(PB * N, line_min_blocks<N, PB * N>()) k_planes_line(PlanesArgs a) {
-  planes_line_body<N, PB>(a, blockIdx.x);
+__device__ __forceinline__ void planes_reg_body(const PlanesArgs& a, const long block) {
+  if constexpr (LineTpl<N>::v == 2)
+    planes_half_body<N, PB>(a, block);
+  else
+    planes_line_body<N, PB>(a, block);
 }
 
 template <int N, int PB>
-__global__ void __launch_bounds__(PB * N, line_min_blocks<N, PB * N>())
+__global__ void __launch_bounds__(LineTpl<N>::v * PB * N, line_min_blocks<N, LineTpl<N>::v * PB * N>())
+    k_planes_line(PlanesArgs a) {
+  planes_reg_body<N, PB>(a, blockIdx.x);
+}
+
+template <int N, int PB>
+__global__ void __launch_bounds__(LineTpl<N>::v * PB * N, line_min_blocks<N, LineTpl<N>::v * PB * N>())
     k_planes_line_batch(const __grid_constant__ PlanesBatch b) {
   int k = 0;
   while (k + 1 < b.n_seg && (long)blockIdx.x >= b.block0[k + 1]) ++k;
-  planes_line_body<N, PB>(b.seg[k], (long)blockIdx.x - b.block0[k]);
+  planes_reg_body<N, PB>(b.seg[k], (long)blockIdx.x - b.block0[k]);
 }
 
 template <typename R, int N, int PB, int NT>
@@ -1659,11 +1715,12 @@ void planes_pb_set(int N, int mixed, int pb) {
   if (N >= 0 && N <= 64) g_pb_tuned[mixed ? 1 : 0][N].store(pb, std::memory_order_relaxed);
 }
 
-// The register-line variant (planes_line_body), FP32 compute precision only: a whole line in
-// registers (N <= 48), PB N threads per block, shared memory within 227 KB.
+// The register-line variants (planes_line_body, planes_half_body), FP32 compute precision only:
+// LineTpl threads per line, whole warps of lines for the two-thread form, shared memory within
+// 227 KB.
 template <typename R, int N, int PB>
 constexpr bool planes_line_fits() {
-  return sizeof(R) == 4 && N <= 48 && PB * N <= 1024 &&
+  return sizeof(R) == 4 && LineTpl<N>::v * PB * N <= 1024 && (LineTpl<N>::v == 1 || PB * N % 16 == 0) &&
          (size_t)PB * N * (N + 1) * sizeof(float2) + N * sizeof(float2) + N * sizeof(float) <= 227 * 1024;
 }
 template <int N, int PB>
@@ -1678,7 +1735,7 @@ static int planes_line_npb(const PlanesArgs& a, cudaStream_t s) {
   if (smem_attr((const void*)kern, planes_line_smem<N, PB>(), attr_done)) return 3;
   const long blocks = (a.n_planes + PB - 1) / PB;
   if (blocks <= 0) return 0;
-  kern<<<(unsigned)blocks, PB * N, planes_line_smem<N, PB>(), s>>>(a);
+  kern<<<(unsigned)blocks, LineTpl<N>::v * PB * N, planes_line_smem<N, PB>(), s>>>(a);
   return cudaGetLastError() == cudaSuccess ? 0 : 3;
 }
 
@@ -1901,7 +1958,7 @@ static int planes_line_batch_npb(const PlanesBatch& b, long n_blocks, cudaStream
   static std::atomic<unsigned long long> attr_done{0};
   if (smem_attr((const void*)kern, planes_line_smem<N, PB>(), attr_done)) return 3;
   if (n_blocks <= 0) return 0;
-  kern<<<(unsigned)n_blocks, PB * N, planes_line_smem<N, PB>(), s>>>(b);
+  kern<<<(unsigned)n_blocks, LineTpl<N>::v * PB * N, planes_line_smem<N, PB>(), s>>>(b);
   return cudaGetLastError() == cudaSuccess ? 0 : 3;
 }
 

@@ -158,7 +158,7 @@ def test_planes_per_block_controls_host_only():
     assert L.planes_per_block(16, "mixed") == 8
     L.set_planes_per_block(16, "mixed", -4)             # whole lines in registers
     assert L.planes_per_block(16, "mixed") == -4
-    for N, prec, pb in ((64, "mixed", -1), (12, "fp64", -2), (16, "mixed", -3)):
+    for N, prec, pb in ((64, "mixed", -8), (12, "fp64", -2), (16, "mixed", -3)):
         with pytest.raises(L.LiseError) as e:           # no register-line variant there
             L.set_planes_per_block(N, prec, pb)
         assert e.value.status == L.EINVAL

@@ -583,7 +583,8 @@ def test_pencil_batch_choice_is_bitwise_neutral(N, precision):
         assert np.array_equal(x, tuned)
 
 
-@pytest.mark.parametrize("N,precision", [(16, "mixed"), (24, "mixed"), (32, "mixed"), (48, "mixed"), (12, "fp64")])
+@pytest.mark.parametrize("N,precision", [(16, "mixed"), (24, "mixed"), (32, "mixed"), (48, "mixed"), (64, "mixed"),
+                                         (12, "fp64")])
 def test_planes_per_block_choice_is_bitwise_neutral(N, precision):
     w = W.ufg_plane_waves(N, 13, noise_eps=0.05)
 

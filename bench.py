@@ -141,15 +141,15 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload, kernel):
+def recorded_traffic(workload, kernel, precision):
     """dram bytes per launch from the committed ncu summary, if it was taken on the
-    current kernel sources (profiles/traffic.json: {workload: {kernel: {...}}})."""
+    current kernel sources in this precision (profiles/traffic.json: {workload: {kernel: {...}}})."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
         e = d[workload][kernel]
-        if e.get("source_hash") != kernel_source_hash():
+        if e.get("source_hash") != kernel_source_hash() or e.get("precision") != precision:
             return None
         return float(e["dram_bytes_per_launch"])
     except Exception:
@@ -493,7 +493,7 @@ def roofline(w, prof, ms_per_step, fp64_peak):
     step_gbs = fused * qp_sites / (ms_per_step / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
             "peak_source": hbm_src + " (MEASURED_PEAKS.json hbm_gbs)", "kernel": dom,
-            "traffic": recorded_traffic(w.name, dom), "launch_ms": per_launch_ms,
+            "traffic": recorded_traffic(w.name, dom, w.precision), "launch_ms": per_launch_ms,
             "algorithmic_bytes_per_launch": bytes_per_launch, "byte_model": model,
             "step": {"achieved": step_gbs, "frac": step_gbs / hbm_peak, "bytes_per_step": fused * qp_sites},
             "design_bytes_per_launch": design_bytes,

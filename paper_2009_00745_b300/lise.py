@@ -164,12 +164,14 @@ def measure_fp64_peak(device=0) -> float:
 
 
 def planes_per_block(N, precision="mixed") -> int:
-    """Planes per block of the FFT planes kernel for this lattice and precision (0: tensor-core kernel)."""
+    """Planes per block of the FFT planes kernel for this lattice and precision (0: tensor-core kernel;
+    negative: the register-line variant with -pb planes per block)."""
     return int(load().lise_planes_per_block(int(N), PRECISIONS[precision]))
 
 
 def set_planes_per_block(N, precision="mixed", pb=0):
-    """Force the FFT planes kernel's planes per block (1, 2, 4, 8 where compiled), or 0 to re-tune."""
+    """Force the FFT planes kernel's variant, or 0 to re-tune: 1, 2, 4, 8 planes per block of the
+    shared-memory kernel, -1, -2, -4, -8 of the register-line kernel (where compiled)."""
     _check(load().lise_set_planes_per_block(int(N), PRECISIONS[precision], int(pb)), "lise_set_planes_per_block")
 
 

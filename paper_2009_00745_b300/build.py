@@ -1,16 +1,22 @@
-"""Build liblise.so (the CUDA library behind include/lise.h) in-tree for sm_103a."""
+"""Build liblise.so (the CUDA library behind include/lise.h) in-tree for sm_103a.
+
+Each source is compiled to an object file on its own (in parallel), then the objects are
+linked into the shared library."""
 import glob
 import os
 import subprocess
+import shutil
 import sys
+import tempfile
+from concurrent.futures import ThreadPoolExecutor
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "liblise.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
-FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
-         "-Xcompiler", "-fPIC", "-shared"]
+FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17", "--split-compile=0",
+         "-Xcompiler", "-fPIC"]
 
 
 def sources():
@@ -18,7 +24,8 @@ def sources():
 
 
 def _inputs():
-    return sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [os.path.join(ROOT, "include", "lise.h")]
+    return sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + sorted(glob.glob(os.path.join(CSRC, "*.h"))) + \
+        [os.path.join(ROOT, "include", "lise.h")]
 
 
 def up_to_date() -> bool:
@@ -31,10 +38,26 @@ def up_to_date() -> bool:
 def build(force: bool = False, verbose: bool = False) -> str:
     if not force and up_to_date():
         return LIB
-    cmd = [NVCC] + FLAGS + ["-o", LIB + ".tmp"] + sources()
-    if verbose:
-        print(" ".join(cmd), flush=True)
-    subprocess.run(cmd, check=True)
+    obj_dir = tempfile.mkdtemp(prefix="lise_build_")
+    srcs = sources()
+    objs = [os.path.join(obj_dir, os.path.basename(f)[:-3] + ".o") for f in srcs]
+
+    def compile_one(pair):
+        src, obj = pair
+        cmd = [NVCC] + FLAGS + ["-c", "-o", obj, src]
+        if verbose:
+            print(" ".join(cmd), flush=True)
+        subprocess.run(cmd, check=True)
+
+    try:
+        with ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
+            list(ex.map(compile_one, zip(srcs, objs)))
+        cmd = [NVCC, "-gencode", "arch=compute_103a,code=sm_103a", "-shared", "-o", LIB + ".tmp"] + objs
+        if verbose:
+            print(" ".join(cmd), flush=True)
+        subprocess.run(cmd, check=True)
+    finally:
+        shutil.rmtree(obj_dir, ignore_errors=True)
     os.replace(LIB + ".tmp", LIB)
     return LIB
 

@@ -556,8 +556,9 @@ __global__ void __launch_bounds__(256) k_planes_oz(PlanesArgs a) {
 //   producers (the next kWsProducerWarps warps): load a plane (one plane ahead), find its
 //     exponent groups, write its digits into operand stage s = i % 2 (i: the block's plane
 //     counter) and arrive on full[s];
-//   issuer (the last warp, one thread): waits for full[s], issues the plane's 56 MMAs into the
-//     columns [256 s, 256 s + 224) and commits to mma_done[s].
+//   issuer (the last warp, one thread): waits for full[s], issues the plane's 14 MMAs (7 data
+//     digits x 2 K-steps, each against the stacked D2 digits) into the columns
+//     [256 s, 256 s + 224) and commits to mma_done[s].
 // A producer refills stage s (operand, scales) only after tmem_free[s].  Every wait is bounded
 // (and gives up early once another role has given up): the block then records bit 4 in the
 // error word, the issuer waits (bounded) for its last MMAs, and the tensor memory is freed.
@@ -738,7 +739,6 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_planes_tc(PlanesArgs a) {
   } else if (w == kWsConsumerWarps + kWsProducerWarps) {
     // ---------------------------------------------------------------- MMA issuer
     if (lane == 0) {
-      constexpr uint32_t idesc = um::idesc_bf16_f32(P::M, N);
       long committed = 0;
       for (long i = 0; i < n_local; ++i) {
         const int s = (int)(i & 1);
@@ -749,15 +749,18 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_planes_tc(PlanesArgs a) {
         um::fence_after();
         const uint32_t a0 = um::su32(sA + (size_t)s * S * P::A_BYTES), b0 = um::su32(sB);
         const uint32_t d0 = tmem + 256u * s;
+        // The D2 digits are stacked along the MMA's N (B row l N + n is digit l of row n), so
+        // that one MMA of width (S - k) N multiplies data digit k by D2 digits 0 .. S - 1 - k and
+        // adds pair (k, l) into the columns of level k + l: it starts at column k N.  Chain
+        // k = 0 covers every level (its first K-step initialises them).  Each level receives
+        // the same exact products in the same order as one MMA per digit pair would give.
 #pragma unroll
-        for (int L = 0; L < S; ++L)
+        for (int k = 0; k < S; ++k)
 #pragma unroll
-          for (int k = 0; k <= L; ++k)
-#pragma unroll
-            for (int ks = 0; ks < P::K / 16; ++ks)
-              um::mma_bf16(d0 + L * N, um::sdesc(a0 + k * P::A_BYTES + ks * 2 * P::LBO, P::LBO, P::SBO),
-                           um::sdesc(b0 + (L - k) * P::B_BYTES + ks * 2 * P::LBO, P::LBO, P::SBO), idesc,
-                           (k > 0 || ks > 0) ? 1u : 0u);
+          for (int ks = 0; ks < P::K / 16; ++ks)
+            um::mma_bf16(d0 + k * N, um::sdesc(a0 + k * P::A_BYTES + ks * 2 * P::LBO, P::LBO, P::SBO),
+                         um::sdesc(b0 + ks * 2 * P::LBO, P::LBO, P::SBO), um::idesc_bf16_f32(P::M, (S - k) * N),
+                         (k > 0 || ks > 0) ? 1u : 0u);
         um::commit(&mma_done[s]);
         committed = i + 1;
       }

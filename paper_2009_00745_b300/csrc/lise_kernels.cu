@@ -824,6 +824,279 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_planes_tc(PlanesArgs a) {
   if (w == 0) um::dealloc(tmem, P::TMEM_COLS);
 }
 
+// T_x + T_y of the FP64 path on tcgen05 for 48^3 lattices.  One plane's lines per axis and part
+// are 2 x 48 = 96 rows, so each axis is one MMA row block of M = 128 (rows g N + line; rows 96-127
+// are not read back), and a plane's seven level accumulators (7 x 48 columns per axis) exceed the
+// tensor memory of two stages: the output columns are taken in chunks of 16.  Unit (axis, chunk),
+// six per plane, accumulates levels L = k + l of the output columns [16 o, 16 o + 16) in one
+// tensor-memory stage of 7 x 16 columns (four stages, columns [128 s, 128 s + 112)): per data digit
+// k and K-step, one MMA of width (7 - k) 16 against the chunk's stacked D2 digits 0 .. 6 - k (B row
+// l 16 + n' is digit l of D2 row 16 o + n'), starting at column 16 k.
+// Roles (one persistent block per SM):
+//   producers: load a plane, find its two exponent groups (re, im), wait until the MMAs of the
+//     previous plane are complete (a_free), write the digits of both axes (A_x: rows (g, y), K = x;
+//     A_y: rows (g, x), K = y) and arrive on a_full;
+//   issuer: for each unit, waits for a_full (first unit of a plane) and for its stage (tmem_free),
+//     issues the 21 MMAs, commits to mma_done[stage]; after a plane's six units commits to a_free;
+//   consumers: for each unit, read the stage's levels back (warp w: lanes 32 (w % 4)..; the two
+//     warps of lane quadrant 3 hold no data rows and only take part in the barriers), combine them
+//     in 64-bit integers into the plane's sums (T_x assigned, then T_y added), release the stage;
+//     after the plane's six units convert the sums (one FP64 rounding) and store T_xy.
+// Level sums with up to seven pairs over K = 48 can exceed 2^22 (levels 5 and 6): those two are
+// converted to integers by the FP32 unit's exact conversion, the others by the 1.5 * 2^23 bias.
+// Every wait is bounded and gives up once another role has given up.
+constexpr int kTccProducerWarps = 6, kTccConsumerWarps = 8;
+constexpr int kTccThreads = 32 * (kTccConsumerWarps + kTccProducerWarps + 1);
+template <int N>
+struct TcPlanesC {
+  static_assert(N == 48, "the chunked tensor-memory planes kernel is laid out for 48-point lines");
+  static constexpr int K = N, KS = K / 16, R = 2 * N, NCH = N / 16, CW = 16;  // rows, chunks, chunk width
+  static constexpr int LBO = 128, SBO = (K / 8) * 128;                    // K-major core matrices
+  static constexpr int DA = (R / 8) * SBO;                                 // one digit of one axis (96 rows)
+  static constexpr int A_AXIS = oz::S * DA + (128 - R) / 8 * SBO;           // + the unread rows 96-127
+  static constexpr int B_CHUNK = oz::S * CW * K * 2;                       // [digit][16 rows][K] per chunk
+  static constexpr int AP = N + 1;                                         // padded row of the sums
+  static constexpr size_t a_off = 0, b_off = (size_t)2 * A_AXIS;
+  static constexpr size_t acc_off = b_off + (size_t)NCH * B_CHUNK;
+  static constexpr size_t smem = acc_off + (size_t)2 * N * AP * 8;         // sums [g][y][AP]
+  static constexpr uint32_t TMEM_COLS = 512;                               // stages at 128 s
+  static constexpr int UNITS = 2 * NCH;                                    // (axis, chunk) per plane
+  // word offset of the chunked core-matrix D2 table behind the mma.sync fragment table
+  static constexpr size_t table_offset = (size_t)oz::S * (N / 8) * (N / 16) * 32 * 2;
+};
+__device__ __forceinline__ int tcc_off(int row, int k) {
+  return (row >> 3) * TcPlanesC<48>::SBO + (k >> 3) * TcPlanesC<48>::LBO + (row & 7) * 16 + (k & 7) * 2;
+}
+
+template <int N>
+__global__ void __launch_bounds__(kTccThreads, 1) k_planes_tcc(PlanesArgs a) {
+  using P = TcPlanesC<N>;
+  constexpr int S = oz::S, AP = P::AP, CW = P::CW;
+  constexpr int NP = 32 * kTccProducerWarps, NC = 32 * kTccConsumerWarps;
+  constexpr int BAR_P = 1, BAR_C = 2;
+  constexpr int BLK = (N / 2) * (N / 2) / NP;  // 2 x 2 blocks of the plane per producer thread
+  static_assert((N / 2) * (N / 2) % NP == 0, "producer blocks");
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char* sA = smem_raw + P::a_off;   // [axis][digit][rows][K], core-matrix layout
+  unsigned char* sB = smem_raw + P::b_off;   // [chunk][digit][16][K], core-matrix layout
+  long long* acc = reinterpret_cast<long long*>(smem_raw + P::acc_off);  // [g][y][AP]
+  __shared__ __align__(8) uint64_t a_full, a_free, mma_done[4], tmem_free[4];
+  __shared__ uint32_t tslot;
+  __shared__ unsigned ered[kTccProducerWarps][2];
+  __shared__ unsigned Es[2][2];  // per plane parity: the plane's exponent fields (re, im)
+  __shared__ volatile int stop;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+
+  const uint4* tb = reinterpret_cast<const uint4*>(a.ozb + P::table_offset);
+  for (int i = tid; i < P::NCH * P::B_CHUNK / 16; i += kTccThreads) reinterpret_cast<uint4*>(sB)[i] = tb[i];
+  if (tid == 0) {
+    um::mbar_init(&a_full, NP);
+    um::mbar_init(&a_free, 1);
+    for (int s = 0; s < 4; ++s) {
+      um::mbar_init(&mma_done[s], 1);
+      um::mbar_init(&tmem_free[s], 1);
+    }
+    stop = 0;
+  }
+  if (w == 0) um::alloc(&tslot, P::TMEM_COLS);
+  um::fence_proxy_async();
+  um::fence_before();
+  __syncthreads();
+  um::fence_after();
+  const uint32_t tmem = tslot;
+  const long limit = wait_limit(a.wait_polls);
+  const long n_local = (a.n_planes - blockIdx.x + gridDim.x - 1) / gridDim.x;
+  auto give_up = [&]() {
+    if (!stop) {
+      stop = 1;
+      if (a.err) atomicOr(a.err, 4);
+    }
+  };
+
+  if (w >= kTccConsumerWarps && w < kTccConsumerWarps + kTccProducerWarps) {
+    // ---------------------------------------------------------------- producers
+    const int pt = tid - NC, pw = pt >> 5;
+    const double2* src0 = a.xr ? reinterpret_cast<const double2*>(a.xr) : a.x;
+    for (long i = 0; i < n_local; ++i) {
+      const long pl = blockIdx.x + i * gridDim.x;
+      const double2* src = src0 + pl * N * N;
+      double2 v[BLK][2][2];
+      int by[BLK], bx[BLK];
+      unsigned e0 = 0, e1 = 0;
+#pragma unroll
+      for (int b = 0; b < BLK; ++b) {
+        const int blk = pt + NP * b;
+        by[b] = 2 * (blk / (N / 2));
+        bx[b] = 2 * (blk % (N / 2));
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+          for (int dx = 0; dx < 2; ++dx) {
+            v[b][dy][dx] = src[(by[b] + dy) * N + bx[b] + dx];
+            e0 = max(e0, oz::exp_field(v[b][dy][dx].x));
+            e1 = max(e1, oz::exp_field(v[b][dy][dx].y));
+          }
+      }
+      e0 = oz::warp_max(e0);
+      e1 = oz::warp_max(e1);
+      if (lane == 0) {
+        ered[pw][0] = e0;
+        ered[pw][1] = e1;
+      }
+      // the previous plane's MMAs have read the operand
+      bool ok = i < 1 || um::mbar_wait_or(&a_free, (uint32_t)((i - 1) & 1), limit, &stop);
+      if (!um::bar_and(BAR_P, NP, ok)) {  // (also makes every warp's ered visible)
+        give_up();
+        break;
+      }
+      unsigned Eg[2] = {0, 0};
+#pragma unroll
+      for (int k = 0; k < kTccProducerWarps; ++k) {
+        Eg[0] = max(Eg[0], ered[k][0]);
+        Eg[1] = max(Eg[1], ered[k][1]);
+      }
+      if (pt == 0) {
+        Es[i & 1][0] = Eg[0];
+        Es[i & 1][1] = Eg[1];
+      }
+#pragma unroll
+      for (int b = 0; b < BLK; ++b)
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+          unsigned short d[2][2][S];
+#pragma unroll
+          for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+            for (int dx = 0; dx < 2; ++dx) oz::split(g ? v[b][dy][dx].y : v[b][dy][dx].x, Eg[g], d[dy][dx]);
+#pragma unroll
+          for (int o = 0; o < 2; ++o) {
+            const int ox = tcc_off(g * N + by[b] + o, bx[b]);  // A_x row (g, y), k = x pair
+            const int oy = tcc_off(g * N + bx[b] + o, by[b]);  // A_y row (g, x), k = y pair
+#pragma unroll
+            for (int k = 0; k < S; ++k) {
+              *reinterpret_cast<unsigned*>(sA + k * P::DA + ox) = (unsigned)d[o][0][k] | ((unsigned)d[o][1][k] << 16);
+              *reinterpret_cast<unsigned*>(sA + P::A_AXIS + k * P::DA + oy) =
+                  (unsigned)d[0][o][k] | ((unsigned)d[1][o][k] << 16);
+            }
+          }
+        }
+      um::fence_proxy_async();  // the digits (generic proxy) before the tensor core reads them
+      um::mbar_arrive(&a_full);
+    }
+  } else if (w == kTccConsumerWarps + kTccProducerWarps) {
+    // ---------------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      long nfree = 0;        // commits to a_free so far
+      bool pending = false;  // MMAs issued since the last commit to a_free
+      bool ok = true;
+      for (long i = 0; i < n_local && ok; ++i) {
+        if (!um::mbar_wait_or(&a_full, (uint32_t)(i & 1), limit, &stop)) {
+          give_up();
+          break;
+        }
+        um::fence_after();
+        for (int u = 0; u < P::UNITS; ++u) {
+          const long j = i * P::UNITS + u;
+          const int s = (int)(j & 3), ax = u / P::NCH, o = u % P::NCH;
+          if (j >= 4 && !um::mbar_wait_or(&tmem_free[s], (uint32_t)(((j >> 2) - 1) & 1), limit, &stop)) {
+            give_up();
+            ok = false;
+            break;
+          }
+          um::fence_after();
+          const uint32_t a0 = um::su32(sA + (size_t)ax * P::A_AXIS), b0 = um::su32(sB + (size_t)o * P::B_CHUNK);
+          const uint32_t d0 = tmem + 128u * s;
+#pragma unroll
+          for (int k = 0; k < S; ++k)
+#pragma unroll
+            for (int ks = 0; ks < P::KS; ++ks)
+              um::mma_bf16(d0 + k * CW, um::sdesc(a0 + k * P::DA + ks * 2 * P::LBO, P::LBO, P::SBO),
+                           um::sdesc(b0 + ks * 2 * P::LBO, P::LBO, P::SBO), um::idesc_bf16_f32(128, (S - k) * CW),
+                           (k > 0 || ks > 0) ? 1u : 0u);
+          um::commit(&mma_done[s]);
+          pending = true;
+        }
+        if (!ok) break;
+        um::commit(&a_free);  // every MMA of the plane has read the operand
+        ++nfree;
+        pending = false;
+      }
+      // every MMA issued completes before the tensor memory is freed (a block that gave up in
+      // the middle of a plane commits once more), bounded
+      if (pending) {
+        um::commit(&a_free);
+        ++nfree;
+      }
+      if (nfree > 0) um::mbar_wait(&a_free, (uint32_t)((nfree - 1) & 1), kDrainPolls);
+    }
+  } else if (w < kTccConsumerWarps) {
+    // ---------------------------------------------------------------- consumers
+    const int q = w & 3, h = w >> 2;   // lane quadrant, column half of the chunk
+    const int r = 32 * q + lane;       // data row (r < 96)
+    const int g = r / N, line = r % N;
+    for (long i = 0; i < n_local; ++i) {
+      const long pl = blockIdx.x + i * gridDim.x;
+      int ps0 = 0, ps1 = 0;
+      bool ok = true;
+      for (int u = 0; u < P::UNITS && ok; ++u) {
+        const long j = i * P::UNITS + u;
+        const int s = (int)(j & 3), ax = u / P::NCH, o = u % P::NCH;
+        ok = um::mbar_wait_or(&mma_done[s], (uint32_t)((j >> 2) & 1), limit, &stop);
+        // (the plane's operand is complete: a_full orders the producers' scales before us)
+        if (ok && u == 0) ok = um::mbar_wait_or(&a_full, (uint32_t)(i & 1), limit, &stop);
+        if (!um::bar_and(BAR_C, NC, ok)) {
+          ok = false;
+          break;
+        }
+        um::fence_after();
+        if (u == 0) {
+          ps0 = oz::out_scale(a.oz_sD, Es[i & 1][0]);
+          ps1 = oz::out_scale(a.oz_sD, Es[i & 1][1]);
+        }
+        if (q < 3) {
+          uint32_t rv[S][8];
+#pragma unroll
+          for (int L = 0; L < S; ++L) um::ld8(rv[L], tmem + ((uint32_t)(32 * q) << 16) + 128u * s + L * CW + 8 * h);
+          um::wait_ld_deps<S>(rv);
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            unsigned lb[S];
+#pragma unroll
+            for (int L = 0; L < S; ++L) {
+              const float f = __uint_as_float(rv[L][c]);
+              lb[L] = L < 5 ? __float_as_uint(f + 12582912.0f) : (unsigned)__float2int_rn(f) + 0x4B400000u;
+            }
+            const long long T = oz::combine_biased(lb);
+            const int n = CW * o + 8 * h + c;
+            if (ax == 0)
+              acc[(g * N + line) * AP + n] = T;   // T_x[g][y = line][x = n]
+            else
+              acc[(g * N + n) * AP + line] += T;  // T_y[g][y = n][x = line]
+          }
+        }
+        um::fence_before();
+        um::bar_sync(BAR_C, NC);  // every consumer has read stage s and written its sums
+        if (tid == 0) um::mbar_arrive(&tmem_free[s]);
+      }
+      if (!ok) {
+        give_up();
+        break;
+      }
+      // T_xy = T_x + T_y of the plane, one rounding; coalesced complex128 stores
+      double2* out = reinterpret_cast<double2*>(a.txy) + pl * N * N;
+      for (int idx = tid; idx < N * N; idx += NC) {
+        const int y = idx / N, x = idx % N;
+        out[idx] = make_double2(oz::to_double_hw(acc[y * AP + x], ps0), oz::to_double_hw(acc[(N + y) * AP + x], ps1));
+      }
+      um::bar_sync(BAR_C, NC);  // the sums are read before the next plane's T_x is assigned
+    }
+  }
+  um::fence_before();
+  __syncthreads();
+  um::fence_after();
+  if (w == 0) um::dealloc(tmem, P::TMEM_COLS);
+}
+
 // T_z x on the tensor cores for one pencils batch (FP64 path, N % 16 == 0):
 // operand xr[j][c] of this thread's site (z, xl); result T_z x into buf[(2j + c) CS + z TX + xl].
 // Exponent groups: (state j, component c, re/im) over the block's (z, x) tile; data
@@ -1689,6 +1962,23 @@ static int planes_oz_n(const PlanesArgs& a, cudaStream_t s) {
   return cudaGetLastError() == cudaSuccess ? 0 : 3;
 }
 
+// persistent: one warp-specialised block per SM (48-point lines, chunked tensor memory)
+template <int N>
+static int planes_tcc_n(const PlanesArgs& a, cudaStream_t s) {
+  using P = TcPlanesC<N>;
+  auto kern = k_planes_tcc<N>;
+  static std::atomic<unsigned long long> attr_done{0};
+  if (smem_attr((const void*)kern, P::smem, attr_done)) return 3;
+  if (a.n_planes <= 0) return 0;
+  if (!a.ozb) return 1;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 3;
+  const long blocks = std::min<long>(a.n_planes, (long)sms);
+  kern<<<(unsigned)blocks, kTccThreads, P::smem, s>>>(a);
+  return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}
+
 // persistent: one warp-specialised block per SM, each walking the planes
 template <int N>
 static int planes_tc_n(const PlanesArgs& a, cudaStream_t s) {
@@ -1769,6 +2059,8 @@ static int planes_n(const PlanesArgs& a, cudaStream_t s, int pb) {
   if constexpr (pencil_oz<R, N>()) {
     if constexpr (N == 32)
       return planes_tc_n<N>(a, s);
+    else if constexpr (N == 48)
+      return planes_tcc_n<N>(a, s);
     else
       return planes_oz_n<N>(a, s);
   } else {
@@ -2202,8 +2494,8 @@ int launch_density(const PointwiseArgs& a, cudaStream_t s) {
 bool ozaki_path(int N, int mixed) { return !mixed && N % 16 == 0 && supported_n(N); }
 
 size_t ozaki_table_words(int N) {
-  // mma.sync fragments, then (N = 32: the tcgen05 planes kernel) the core-matrix table
-  return (size_t)oz::S * (N / 8) * (N / 16) * 32 * 2 + (N == 32 ? (size_t)oz::S * N * N / 2 : 0);
+  // mma.sync fragments, then (N = 32, 48: the tcgen05 planes kernels) the core-matrix table
+  return (size_t)oz::S * (N / 8) * (N / 16) * 32 * 2 + ((N == 32 || N == 48) ? (size_t)oz::S * N * N / 2 : 0);
 }
 
 // D2[n][k] = (1/N) sum_j (alpha/2) k_j^2 cos(k_j (n - k) a), k_j = 2 pi (j or j - N) / (N a),
@@ -2266,6 +2558,20 @@ int ozaki_table(int N, double a, double alpha, uint32_t* out) {
           const size_t byte = (size_t)l * N * N * 2 + (size_t)(n / 8) * (N / 8) * 128 + (k / 8) * 128 + (n % 8) * 16 + (k % 8) * 2;
           t[byte / 4] = bf16(D(l, n, k)) | (bf16(D(l, n, k + 1)) << 16);
         }
+  }
+  if (N == 48) {
+    // [chunk o][digit][n' < 16][k] (row l 16 + n' of chunk o is digit l of D2 row 16 o + n'),
+    // K-major core matrices, for the chunked tcgen05 planes kernel
+    uint32_t* t = out + (size_t)oz::S * NTL * KS * 32 * 2;
+    const size_t sbo = (size_t)(N / 8) * 128, chunk = (size_t)oz::S * 16 * N * 2;
+    for (int o = 0; o < N / 16; ++o)
+      for (int l = 0; l < oz::S; ++l)
+        for (int n1 = 0; n1 < 16; ++n1)
+          for (int k = 0; k < N; k += 2) {
+            const int row = l * 16 + n1;
+            const size_t byte = o * chunk + (size_t)(row / 8) * sbo + (k / 8) * 128 + (row % 8) * 16 + (k % 8) * 2;
+            t[byte / 4] = bf16(D(l, 16 * o + n1, k)) | (bf16(D(l, 16 * o + n1, k + 1)) << 16);
+          }
   }
   return sD;
 }

@@ -36,7 +36,7 @@ unsigned char* g_scratch_dev[kMaxDevices] = {};  // device address of g_rhs_scra
 alignas(16) double g_tab_d[4 * 64];
 alignas(16) float g_tab_f[4 * 64];
 // D2 digit fragments of the FP64 tensor-core path (largest lattice: 64)
-alignas(16) uint32_t g_tab_oz[7 * 8 * 4 * 32 * 2];
+alignas(16) uint32_t g_tab_oz[7 * 6 * 3 * 32 * 2 + 7 * 48 * 48 / 2];  // the largest table: N = 48
 
 size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 

@@ -1172,12 +1172,10 @@ template <typename R, int N>
 __host__ __device__ constexpr bool pencil_oz() { return sizeof(R) == 8 && N % 16 == 0; }
 // x-tile width of the pencils kernel: 4 on the FP64 tensor-core path (128-thread blocks, several
 // resident per SM, so that blocks in their digit/tensor phase overlap others in their FP64
-// epilogue), for N not a multiple of 8, and for the FP32 compute precision at N = 48 (192-thread
-// blocks, four resident per SM instead of two of 384 threads: 48^3 x 4096 mixed pencils launches
-// 9.64 -> 9.1 ms); else 8
+// epilogue) and for N not a multiple of 8, else 8
 template <typename R, int N>
 __host__ __device__ constexpr int pencil_tx_c() {
-  return (pencil_oz<R, N>() || N % 8 != 0 || (sizeof(R) == 4 && N == 48)) ? 4 : 8;
+  return (pencil_oz<R, N>() || N % 8 != 0) ? 4 : 8;
 }
 template <typename T, int N, int TX, int QB>
 __host__ __device__ constexpr int pencil_smem_bytes() {
@@ -1384,10 +1382,11 @@ __device__ __forceinline__ void pencils_body(const PencilArgs& a, const int g, c
       }
       // H x = [[h, Delta], [Delta*, -h*]] x with h = T + W (W real, T real-symmetric);
       // with trivial-phase removal (Eq. sp_en) the generator is H - eta_q.
-      // The FP64 tensor-core path reloads the operand (an L1/L2 hit) rather than keeping
-      // it in registers across the digit products.
+      // The FP64 tensor-core path reloads the operand (an L2 hit) rather than keeping it in
+      // registers across the digit products.  The epilogue's loads bypass L1 (ld.global.cg;
+      // 32^3 x 2048 FP64: 5.38 -> 5.34 ms per launch).
       auto opnd = [&](long i) -> T {
-        return a.xr ? reinterpret_cast<const T*>(a.xr)[i] : to_r<R>(a.x[i]);
+        return a.xr ? __ldcg(reinterpret_cast<const T*>(a.xr) + i) : to_r<R>(__ldcg(a.x + i));
       };
       const T u = kOz ? opnd(iu) : xr[j][0], v = kOz ? opnd(iv) : xr[j][1];
       const R w = a.eta ? Wr - (R)a.eta[q] : Wr;
@@ -1454,9 +1453,9 @@ __device__ __forceinline__ void pencils_body(const PencilArgs& a, const int g, c
             reinterpret_cast<double2*>(a.pc)[i] = make_double2(fma(-17.0, fd.x, rr.x), fma(-17.0, fd.y, rr.y));
             yd[c] = yn;
           } else {
-            const T rr = kPrefetch ? rstage[si_] : reinterpret_cast<const T*>(a.r)[i];
+            const T rr = kPrefetch ? rstage[si_] : __ldcg(reinterpret_cast<const T*>(a.r) + i);
             if constexpr (sizeof(R) == 8) {
-              const double2 qv = a.q[i];
+              const double2 qv = __ldcg(a.q + i);
               yn = make_double2(fma((double)k1, (double)f.x, qv.x), fma((double)k1, (double)f.y, qv.y));
             } else {
               yn = dadd(kPrefetch ? qstage[si_] : a.q[i], to_d(T{k1 * f.x, k1 * f.y}));
@@ -1489,10 +1488,10 @@ __device__ __forceinline__ void pencils_body(const PencilArgs& a, const int g, c
           const long i = c ? iv : iu;
           const T f = c ? fvr : fur;
           dslot[i] = f;
-          const T e0 = reinterpret_cast<const T*>(a.d0)[i], e1 = reinterpret_cast<const T*>(a.d1)[i],
-                  e2 = reinterpret_cast<const T*>(a.d2)[i];
-          const T pcv = reinterpret_cast<const T*>(a.pc)[i];
-          const double2 xv = a.x[i], y0v = a.y0[i];
+          const T e0 = __ldcg(reinterpret_cast<const T*>(a.d0) + i), e1 = __ldcg(reinterpret_cast<const T*>(a.d1) + i),
+                  e2 = __ldcg(reinterpret_cast<const T*>(a.d2) + i);
+          const T pcv = __ldcg(reinterpret_cast<const T*>(a.pc) + i);
+          const double2 xv = __ldcg(a.x + i), y0v = __ldcg(a.y0 + i);
           T Rv, mv;
           double2 qv;
           if constexpr (sizeof(R) == 8) {
@@ -1564,8 +1563,7 @@ __device__ __forceinline__ void pencils_body(const PencilArgs& a, const int g, c
 #define LISE_PENCILS_BOUNDS                                                                                    \
   __launch_bounds__(N * TX, (N * TX >= 384 && sizeof(R) == 4) || N * TX == 256                                 \
                                 ? 2                                                                            \
-                                : ((sizeof(R) == 8 && N * TX == 128) ? 7                                       \
-                                                                     : (N * TX == 192 ? (sizeof(R) == 8 ? 3 : (TX == 4 ? 4 : 1)) : 1)))
+                                : ((sizeof(R) == 8 && N * TX == 128) ? 7 : ((sizeof(R) == 8 && N * TX == 192) ? 3 : 1)))
 
 template <typename R, int N, int TX, int QB, int MODE, bool ST = false>
 __global__ void LISE_PENCILS_BOUNDS k_pencils(const __grid_constant__ PencilArgs a) {
@@ -1943,7 +1941,7 @@ bool supported_n(int N) {
     default: return false;
   }
 }
-int pencil_tx(int N, int mixed) { return (ozaki_path(N, mixed) || N % 8 != 0 || (mixed && N == 48)) ? 4 : 8; }
+int pencil_tx(int N, int mixed) { return (ozaki_path(N, mixed) || N % 8 != 0) ? 4 : 8; }
 int pencil_qb(int N, int mixed) {
   const int t = pencil_qb_get(N, mixed);
   return t ? t : ((N >= 40 || (N >= 32 && (mixed || ozaki_path(N, mixed)))) ? 2 : 4);

@@ -143,12 +143,13 @@ def kernel_source_hash():
 
 def recorded_traffic(workload, kernel, precision):
     """dram bytes per launch from the committed ncu summary, if it was taken on the
-    current kernel sources in this precision (profiles/traffic.json: {workload: {kernel: {...}}})."""
+    current kernel sources in this precision (profiles/traffic.json: {workload: {kernel: {...}}},
+    or {"workload@precision": {...}} for a workload measured in a precision other than its own)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
-        e = d[workload][kernel]
+        e = d.get(f"{workload}@{precision}", d.get(workload, {}))[kernel]
         if e.get("source_hash") != kernel_source_hash() or e.get("precision") != precision:
             return None
         return float(e["dram_bytes_per_launch"])

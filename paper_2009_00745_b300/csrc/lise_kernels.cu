@@ -1004,14 +1004,18 @@ __global__ void __launch_bounds__(kTccThreads, 1) k_planes_tcc(PlanesArgs a) {
             break;
           }
           um::fence_after();
-          const uint32_t a0 = um::su32(sA + (size_t)ax * P::A_AXIS), b0 = um::su32(sB + (size_t)o * P::B_CHUNK);
           const uint32_t d0 = tmem + 128u * s;
+          // descriptors of the unit's first core matrices; the others differ only in the start
+          // address field (shared-memory addresses are below 2^18, so the 14-bit field of
+          // address / 16 never carries into the next field)
+          const uint64_t ad0 = um::sdesc(um::su32(sA + (size_t)ax * P::A_AXIS), P::LBO, P::SBO);
+          const uint64_t bd0 = um::sdesc(um::su32(sB + (size_t)o * P::B_CHUNK), P::LBO, P::SBO);
 #pragma unroll
           for (int k = 0; k < S; ++k)
 #pragma unroll
             for (int ks = 0; ks < P::KS; ++ks)
-              um::mma_bf16(d0 + k * CW, um::sdesc(a0 + k * P::DA + ks * 2 * P::LBO, P::LBO, P::SBO),
-                           um::sdesc(b0 + ks * 2 * P::LBO, P::LBO, P::SBO), um::idesc_bf16_f32(128, (S - k) * CW),
+              um::mma_bf16(d0 + k * CW, ad0 + (uint64_t)((k * P::DA + ks * 2 * P::LBO) >> 4),
+                           bd0 + (uint64_t)((ks * 2 * P::LBO) >> 4), um::idesc_bf16_f32(128, (S - k) * CW),
                            (k > 0 || ks > 0) ? 1u : 0u);
           um::commit(&mma_done[s]);
           pending = true;

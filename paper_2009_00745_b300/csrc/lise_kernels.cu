@@ -827,21 +827,21 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_planes_tc(PlanesArgs a) {
 // T_x + T_y of the FP64 path on tcgen05 for 48^3 lattices.  One plane's lines per axis and part
 // are 2 x 48 = 96 rows, so each axis is one MMA row block of M = 128 (rows g N + line; rows 96-127
 // are not read back), and a plane's seven level accumulators (7 x 48 columns per axis) exceed the
-// tensor memory of two stages: the output columns are taken in chunks of 16.  Unit (axis, chunk),
-// six per plane, accumulates levels L = k + l of the output columns [16 o, 16 o + 16) in one
-// tensor-memory stage of 7 x 16 columns (four stages, columns [128 s, 128 s + 112)): per data digit
-// k and K-step, one MMA of width (7 - k) 16 against the chunk's stacked D2 digits 0 .. 6 - k (B row
-// l 16 + n' is digit l of D2 row 16 o + n'), starting at column 16 k.
+// tensor memory of two stages: the output columns are taken in chunks, [0, 32) and [32, 48).  Unit
+// (axis, chunk), four per plane, accumulates levels L = k + l of the chunk's w output columns in one
+// tensor-memory stage of 7 w columns (two stages, columns [256 s, 256 s + 7 w)): per data digit k and
+// K-step, one MMA of width (7 - k) w against the chunk's stacked D2 digits 0 .. 6 - k (B row l w + n'
+// is digit l of the chunk's D2 row n'), starting at column k w.
 // Roles (one persistent block per SM):
 //   producers: load a plane, find its two exponent groups (re, im), wait until the MMAs of the
 //     previous plane are complete (a_free), write the digits of both axes (A_x: rows (g, y), K = x;
 //     A_y: rows (g, x), K = y) and arrive on a_full;
 //   issuer: for each unit, waits for a_full (first unit of a plane) and for its stage (tmem_free),
-//     issues the 21 MMAs, commits to mma_done[stage]; after a plane's six units commits to a_free;
+//     issues the 21 MMAs, commits to mma_done[stage]; after a plane's four units commits to a_free;
 //   consumers: for each unit, read the stage's levels back (warp w: lanes 32 (w % 4)..; the two
 //     warps of lane quadrant 3 hold no data rows and only take part in the barriers), combine them
 //     in 64-bit integers into the plane's sums (T_x assigned, then T_y added), release the stage;
-//     after the plane's six units convert the sums (one FP64 rounding) and store T_xy.
+//     after the plane's four units convert the sums (one FP64 rounding) and store T_xy.
 // Level sums with up to seven pairs over K = 48 can exceed 2^22 (levels 5 and 6): those two are
 // converted to integers by the FP32 unit's exact conversion, the others by the 1.5 * 2^23 bias.
 // Every wait is bounded and gives up once another role has given up.
@@ -850,16 +850,21 @@ constexpr int kTccThreads = 32 * (kTccConsumerWarps + kTccProducerWarps + 1);
 template <int N>
 struct TcPlanesC {
   static_assert(N == 48, "the chunked tensor-memory planes kernel is laid out for 48-point lines");
-  static constexpr int K = N, KS = K / 16, R = 2 * N, NCH = N / 16, CW = 16;  // rows, chunks, chunk width
+  static constexpr int K = N, KS = K / 16, R = 2 * N, NCH = 2;            // rows, chunks per axis
+  // output-column chunks: [0, 32) and [32, 48)
+  __host__ __device__ static constexpr int cw(int o) { return o == 0 ? 32 : 16; }
+  __host__ __device__ static constexpr int c0(int o) { return o == 0 ? 0 : 32; }
   static constexpr int LBO = 128, SBO = (K / 8) * 128;                    // K-major core matrices
   static constexpr int DA = (R / 8) * SBO;                                 // one digit of one axis (96 rows)
   static constexpr int A_AXIS = oz::S * DA + (128 - R) / 8 * SBO;           // + the unread rows 96-127
-  static constexpr int B_CHUNK = oz::S * CW * K * 2;                       // [digit][16 rows][K] per chunk
+  // [digit][cw(o) rows][K] per chunk, chunk 1 after chunk 0
+  __host__ __device__ static constexpr int b_chunk_off(int o) { return o == 0 ? 0 : oz::S * 32 * K * 2; }
+  static constexpr int B_BYTES = oz::S * N * K * 2;
   static constexpr int AP = N + 1;                                         // padded row of the sums
   static constexpr size_t a_off = 0, b_off = (size_t)2 * A_AXIS;
-  static constexpr size_t acc_off = b_off + (size_t)NCH * B_CHUNK;
+  static constexpr size_t acc_off = b_off + (size_t)B_BYTES;
   static constexpr size_t smem = acc_off + (size_t)2 * N * AP * 8;         // sums [g][y][AP]
-  static constexpr uint32_t TMEM_COLS = 512;                               // stages at 128 s
+  static constexpr uint32_t TMEM_COLS = 512;                               // two stages at 256 s
   static constexpr int UNITS = 2 * NCH;                                    // (axis, chunk) per plane
   // word offset of the chunked core-matrix D2 table behind the mma.sync fragment table
   static constexpr size_t table_offset = (size_t)oz::S * (N / 8) * (N / 16) * 32 * 2;
@@ -871,7 +876,7 @@ __device__ __forceinline__ int tcc_off(int row, int k) {
 template <int N>
 __global__ void __launch_bounds__(kTccThreads, 1) k_planes_tcc(PlanesArgs a) {
   using P = TcPlanesC<N>;
-  constexpr int S = oz::S, AP = P::AP, CW = P::CW;
+  constexpr int S = oz::S, AP = P::AP;
   constexpr int NP = 32 * kTccProducerWarps, NC = 32 * kTccConsumerWarps;
   constexpr int BAR_P = 1, BAR_C = 2;
   constexpr int BLK = (N / 2) * (N / 2) / NP;  // 2 x 2 blocks of the plane per producer thread
@@ -880,7 +885,7 @@ __global__ void __launch_bounds__(kTccThreads, 1) k_planes_tcc(PlanesArgs a) {
   unsigned char* sA = smem_raw + P::a_off;   // [axis][digit][rows][K], core-matrix layout
   unsigned char* sB = smem_raw + P::b_off;   // [chunk][digit][16][K], core-matrix layout
   long long* acc = reinterpret_cast<long long*>(smem_raw + P::acc_off);  // [g][y][AP]
-  __shared__ __align__(8) uint64_t a_full, a_free, mma_done[4], tmem_free[4];
+  __shared__ __align__(8) uint64_t a_full, a_free, mma_done[2], tmem_free[2];
   __shared__ uint32_t tslot;
   __shared__ unsigned ered[kTccProducerWarps][2];
   __shared__ unsigned Es[2][2];  // per plane parity: the plane's exponent fields (re, im)
@@ -888,11 +893,11 @@ __global__ void __launch_bounds__(kTccThreads, 1) k_planes_tcc(PlanesArgs a) {
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
 
   const uint4* tb = reinterpret_cast<const uint4*>(a.ozb + P::table_offset);
-  for (int i = tid; i < P::NCH * P::B_CHUNK / 16; i += kTccThreads) reinterpret_cast<uint4*>(sB)[i] = tb[i];
+  for (int i = tid; i < P::B_BYTES / 16; i += kTccThreads) reinterpret_cast<uint4*>(sB)[i] = tb[i];
   if (tid == 0) {
     um::mbar_init(&a_full, NP);
     um::mbar_init(&a_free, 1);
-    for (int s = 0; s < 4; ++s) {
+    for (int s = 0; s < 2; ++s) {
       um::mbar_init(&mma_done[s], 1);
       um::mbar_init(&tmem_free[s], 1);
     }
@@ -995,27 +1000,29 @@ __global__ void __launch_bounds__(kTccThreads, 1) k_planes_tcc(PlanesArgs a) {
           break;
         }
         um::fence_after();
+#pragma unroll
         for (int u = 0; u < P::UNITS; ++u) {
           const long j = i * P::UNITS + u;
-          const int s = (int)(j & 3), ax = u / P::NCH, o = u % P::NCH;
-          if (j >= 4 && !um::mbar_wait_or(&tmem_free[s], (uint32_t)(((j >> 2) - 1) & 1), limit, &stop)) {
+          const int s = (int)(j & 1), ax = u / P::NCH, o = u % P::NCH;
+          if (j >= 2 && !um::mbar_wait_or(&tmem_free[s], (uint32_t)(((j >> 1) - 1) & 1), limit, &stop)) {
             give_up();
             ok = false;
             break;
           }
           um::fence_after();
-          const uint32_t d0 = tmem + 128u * s;
+          const uint32_t d0 = tmem + 256u * s;
           // descriptors of the unit's first core matrices; the others differ only in the start
           // address field (shared-memory addresses are below 2^18, so the 14-bit field of
           // address / 16 never carries into the next field)
           const uint64_t ad0 = um::sdesc(um::su32(sA + (size_t)ax * P::A_AXIS), P::LBO, P::SBO);
-          const uint64_t bd0 = um::sdesc(um::su32(sB + (size_t)o * P::B_CHUNK), P::LBO, P::SBO);
+          const uint64_t bd0 = um::sdesc(um::su32(sB + P::b_chunk_off(o)), P::LBO, P::SBO);
+          const int cw = P::cw(o);
 #pragma unroll
           for (int k = 0; k < S; ++k)
 #pragma unroll
             for (int ks = 0; ks < P::KS; ++ks)
-              um::mma_bf16(d0 + k * CW, ad0 + (uint64_t)((k * P::DA + ks * 2 * P::LBO) >> 4),
-                           bd0 + (uint64_t)((ks * 2 * P::LBO) >> 4), um::idesc_bf16_f32(128, (S - k) * CW),
+              um::mma_bf16(d0 + k * cw, ad0 + (uint64_t)((k * P::DA + ks * 2 * P::LBO) >> 4),
+                           bd0 + (uint64_t)((ks * 2 * P::LBO) >> 4), um::idesc_bf16_f32(128, (S - k) * cw),
                            (k > 0 || ks > 0) ? 1u : 0u);
           um::commit(&mma_done[s]);
           pending = true;
@@ -1044,8 +1051,8 @@ __global__ void __launch_bounds__(kTccThreads, 1) k_planes_tcc(PlanesArgs a) {
       bool ok = true;
       for (int u = 0; u < P::UNITS && ok; ++u) {
         const long j = i * P::UNITS + u;
-        const int s = (int)(j & 3), ax = u / P::NCH, o = u % P::NCH;
-        ok = um::mbar_wait_or(&mma_done[s], (uint32_t)((j >> 2) & 1), limit, &stop);
+        const int s = (int)(j & 1), ax = u / P::NCH, o = u % P::NCH;
+        ok = um::mbar_wait_or(&mma_done[s], (uint32_t)((j >> 1) & 1), limit, &stop);
         // (the plane's operand is complete: a_full orders the producers' scales before us)
         if (ok && u == 0) ok = um::mbar_wait_or(&a_full, (uint32_t)(i & 1), limit, &stop);
         if (!um::bar_and(BAR_C, NC, ok)) {
@@ -1058,24 +1065,29 @@ __global__ void __launch_bounds__(kTccThreads, 1) k_planes_tcc(PlanesArgs a) {
           ps1 = oz::out_scale(a.oz_sD, Es[i & 1][1]);
         }
         if (q < 3) {
-          uint32_t rv[S][8];
+          // this warp's half of the chunk: cw / 2 columns, 8 at a time
+          const int cw = P::cw(o);
+          for (int part = 0; part < cw / 16; ++part) {
+            const int col = (cw / 2) * h + 8 * part;  // first column within the chunk
+            uint32_t rv[S][8];
 #pragma unroll
-          for (int L = 0; L < S; ++L) um::ld8(rv[L], tmem + ((uint32_t)(32 * q) << 16) + 128u * s + L * CW + 8 * h);
-          um::wait_ld_deps<S>(rv);
+            for (int L = 0; L < S; ++L) um::ld8(rv[L], tmem + ((uint32_t)(32 * q) << 16) + 256u * s + L * cw + col);
+            um::wait_ld_deps<S>(rv);
 #pragma unroll
-          for (int c = 0; c < 8; ++c) {
-            unsigned lb[S];
+            for (int c = 0; c < 8; ++c) {
+              unsigned lb[S];
 #pragma unroll
-            for (int L = 0; L < S; ++L) {
-              const float f = __uint_as_float(rv[L][c]);
-              lb[L] = L < 5 ? __float_as_uint(f + 12582912.0f) : (unsigned)__float2int_rn(f) + 0x4B400000u;
+              for (int L = 0; L < S; ++L) {
+                const float f = __uint_as_float(rv[L][c]);
+                lb[L] = L < 5 ? __float_as_uint(f + 12582912.0f) : (unsigned)__float2int_rn(f) + 0x4B400000u;
+              }
+              const long long T = oz::combine_biased(lb);
+              const int n = P::c0(o) + col + c;
+              if (ax == 0)
+                acc[(g * N + line) * AP + n] = T;   // T_x[g][y = line][x = n]
+              else
+                acc[(g * N + n) * AP + line] += T;  // T_y[g][y = n][x = line]
             }
-            const long long T = oz::combine_biased(lb);
-            const int n = CW * o + 8 * h + c;
-            if (ax == 0)
-              acc[(g * N + line) * AP + n] = T;   // T_x[g][y = line][x = n]
-            else
-              acc[(g * N + n) * AP + line] += T;  // T_y[g][y = n][x = line]
           }
         }
         um::fence_before();
@@ -2562,18 +2574,23 @@ int ozaki_table(int N, double a, double alpha, uint32_t* out) {
         }
   }
   if (N == 48) {
-    // [chunk o][digit][n' < 16][k] (row l 16 + n' of chunk o is digit l of D2 row 16 o + n'),
-    // K-major core matrices, for the chunked tcgen05 planes kernel
+    // output-column chunks [0, 32) and [32, 48): [chunk o][digit][n' < width][k] (row l width + n'
+    // of chunk o is digit l of D2 row start + n'), K-major core matrices, for the chunked tcgen05
+    // planes kernel
     uint32_t* t = out + (size_t)oz::S * NTL * KS * 32 * 2;
-    const size_t sbo = (size_t)(N / 8) * 128, chunk = (size_t)oz::S * 16 * N * 2;
-    for (int o = 0; o < N / 16; ++o)
+    const size_t sbo = (size_t)(N / 8) * 128;
+    const int width[2] = {32, 16}, start[2] = {0, 32};
+    size_t base = 0;
+    for (int o = 0; o < 2; ++o) {
       for (int l = 0; l < oz::S; ++l)
-        for (int n1 = 0; n1 < 16; ++n1)
+        for (int n1 = 0; n1 < width[o]; ++n1)
           for (int k = 0; k < N; k += 2) {
-            const int row = l * 16 + n1;
-            const size_t byte = o * chunk + (size_t)(row / 8) * sbo + (k / 8) * 128 + (row % 8) * 16 + (k % 8) * 2;
-            t[byte / 4] = bf16(D(l, 16 * o + n1, k)) | (bf16(D(l, 16 * o + n1, k + 1)) << 16);
+            const int row = l * width[o] + n1;
+            const size_t byte = base + (size_t)(row / 8) * sbo + (k / 8) * 128 + (row % 8) * 16 + (k % 8) * 2;
+            t[byte / 4] = bf16(D(l, start[o] + n1, k)) | (bf16(D(l, start[o] + n1, k + 1)) << 16);
           }
+      base += (size_t)oz::S * width[o] * N * 2;
+    }
   }
   return sD;
 }

@@ -747,7 +747,10 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_planes_tc(PlanesArgs a) {
           break;
         }
         um::fence_after();
-        const uint32_t a0 = um::su32(sA + (size_t)s * S * P::A_BYTES), b0 = um::su32(sB);
+        // descriptors of the first core matrices; the others differ only in the start-address field
+        // (shared-memory addresses are below 2^18: the 14-bit field of address / 16 never carries)
+        const uint64_t ad0 = um::sdesc(um::su32(sA + (size_t)s * S * P::A_BYTES), P::LBO, P::SBO);
+        const uint64_t bd0 = um::sdesc(um::su32(sB), P::LBO, P::SBO);
         const uint32_t d0 = tmem + 256u * s;
         // The D2 digits are stacked along the MMA's N (B row l N + n is digit l of row n), so
         // that one MMA of width (S - k) N multiplies data digit k by D2 digits 0 .. S - 1 - k and
@@ -758,8 +761,8 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_planes_tc(PlanesArgs a) {
         for (int k = 0; k < S; ++k)
 #pragma unroll
           for (int ks = 0; ks < P::K / 16; ++ks)
-            um::mma_bf16(d0 + k * N, um::sdesc(a0 + k * P::A_BYTES + ks * 2 * P::LBO, P::LBO, P::SBO),
-                         um::sdesc(b0 + ks * 2 * P::LBO, P::LBO, P::SBO), um::idesc_bf16_f32(P::M, (S - k) * N),
+            um::mma_bf16(d0 + k * N, ad0 + (uint64_t)((k * P::A_BYTES + ks * 2 * P::LBO) >> 4),
+                         bd0 + (uint64_t)((ks * 2 * P::LBO) >> 4), um::idesc_bf16_f32(P::M, (S - k) * N),
                          (k > 0 || ks > 0) ? 1u : 0u);
         um::commit(&mma_done[s]);
         committed = i + 1;

@@ -3,10 +3,11 @@ context recovers through a new state.
 
 lise_set_wait_limit(ctx, 0) makes every bounded wait give up without polling (nothing
 else is changed: no fault, no trap, no endless loop).  The kernels that wait on the
-hardware are the tensor-memory planes kernel (FP64 path, 32^3 lattices: the MMA
-completion) and the staged pencils kernel (mixed path: the tensor-memory-accelerator
-copies); a block whose wait gave up lets the work it has in flight finish, frees its
-tensor memory and exits, and the host reports LISE_ETIMEOUT at the next synchronising call.
+hardware are the tensor-memory planes kernels (FP64 path, 32^3 and 48^3 lattices: the MMA
+completion and the hand-offs between their roles) and the staged pencils kernel (mixed
+path: the tensor-memory-accelerator copies); a block whose wait gave up lets the work it
+has in flight finish, frees its tensor memory and exits, and the host reports LISE_ETIMEOUT
+at the next synchronising call.
 """
 import numpy as np
 import pytest
@@ -24,7 +25,7 @@ def _lib():
     L.load()
 
 
-@pytest.mark.parametrize("N,precision,n_qp", [(32, "fp64", 8), (16, "mixed", 12), (48, "mixed", 6)])
+@pytest.mark.parametrize("N,precision,n_qp", [(32, "fp64", 8), (48, "fp64", 4), (16, "mixed", 12), (48, "mixed", 6)])
 def test_wait_that_runs_out_is_reported_and_the_context_recovers(N, precision, n_qp):
     w = W.ufg_plane_waves(N, n_qp, noise_eps=0.05)
     with L.Context.from_workload(w, precision=precision) as ref:

@@ -27,9 +27,9 @@ def _noalloc(p, psi_dev, t, out_dev):
 
 
 @pytest.mark.parametrize("N,n_qp,precision,tol", [(16, 24, "fp64", TOL_RHS), (16, 24, "mixed", TOL_RHS),
-                                                  (32, 24, "fp64", TOL_RHS)])
+                                                  (32, 24, "fp64", TOL_RHS), (48, 4, "fp64", TOL_RHS)])
 def test_noalloc_matches_context_rhs_twice(N, n_qp, precision, tol):
-    # (32^3 FP64 runs the tensor-memory planes kernel with its core-matrix D2 table)
+    # (32^3 and 48^3 FP64 run the tensor-memory planes kernels with their core-matrix D2 tables)
     import torch
     from paper_2009_00745_b300 import build
     build.build()
